@@ -1,0 +1,230 @@
+"""Seeded synthetic inputs: the initial conditions of the benchmark cases.
+
+This module is shared by the CUDA-path tests, the oracle tests and the
+benchmark. It holds initial and exact solutions of the flows only, none of the
+scheme's arithmetic. Every state is returned as conservative variables
+(rho, rho u, rho v, E) in structure-of-arrays form ``[4][ny][nx]`` (x fastest),
+float64, with cell centres at x_j = x0 + (j + 1/2) dx.
+
+Cases (Sec. 3 of the paper, plus the synthetic ensemble members):
+
+* ``isentropic_vortex`` -- Example 1 (order of accuracy), on a periodic square.
+* ``riemann_2d``       -- Example 9 (Schulz-Rinne 2D Riemann problem).
+* ``viscous_shock_tube`` -- Example 10 (Daru-Tenaud), Re = 1000.
+* ``kelvin_helmholtz`` -- seeded periodic shear layer (ensemble member).
+* ``entropy_wave``, ``free_stream``, ``shear_wave`` -- exact-solution checks.
+* ``ensemble``         -- seeded table of uneven vortex / shear-layer cases.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+BC_PERIODIC, BC_TRANSMISSIVE, BC_NOSLIP_WALL, BC_SYMMETRY = 0, 1, 2, 3
+
+
+@dataclass
+class Case:
+    name: str
+    Q: np.ndarray          # [4][ny][nx] conservative state, float64
+    dx: float
+    dy: float
+    gamma: float
+    mu: float
+    Pr: float
+    bc: tuple              # (west, east, south, north)
+    t_end: float = 0.0
+    cfl: float = 0.5
+    meta: dict | None = None
+
+    @property
+    def nx(self) -> int:
+        return self.Q.shape[2]
+
+    @property
+    def ny(self) -> int:
+        return self.Q.shape[1]
+
+
+def prim_to_cons(rho, u, v, p, gamma):
+    """Ideal-gas conservative state from primitive fields (works on complex
+    input too, for complex-step derivatives in tests)."""
+    E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)
+    return np.stack([rho, rho * u, rho * v, E])
+
+
+def centres(n, lo, hi):
+    d = (hi - lo) / n
+    return lo + (np.arange(n) + 0.5) * d, d
+
+
+# --------------------------------------------------------------------------
+# Example 1: isentropic vortex
+# --------------------------------------------------------------------------
+
+def vortex_prims(X, Y, t=0.0, eps=5.0, gamma=1.4, centre=(5.0, 5.0),
+                 period=(10.0, 10.0), u_inf=1.0, v_inf=1.0):
+    """Exact primitive fields of the convected isentropic vortex at time t.
+
+    The periodic problem's exact solution is its initial data translated by
+    (u_inf, v_inf) t; the displacement from the vortex centre is taken as the
+    minimum image inside one period, as in the initial data. X, Y may be
+    complex (complex-step differentiation in tests)."""
+    Lx, Ly = period
+    xr = X - centre[0] - u_inf * t
+    yr = Y - centre[1] - v_inf * t
+    # minimum image on the real part only (keeps complex steps intact)
+    xr = xr - Lx * np.round(np.real(xr) / Lx)
+    yr = yr - Ly * np.round(np.real(yr) / Ly)
+    r2 = xr * xr + yr * yr
+    T = 1.0 - (gamma - 1.0) * eps ** 2 / (8.0 * gamma * np.pi ** 2) * np.exp(1.0 - r2)
+    g = eps / (2.0 * np.pi) * np.exp(0.5 * (1.0 - r2))
+    u = u_inf - g * yr
+    v = v_inf + g * xr
+    rho = T ** (1.0 / (gamma - 1.0))
+    p = rho ** gamma
+    return rho, u, v, p
+
+
+def isentropic_vortex(n, ny=None, eps=5.0, gamma=1.4, domain=(0.0, 10.0, 0.0, 10.0),
+                      t=0.0, cfl=0.5, t_end=0.0):
+    """Example 1 on a periodic box (default [0,10]^2 centred at (5,5); the
+    paper's [-5,5]^2 is the same flow shifted)."""
+    ny = n if ny is None else ny
+    x0, x1, y0, y1 = domain
+    xc, dx = centres(n, x0, x1)
+    yc, dy = centres(ny, y0, y1)
+    X, Y = np.meshgrid(xc, yc)
+    centre = (0.5 * (x0 + x1), 0.5 * (y0 + y1))
+    rho, u, v, p = vortex_prims(X, Y, t, eps, gamma, centre, (x1 - x0, y1 - y0))
+    Q = prim_to_cons(rho, u, v, p, gamma)
+    return Case("isentropic_vortex", np.ascontiguousarray(Q), dx, dy, gamma, 0.0, 0.72,
+                (BC_PERIODIC,) * 4, t_end, cfl,
+                {"eps": eps, "domain": domain, "centre": centre})
+
+
+# --------------------------------------------------------------------------
+# Example 9: 2D Riemann problem (Schulz-Rinne), quadrants split at (0.8, 0.8)
+# --------------------------------------------------------------------------
+
+def riemann_2d(n, ny=None, t_end=0.3, cfl=0.5, split=(0.8, 0.8)):
+    ny = n if ny is None else ny
+    xc, dx = centres(n, 0.0, 1.0)
+    yc, dy = centres(ny, 0.0, 1.0)
+    X, Y = np.meshgrid(xc, yc)
+    s11 = 4.0 / np.sqrt(11.0)
+    states = {  # (rho, u, v, p) as printed in Example 9
+        "ur": (1.5, 0.0, 0.0, 1.5),
+        "ul": (33.0 / 62.0, s11, 0.0, 0.3),
+        "ll": (77.0 / 558.0, s11, s11, 9.0 / 310.0),
+        "lr": (33.0 / 62.0, 0.0, s11, 0.3),
+    }
+    right = X > split[0]
+    top = Y > split[1]
+    prim = np.zeros((4, ny, n))
+    for key, mask in (("ur", right & top), ("ul", ~right & top),
+                      ("ll", ~right & ~top), ("lr", right & ~top)):
+        for m in range(4):
+            prim[m][mask] = states[key][m]
+    Q = prim_to_cons(*prim, 1.4)
+    return Case("riemann_2d", np.ascontiguousarray(Q), dx, dy, 1.4, 0.0, 0.72,
+                (BC_TRANSMISSIVE,) * 4, t_end, cfl, {"split": split})
+
+
+# --------------------------------------------------------------------------
+# Example 10: viscous shock tube (Daru-Tenaud), [0,1] x [0,0.5]
+# --------------------------------------------------------------------------
+
+def viscous_shock_tube(nx, ny=None, Re=1000.0, Pr=0.73, gamma=1.4, t_end=1.0, cfl=0.5):
+    ny = nx // 2 if ny is None else ny
+    xc, dx = centres(nx, 0.0, 1.0)
+    yc, dy = centres(ny, 0.0, 0.5)
+    X, _ = np.meshgrid(xc, yc)
+    left = X < 0.5
+    rho = np.where(left, 120.0, 1.2)
+    p = rho / gamma
+    z = np.zeros_like(rho)
+    Q = prim_to_cons(rho, z, z, p, gamma)
+    return Case("viscous_shock_tube", np.ascontiguousarray(Q), dx, dy, gamma, 1.0 / Re, Pr,
+                (BC_NOSLIP_WALL, BC_NOSLIP_WALL, BC_NOSLIP_WALL, BC_SYMMETRY), t_end, cfl)
+
+
+# --------------------------------------------------------------------------
+# Seeded shear layer and exact-solution checks
+# --------------------------------------------------------------------------
+
+def kelvin_helmholtz(n, rng, ny=None, amp=0.01, modes=4, cfl=0.5):
+    """Periodic [0,1]^2 shear layer: rho = 2, u = -0.5 for |y - 1/2| < 1/4,
+    else rho = 1, u = +0.5; p = 2.5; v = sum_m a_m sin(2 pi m x + phi_m),
+    normalised to max |v| = amp. a_m, phi_m come from `rng`."""
+    ny = n if ny is None else ny
+    xc, dx = centres(n, 0.0, 1.0)
+    yc, dy = centres(ny, 0.0, 1.0)
+    X, Y = np.meshgrid(xc, yc)
+    a = rng.uniform(0.2, 1.0, modes)
+    ph = rng.uniform(0.0, 2 * np.pi, modes)
+    xs = np.linspace(0.0, 1.0, 4096, endpoint=False)
+    shape = sum(a[m] * np.sin(2 * np.pi * (m + 1) * xs + ph[m]) for m in range(modes))
+    scale = amp / np.max(np.abs(shape))
+    inner = np.abs(Y - 0.5) < 0.25
+    rho = np.where(inner, 2.0, 1.0)
+    u = np.where(inner, -0.5, 0.5)
+    v = scale * sum(a[m] * np.sin(2 * np.pi * (m + 1) * X + ph[m]) for m in range(modes))
+    p = np.full_like(rho, 2.5)
+    Q = prim_to_cons(rho, u, v, p, 1.4)
+    return Case("kelvin_helmholtz", np.ascontiguousarray(Q), dx, dy, 1.4, 0.0, 0.72,
+                (BC_PERIODIC,) * 4, 0.0, cfl, {"a": a, "phi": ph, "scale": scale})
+
+
+def entropy_wave(n, amp=0.2, L=10.0, gamma=1.4):
+    """rho = 1 + amp sin(2 pi (x + y)/L), u = v = p = 1: translates exactly."""
+    xc, dx = centres(n, 0.0, L)
+    X, Y = np.meshgrid(xc, xc)
+    rho = 1.0 + amp * np.sin(2 * np.pi * (X + Y) / L)
+    one = np.ones_like(rho)
+    Q = prim_to_cons(rho, one, one, one, gamma)
+    return Case("entropy_wave", np.ascontiguousarray(Q), dx, dx, gamma, 0.0, 0.72,
+                (BC_PERIODIC,) * 4)
+
+
+def free_stream(nx, ny, state=(1.3, 0.7, -0.4, 2.1), gamma=1.4, bc=(BC_PERIODIC,) * 4,
+                dx=0.1, dy=0.07):
+    rho, u, v, p = (np.full((ny, nx), s) for s in state)
+    Q = prim_to_cons(rho, u, v, p, gamma)
+    return Case("free_stream", np.ascontiguousarray(Q), dx, dy, gamma, 0.0, 0.72, bc)
+
+
+def shear_wave(n, amp=1e-6, L=1.0, mu=1e-2, gamma=1.4, Pr=0.72, rho0=1.0, p0=1.0):
+    """v = amp sin(2 pi x / L) on a uniform state at rest, periodic: to first
+    order in amp it decays as exp(-(mu/rho0) k^2 t), k = 2 pi / L."""
+    xc, dx = centres(n, 0.0, L)
+    X, _ = np.meshgrid(xc, xc)
+    rho = np.full_like(X, rho0)
+    u = np.zeros_like(X)
+    v = amp * np.sin(2 * np.pi * X / L)
+    p = np.full_like(X, p0)
+    Q = prim_to_cons(rho, u, v, p, gamma)
+    return Case("shear_wave", np.ascontiguousarray(Q), dx, dx, gamma, mu, Pr,
+                (BC_PERIODIC,) * 4, meta={"amp": amp, "k": 2 * np.pi / L})
+
+
+def ensemble(n_cases=64, seed=762, sizes=(256, 512, 1024, 2048)):
+    """Seeded table of independent cases of uneven size: half isentropic
+    vortices with strength U[1,5] on [0,10]^2, half shear layers."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_cases):
+        n = int(rng.choice(sizes))
+        if k % 2 == 0:
+            eps = float(rng.uniform(1.0, 5.0))
+            out.append(("vortex", n, {"eps": eps}))
+        else:
+            out.append(("kh", n, {"seed": int(rng.integers(0, 2**31 - 1))}))
+    return out
+
+
+def make_ensemble_case(kind, n, params):
+    if kind == "vortex":
+        return isentropic_vortex(n, eps=params["eps"])
+    return kelvin_helmholtz(n, np.random.default_rng(params["seed"]))
