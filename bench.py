@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Benchmark of the MEG7-prim TVD-RK3 step on one GB300.
+
+Workload: the 2D Riemann problem of Example 9 (Schulz-Rinne four quadrants,
+split at (0.8, 0.8)) on a 1024 x 1024 grid with transmissive boundaries,
+CFL 0.5, FP64 (the plain method). One step = one TVD-RK3 step = three fused
+residual + stage-update passes, three ghost fills and the CFL wavespeed
+reduction, with dt formed on the device. Metric: cell-updates/s, one
+cell-update = one interior cell through one RK stage. The FP32 form
+(stencil arithmetic in FP32, FP64 stage accumulation) is timed on the same
+workload and reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbr|reference]
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (weak scaling, no collective on the data path); the wall time is the
+max over ranks and the value the total over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s"
+N_DEFAULT = 1024
+CFL = 0.5
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gbr", "reference"], default="gbr")
+    ap.add_argument("--n", type=int, default=N_DEFAULT, help="grid size (cells per side)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# Algorithmic work per cell-update (one interior cell through one RK stage)
+# of the plain smooth-region path; derivation in the design doc.
+FLOP_PER_CELL_UPDATE = None  # filled from paper_2305_00762_gb300.costs
+FP64_PEAK_GFLOPS = 1250.0     # GB300 FP64 (non-tensor) nominal, 152 SMs
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        if not getattr(self, "lines", None):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+        return dist, rank, ws, local
+    return None, 0, 1, 0
+
+
+def barrier(dist, torch):
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def allmax(dist, torch, x):
+    if dist is None:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(case, budget_s=12.0):
+    """The oracle, as it stands, on the host cores: whole RK3 steps of the
+    same workload until about budget_s seconds have passed."""
+    import oracle as O
+    O.build()
+    cfg = O.Config(case.nx, case.ny, case.dx, case.dy, case.gamma, case.mu, case.Pr, case.bc)
+    Q = case.Q.copy()
+    dt = CFL / O.max_wavespeed(cfg, Q)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        Q, rc = O.rk3_step(cfg, Q, dt)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or el / n * (n + 1) > 2.5 * budget_s:
+            break
+    return {"value": 3.0 * case.nx * case.ny * n / el, "unit": METRIC, "cores": O.num_threads(),
+            "kind": "oracle",
+            "sample": f"{n} RK3 step(s) of the {case.nx}x{case.ny} Riemann workload, FP64, {el:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle (plain FP64 C, OpenMP over rows) on the
+    host cores; each step is one RK3 step of a bounded sample of the same
+    workload (a 256 x 256 crop's worth: the 256^2 Riemann problem)."""
+    dist, rank, ws, _ = (None, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0)
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2305_00762_gb300 import cases
+    O.build()
+    n = 256
+    c = cases.riemann_2d(n)
+    cfg = O.Config(c.nx, c.ny, c.dx, c.dy, c.gamma, c.mu, c.Pr, c.bc)
+    Q = c.Q.copy()
+    for _ in range(args.warmup):
+        Q, _ = O.rk3_step(cfg, Q, CFL / O.max_wavespeed(cfg, Q))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Q, _ = O.rk3_step(cfg, Q, CFL / O.max_wavespeed(cfg, Q))
+    el = time.perf_counter() - t0
+    v = 3.0 * n * n * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"riemann_2d_{N_DEFAULT}x{N_DEFAULT}_fp64", "sample": f"{n}x{n}",
+                   "cfl": CFL},
+        "cpu_baseline": {"value": v, "unit": METRIC, "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"{args.steps} RK3 steps of the {n}x{n} Riemann problem"},
+        "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def time_steps(torch, solver, steps, flush):
+    """Device time of `steps` RK3 steps, L2 flushed between steps (outside
+    the events); per-step events on the library's stream."""
+    st = torch.cuda.current_stream()
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        solver.step_cfl(CFL)
+        b.record(st)
+        b.synchronize()
+        total += a.elapsed_time(b)
+    return total
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    dist, rank, ws, local = dist_init()
+    torch.cuda.set_device(local)
+    from paper_2305_00762_gb300 import build, cases, costs, gbr
+    build.build()
+    gbr.load()
+    case = cases.riemann_2d(args.n)
+    st = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+    cells = case.nx * case.ny
+
+    def make(precision):
+        s = gbr.Solver.for_case(case, stream=st.cuda_stream, precision=precision)
+        s.set_state(torch.from_numpy(case.Q).cuda())
+        return s
+
+    results = {}
+    for prec in (64, 32):
+        s = make(prec)
+        for _ in range(args.warmup):
+            s.step_cfl(CFL)
+        s.sync()
+        s.timing(True)
+        barrier(dist, torch)
+        with ClockSampler(local) as clk:
+            ms = time_steps(torch, s, args.steps, flush)
+        barrier(dist, torch)
+        tm, dropped = s.get_timing()
+        s.timing(False)
+        ms = allmax(dist, torch, ms)
+        rc = s.sync(allow=(gbr.GBR_ERR_NONPHYSICAL,))
+        results[prec] = {"ms": ms, "timing": tm, "clocks": clk.summary(), "status": rc}
+        s.close()
+
+    # End to end through the public API with host buffers: every step copies
+    # the state in from pinned host memory and the new state back out.
+    s = make(64)
+    hq = torch.from_numpy(case.Q.copy()).pin_memory()
+    hout = torch.empty_like(hq).pin_memory()
+    for _ in range(args.warmup):
+        gbr.gbr_set_state(s.ctx, hq.numpy(), case.nx, case.ny)
+        s.step_cfl(CFL)
+        gbr.gbr_get_state(s.ctx, hout.numpy(), case.nx, case.ny)
+    barrier(dist, torch)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        gbr.gbr_set_state(s.ctx, hq.numpy(), case.nx, case.ny)
+        s.step_cfl(CFL)
+        gbr.gbr_get_state(s.ctx, hout.numpy(), case.nx, case.ny)
+    barrier(dist, torch)
+    e2e_s = allmax(dist, torch, time.perf_counter() - t0)
+    s.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    r64, r32 = results[64], results[32]
+    upd = 3.0 * cells * args.steps * ws
+    value = upd / (r64["ms"] * 1e-3)
+    stage_ms, stage_n = r64["timing"]["stage"]
+    stage_avg_s = stage_ms / max(stage_n, 1) * 1e-3
+    flop_cell = costs.fp64_flop_per_cell_update()
+    achieved = flop_cell * cells / stage_avg_s / 1e9          # GFLOP/s
+    bytes_cell = costs.hbm_bytes_per_cell_update()
+    hbm = bytes_cell * cells / stage_avg_s / 1e9                  # GB/s
+    pk = peaks()
+    hbm_peak = pk.get("hbm_gbs", 6800.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r64["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"riemann_2d_{args.n}x{args.n}_fp64", "nx": args.n, "ny": args.n,
+                   "cfl": CFL, "bc": "transmissive", "l2": "flushed between steps (256 MB write)",
+                   "replicas": ws},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                     "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                     "kernel": "stage_kernel<double> (fused residual + RK stage)",
+                     "flop_per_cell_update": flop_cell, "stage_ms_avg": stage_avg_s * 1e3,
+                     "hbm_achieved_gbs": hbm, "hbm_peak_gbs": hbm_peak, "hbm_frac": hbm / hbm_peak},
+        "fp32_form": {"value": upd / (r32["ms"] * 1e-3), "ms_per_step": r32["ms"] / args.steps,
+                      "speedup_vs_fp64": r64["ms"] / r32["ms"],
+                      "stage_ms_avg": r32["timing"]["stage"][0] / max(r32["timing"]["stage"][1], 1),
+                      "hbm_frac": bytes_cell * cells / (r32["timing"]["stage"][0] /
+                                                        max(r32["timing"]["stage"][1], 1) * 1e-3) / 1e9 / hbm_peak,
+                      "clocks": r32["clocks"]},
+        "e2e": {"value": 3.0 * cells * args.steps * ws / e2e_s, "unit": METRIC,
+                "h2d_bytes_per_step": 32 * cells, "d2h_bytes_per_step": 32 * cells},
+        "gpu_launches": int(sum(n for _, n in r64["timing"].values())),
+        "clocks": r64["clocks"],
+        "status": gbr.error_string(r64["status"]),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(case)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * gbr.h -- C ABI of the GB300 (sm_103a) library for the seventh-order
+ * gradient-based reconstruction scheme MEG7-prim of Chamarthi, "Efficient
+ * high-order gradient-based reconstruction for compressible flows"
+ * (arXiv:2305.00762): the per-Runge-Kutta-stage residual of the 2D
+ * compressible Navier-Stokes equations on a uniform Cartesian grid.
+ *
+ * Conventions shared by every entry point
+ * --------------------------------------
+ * State layout. A state Q is the conservative vector (rho, rho u, rho v, E)
+ * (Sec. 1, Eq. CNS-base) of the nx * ny interior cells, structure of arrays,
+ * float64: Q[m * ny * nx + i * nx + j] for component m = 0..3, row i (y) and
+ * column j (x), x fastest. Residuals use the same layout. Cell (j, i) has
+ * centre (x0 + (j + 1/2) dx, y0 + (i + 1/2) dy).
+ *
+ * Pointers. Arguments named "on_device" select whether a buffer pointer is a
+ * device pointer (1; it must be usable on the context's device and stream) or
+ * host memory (0; pageable or pinned). The library only reads or writes
+ * caller buffers during the call (host buffers) or in stream order before the
+ * next synchronising call (device buffers); it keeps no caller pointer.
+ *
+ * Ownership. Every device buffer the solver needs (three padded states, the
+ * residual scratch, reduction words) is allocated by gbr_create with
+ * cudaMalloc and freed by gbr_destroy.
+ *
+ * Errors. Every call returns int: GBR_OK (0) or a negative gbr_status. No
+ * call aborts, traps or prints. Errors raised asynchronously on the device
+ * (a non-physical state) are reported by the next synchronising call
+ * (gbr_max_wavespeed, gbr_get_state with a host buffer, gbr_sync). Calls with
+ * a NULL context or out-of-range arguments return GBR_ERR_ARG and change
+ * nothing.
+ *
+ * Streams. All work is issued on the context's stream (the legacy default
+ * stream until gbr_set_stream). Host-buffer transfers synchronise that stream.
+ */
+#ifndef GBR_H
+#define GBR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Ghost layers per side. Sec. 2.3: the LC bound at face j+1/2 uses d_{j-1},
+ * which uses Phi'_{j-2}, which uses Phi_{j-5}; face j-1/2 adds one cell. */
+#define GBR_GHOST 6
+
+typedef enum {
+    GBR_OK = 0,
+    GBR_ERR_ARG = -1,         /* NULL pointer, bad size or value */
+    GBR_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+    GBR_ERR_NONPHYSICAL = -3, /* a stage produced rho <= 0, p <= 0 or a non-finite value */
+    GBR_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+    GBR_ERR_STATE = -5,       /* call out of order (e.g. no state set yet) */
+    GBR_ERR_NOMEM = -6,       /* device allocation failed */
+    GBR_ERR_UNSUPPORTED = -7  /* option or mode not available */
+} gbr_status;
+
+/* Boundary conditions by ghost cells (Sec. 3, "ghost cell approach"; the
+ * kinds used by Examples 1, 9 and 10). Periodic must be paired on opposite
+ * sides. */
+typedef enum {
+    GBR_BC_PERIODIC = 0,     /* wrap around */
+    GBR_BC_TRANSMISSIVE = 1, /* zero gradient: copy of the nearest interior cell */
+    GBR_BC_NOSLIP_WALL = 2,  /* mirror; both velocity components change sign */
+    GBR_BC_SYMMETRY = 3      /* mirror; the normal velocity changes sign */
+} gbr_bc_kind;
+
+/* Boundary kinds per side and the uniform cell sizes (the grid is
+ * [x0, x0 + nx dx] x [y0, y0 + ny dy]; only dx, dy enter the scheme). */
+typedef struct {
+    int west, east, south, north; /* gbr_bc_kind */
+    double dx, dy;                /* > 0 */
+} gbr_bc;
+
+/* Options for gbr_set_option. */
+typedef enum {
+    /* Arithmetic of the stencil, reconstruction and flux work: 64 (default)
+     * or 32. The stage accumulation and the positivity check stay FP64. */
+    GBR_OPT_PRECISION = 0,
+    /* 1: record the detector flag sigma of every face of the next residual
+     * or stage evaluation (read back with gbr_get_flags); 0: off (default). */
+    GBR_OPT_RECORD_FLAGS = 1,
+    /* Discontinuity sensor: 0 = the density detector of Sec. 2.4 (default);
+     * 1 = the learned sensor (requires gbr_set_sensor_weights and
+     * precision 32), with the density detector as fallback. */
+    GBR_OPT_SENSOR = 2,
+    /* 1: bracket every kernel launch with CUDA events on the context's
+     * stream (read back with gbr_get_timing); 0: off (default). */
+    GBR_OPT_TIMING = 3
+} gbr_option;
+
+/* Kernel classes reported by gbr_get_timing. */
+typedef enum {
+    GBR_KERNEL_STAGE = 0, /* fused residual + stage update (or residual only) */
+    GBR_KERNEL_GHOST = 1, /* ghost-cell fill (+ per-step scalars) */
+    GBR_KERNEL_WAVESPEED = 2, /* standalone CFL wavespeed reduction */
+    GBR_KERNEL_CLASSES = 3
+} gbr_kernel_class;
+
+typedef struct gbr_ctx gbr_ctx; /* opaque, library-owned */
+
+/* Create a solver for nx x ny interior cells (nx, ny >= GBR_GHOST) of an
+ * ideal gas with ratio of specific heats gamma > 1 (Eq. pressure), constant
+ * dynamic viscosity mu >= 0 (mu = 0: Euler) and Prandtl number Pr > 0
+ * (Eqs. visc, visc-interface). bc: boundary kinds and cell sizes (read during
+ * the call only). On success *out owns device memory of about
+ * 3 * 32 (nx + 12)(ny + 12) + 32 nx ny bytes on the current CUDA device. */
+int gbr_create(int nx, int ny, double gamma, double mu, double Pr, const gbr_bc *bc, gbr_ctx **out);
+
+/* Free the context and its device memory (after synchronising its stream).
+ * NULL is accepted and ignored. */
+int gbr_destroy(gbr_ctx *ctx);
+
+/* Issue all later work on `stream` (a cudaStream_t, e.g.
+ * torch.cuda.current_stream().cuda_stream; NULL = legacy default stream). */
+int gbr_set_stream(gbr_ctx *ctx, void *stream);
+
+/* Copy the state Q ([4][ny][nx], float64) into the solver (Sec. 1: the
+ * conservative cell-centre point values). The state's CFL wavespeed is
+ * computed on the device right away. */
+int gbr_set_state(gbr_ctx *ctx, const double *Q, int on_device);
+
+/* Copy the current state out ([4][ny][nx], float64). With a host buffer the
+ * call synchronises and reports pending device errors. */
+int gbr_get_state(gbr_ctx *ctx, double *Q, int on_device);
+
+/* Res(Q) of the current state, Eqs. eqn-differencing_residual and deriv:
+ * Res = -(F_{j+1/2} - F_{j-1/2})/dx - (G_{i+1/2} - G_{i-1/2})/dy with the
+ * MEG7 convective flux (Secs. 2.2-2.4) and the alpha-damping viscous flux
+ * (Sec. 2.1). res: [4][ny][nx] float64. */
+int gbr_residual(gbr_ctx *ctx, double *res, int on_device);
+
+/* One third-order TVD Runge-Kutta step of size dt > 0 (Sec. 2.5, Eq. rk):
+ * three fused residual + stage-update passes. Every stage state is checked
+ * for rho > 0, p > 0 and finiteness in FP64; a failure is reported as
+ * GBR_ERR_NONPHYSICAL by the next synchronising call. The new state's CFL
+ * wavespeed is reduced in the last stage. Asynchronous. */
+int gbr_step(gbr_ctx *ctx, double dt);
+
+/* One RK3 step with dt = min(cfl / lambda(Q^n), dt_max) formed on the device
+ * (Sec. 2.5), so that consecutive steps need no host synchronisation; the
+ * simulated time advances by that dt (gbr_get_time). cfl > 0, dt_max > 0. */
+int gbr_step_cfl(gbr_ctx *ctx, double cfl, double dt_max);
+
+/* Simulated time accumulated by gbr_step / gbr_step_cfl since the last
+ * gbr_set_state (synchronises). */
+int gbr_get_time(gbr_ctx *ctx, double *t);
+
+/* lambda = max over cells of max((|u|+c)/dx, (|v|+c)/dy, 4 nu/dx^2,
+ * 4 nu/dy^2), c = sqrt(gamma p / rho), nu = mu / rho (Sec. 2.5: dt =
+ * CFL / lambda). Synchronises; returns pending device errors. */
+int gbr_max_wavespeed(gbr_ctx *ctx, double *lambda);
+
+/* Set an option (gbr_option). Returns GBR_ERR_ARG for an unknown key or a
+ * bad value, GBR_ERR_UNSUPPORTED for a mode that cannot run. */
+int gbr_set_option(gbr_ctx *ctx, int key, double val);
+
+/* Detector flags of the last evaluation made with GBR_OPT_RECORD_FLAGS on
+ * (Eqs. detector and buffer): sigx [ny][nx+1] for the x faces j-1/2 .. nx-1/2
+ * of every row, sigy [ny+1][nx] for the y faces; 1 = smooth (flux
+ * reconstruction), 0 = discontinuity (MEG7 states). During a full step the
+ * flags of the last stage are kept. */
+int gbr_get_flags(gbr_ctx *ctx, unsigned char *sigx, unsigned char *sigy, int on_device);
+
+/* Event timing recorded since the option was set or the last call:
+ * ms[k] = summed device time (milliseconds) and launches[k] = launch count of
+ * kernel class k (arrays of GBR_KERNEL_CLASSES entries, host memory).
+ * Synchronises, then clears the record. At most 65536 launches are kept;
+ * later ones are counted in launches[] but not timed (*dropped > 0). */
+int gbr_get_timing(gbr_ctx *ctx, double *ms, int *launches, int *dropped);
+
+/* Wait for the context's stream and report pending device errors. */
+int gbr_sync(gbr_ctx *ctx);
+
+/* Static text for a gbr_status value. */
+const char *gbr_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBR_H */

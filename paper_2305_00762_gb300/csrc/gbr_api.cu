@@ -1,0 +1,466 @@
+// Host implementation of the C ABI declared in include/gbr.h.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/gbr.h"
+#include "gbr_internal.h"
+
+using namespace gbr;
+
+struct gbr_ctx {
+    Grid g;
+    Physics ph;
+    int bc[4];
+    int device;
+    cudaStream_t stream;
+    double* Qn;   // current state (padded)
+    double* Qa;   // stage buffers (padded)
+    double* Qb;
+    double* R;    // residual scratch [4][ny][nx]
+    DevScalars* ds;
+    unsigned char* sigx;
+    unsigned char* sigy;
+    int precision;
+    int record_flags;
+    int sensor;
+    int have_state;
+    int lam_cur;
+    // launch timing (GBR_OPT_TIMING)
+    int timing;
+    std::vector<cudaEvent_t> ev;   // pairs: start, stop
+    std::vector<int> ev_class;
+    int ev_used;
+    int launches[GBR_KERNEL_CLASSES];
+    int dropped;
+};
+
+namespace {
+
+struct DeviceGuard {  // make the context's device current for one call
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return GBR_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? GBR_ERR_NOMEM : GBR_ERR_CUDA;
+}
+
+#define GBR_TRY(expr)                         \
+    do {                                      \
+        int rc_ = cuda_status(expr);          \
+        if (rc_ != GBR_OK) return rc_;        \
+    } while (0)
+
+bool bc_ok(const gbr_bc* bc)
+{
+    const int k[4] = {bc->west, bc->east, bc->south, bc->north};
+    for (int i = 0; i < 4; ++i)
+        if (k[i] < GBR_BC_PERIODIC || k[i] > GBR_BC_SYMMETRY) return false;
+    if ((bc->west == GBR_BC_PERIODIC) != (bc->east == GBR_BC_PERIODIC)) return false;
+    if ((bc->south == GBR_BC_PERIODIC) != (bc->north == GBR_BC_PERIODIC)) return false;
+    return bc->dx > 0.0 && bc->dy > 0.0;
+}
+
+int copy_state(gbr_ctx* c, double* dst_padded, const double* src, cudaMemcpyKind kind)
+{
+    for (int m = 0; m < 4; ++m) {
+        GBR_TRY(cudaMemcpy2DAsync(dst_padded + m * c->g.plane + (long long)kGhost * c->g.pitch + kGhost,
+                                  sizeof(double) * c->g.pitch, src + (size_t)m * c->g.nx * c->g.ny,
+                                  sizeof(double) * c->g.nx, sizeof(double) * c->g.nx, c->g.ny, kind,
+                                  c->stream));
+    }
+    return GBR_OK;
+}
+
+int read_back_errors(gbr_ctx* c, DevScalars* host)
+{
+    GBR_TRY(cudaMemcpyAsync(host, c->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    GBR_TRY(cudaStreamSynchronize(c->stream));
+    return (host->err & 1u) ? GBR_ERR_NONPHYSICAL : GBR_OK;
+}
+
+constexpr int kMaxTimed = 65536;
+
+// Bracket one launch with events when timing is on.
+struct Timed {
+    gbr_ctx* c;
+    int slot = -1;
+    Timed(gbr_ctx* c_, int cls) : c(c_)
+    {
+        if (!c->timing) return;
+        c->launches[cls]++;
+        if (c->ev_used >= kMaxTimed) {
+            c->dropped++;
+            return;
+        }
+        if ((int)c->ev.size() < 2 * (c->ev_used + 1)) {
+            cudaEvent_t a, b;
+            if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+                cudaGetLastError();
+                c->dropped++;
+                return;
+            }
+            c->ev.push_back(a);
+            c->ev.push_back(b);
+            c->ev_class.push_back(cls);
+        }
+        slot = c->ev_used++;
+        c->ev_class[slot] = cls;
+        cudaEventRecord(c->ev[2 * slot], c->stream);
+    }
+    ~Timed()
+    {
+        if (slot >= 0) cudaEventRecord(c->ev[2 * slot + 1], c->stream);
+    }
+};
+
+int ghosts(gbr_ctx* c, double* q, int mode, double dt, double cfl, double dt_max)
+{
+    Timed tm(c, GBR_KERNEL_GHOST);
+    GhostParams p;
+    p.g = c->g;
+    p.q = q;
+    for (int k = 0; k < 4; ++k) p.bc[k] = c->bc[k];
+    p.ds = c->ds;
+    p.mode = mode;
+    p.cur = c->lam_cur;
+    p.next = 1 - c->lam_cur;
+    p.dt = dt;
+    p.cfl = cfl;
+    p.dt_max = dt_max;
+    return cuda_status(launch_ghosts(p, c->stream));
+}
+
+StageParams stage_params(gbr_ctx* c, const double* q)
+{
+    StageParams p;
+    memset(&p, 0, sizeof(p));
+    p.g = c->g;
+    p.ph = c->ph;
+    p.q = q;
+    p.qn = c->Qn;
+    p.err = &c->ds->err;
+    p.sigx = c->record_flags ? c->sigx : nullptr;
+    p.sigy = c->record_flags ? c->sigy : nullptr;
+    return p;
+}
+
+int stage(gbr_ctx* c, const StageParams& p)
+{
+    Timed tm(c, GBR_KERNEL_STAGE);
+    cudaError_t e = (c->precision == 32) ? launch_stage_f32(p, c->stream) : launch_stage_f64(p, c->stream);
+    return cuda_status(e);
+}
+
+// Eq. rk: Q1 = Qn + dt R(Qn); Q2 = 3/4 Qn + 1/4 Q1 + 1/4 dt R(Q1);
+// Qn+1 = 1/3 Qn + 2/3 Q2 + 2/3 dt R(Q2). dt is a host value (dt_dev null) or
+// the device word formed by the first ghost fill.
+int rk3_step(gbr_ctx* c, int mode, double dt, double cfl, double dt_max)
+{
+    int rc;
+    const double* dt_dev = (mode == 2) ? &c->ds->dt : nullptr;
+    if ((rc = ghosts(c, c->Qn, mode, dt, cfl, dt_max)) != GBR_OK) return rc;
+    StageParams p = stage_params(c, c->Qn);
+    p.qout = c->Qa;
+    p.dt = dt;
+    p.dt_ptr = dt_dev;
+    p.ca = 0.0;
+    p.cb = 1.0;
+    p.cc = 1.0;
+    if ((rc = stage(c, p)) != GBR_OK) return rc;
+    if ((rc = ghosts(c, c->Qa, 0, 0, 0, 0)) != GBR_OK) return rc;
+    p = stage_params(c, c->Qa);
+    p.qout = c->Qb;
+    p.dt = dt;
+    p.dt_ptr = dt_dev;
+    p.ca = 0.75;
+    p.cb = 0.25;
+    p.cc = 0.25;
+    if ((rc = stage(c, p)) != GBR_OK) return rc;
+    if ((rc = ghosts(c, c->Qb, 0, 0, 0, 0)) != GBR_OK) return rc;
+    p = stage_params(c, c->Qb);
+    p.qout = c->Qn;  // each cell reads its own Q^n before writing it
+    p.dt = dt;
+    p.dt_ptr = dt_dev;
+    p.ca = 1.0 / 3.0;
+    p.cb = 2.0 / 3.0;
+    p.cc = 2.0 / 3.0;
+    p.lam_out = &c->ds->lam[1 - c->lam_cur];
+    if ((rc = stage(c, p)) != GBR_OK) return rc;
+    c->lam_cur = 1 - c->lam_cur;
+    return GBR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gbr_create(int nx, int ny, double gamma, double mu, double Pr, const gbr_bc* bc, gbr_ctx** out)
+{
+    if (!out || !bc) return GBR_ERR_ARG;
+    *out = nullptr;
+    if (nx < kGhost || ny < kGhost || !(gamma > 1.0) || !(mu >= 0.0) || !(Pr > 0.0) || !bc_ok(bc))
+        return GBR_ERR_ARG;
+    if ((long long)nx * ny > (1LL << 31)) return GBR_ERR_ARG;
+    gbr_ctx* c = new (std::nothrow) gbr_ctx();  // value-initialised: scalars zero
+    if (!c) return GBR_ERR_NOMEM;
+    c->g.nx = nx;
+    c->g.ny = ny;
+    c->g.pitch = ((nx + 2 * kGhost + 15) / 16) * 16;
+    c->g.plane = (((long long)c->g.pitch * (ny + 2 * kGhost) + 15) / 16) * 16;
+    c->ph.gamma = gamma;
+    c->ph.mu = mu;
+    c->ph.Pr = Pr;
+    c->ph.dx = bc->dx;
+    c->ph.dy = bc->dy;
+    c->bc[0] = bc->west;
+    c->bc[1] = bc->east;
+    c->bc[2] = bc->south;
+    c->bc[3] = bc->north;
+    c->precision = 64;
+    c->stream = 0;
+    int rc = cuda_status(cudaGetDevice(&c->device));
+    const size_t sbytes = sizeof(double) * 4 * (size_t)c->g.plane;
+    if (rc == GBR_OK) rc = cuda_status(cudaMalloc(&c->Qn, sbytes));
+    if (rc == GBR_OK) rc = cuda_status(cudaMalloc(&c->Qa, sbytes));
+    if (rc == GBR_OK) rc = cuda_status(cudaMalloc(&c->Qb, sbytes));
+    if (rc == GBR_OK) rc = cuda_status(cudaMalloc(&c->R, sizeof(double) * 4 * (size_t)nx * ny));
+    if (rc == GBR_OK) rc = cuda_status(cudaMalloc(&c->ds, sizeof(DevScalars)));
+    if (rc == GBR_OK) rc = cuda_status(cudaMemset(c->Qn, 0, sbytes));
+    if (rc == GBR_OK) rc = cuda_status(cudaMemset(c->Qa, 0, sbytes));
+    if (rc == GBR_OK) rc = cuda_status(cudaMemset(c->Qb, 0, sbytes));
+    if (rc == GBR_OK) rc = cuda_status(cudaMemset(c->ds, 0, sizeof(DevScalars)));
+    if (rc != GBR_OK) {
+        gbr_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return GBR_OK;
+}
+
+int gbr_destroy(gbr_ctx* c)
+{
+    if (!c) return GBR_OK;
+    DeviceGuard dg(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(c->Qn);
+    cudaFree(c->Qa);
+    cudaFree(c->Qb);
+    cudaFree(c->R);
+    cudaFree(c->ds);
+    cudaFree(c->sigx);
+    cudaFree(c->sigy);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    cudaGetLastError();
+    delete c;
+    return GBR_OK;
+}
+
+int gbr_set_stream(gbr_ctx* c, void* stream)
+{
+    if (!c) return GBR_ERR_ARG;
+    c->stream = (cudaStream_t)stream;
+    return GBR_OK;
+}
+
+int gbr_set_state(gbr_ctx* c, const double* Q, int on_device)
+{
+    if (!c || !Q) return GBR_ERR_ARG;
+    DeviceGuard dg(c->device);
+    int rc = copy_state(c, c->Qn, Q, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+    if (rc != GBR_OK) return rc;
+    GBR_TRY(cudaMemsetAsync(c->ds, 0, sizeof(DevScalars), c->stream));
+    c->lam_cur = 0;
+    {
+        Timed tm(c, GBR_KERNEL_WAVESPEED);
+        GBR_TRY(launch_wavespeed(c->g, c->ph, c->Qn, &c->ds->lam[0], c->stream));
+    }
+    if (!on_device) GBR_TRY(cudaStreamSynchronize(c->stream));
+    c->have_state = 1;
+    return GBR_OK;
+}
+
+int gbr_get_state(gbr_ctx* c, double* Q, int on_device)
+{
+    if (!c || !Q) return GBR_ERR_ARG;
+    if (!c->have_state) return GBR_ERR_STATE;
+    DeviceGuard dg(c->device);
+    for (int m = 0; m < 4; ++m) {
+        GBR_TRY(cudaMemcpy2DAsync(Q + (size_t)m * c->g.nx * c->g.ny, sizeof(double) * c->g.nx,
+                                  c->Qn + m * c->g.plane + (long long)kGhost * c->g.pitch + kGhost,
+                                  sizeof(double) * c->g.pitch, sizeof(double) * c->g.nx, c->g.ny,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (on_device) return GBR_OK;
+    DevScalars h;
+    return read_back_errors(c, &h);
+}
+
+int gbr_residual(gbr_ctx* c, double* res, int on_device)
+{
+    if (!c || !res) return GBR_ERR_ARG;
+    if (!c->have_state) return GBR_ERR_STATE;
+    DeviceGuard dg(c->device);
+    int rc = ghosts(c, c->Qn, 0, 0, 0, 0);
+    if (rc != GBR_OK) return rc;
+    StageParams p = stage_params(c, c->Qn);
+    p.res = on_device ? res : c->R;
+    if ((rc = stage(c, p)) != GBR_OK) return rc;
+    if (on_device) return GBR_OK;
+    GBR_TRY(cudaMemcpyAsync(res, c->R, sizeof(double) * 4 * (size_t)c->g.nx * c->g.ny, cudaMemcpyDeviceToHost,
+                            c->stream));
+    GBR_TRY(cudaStreamSynchronize(c->stream));
+    return GBR_OK;
+}
+
+int gbr_step(gbr_ctx* c, double dt)
+{
+    if (!c || !(dt > 0.0)) return GBR_ERR_ARG;
+    if (!c->have_state) return GBR_ERR_STATE;
+    DeviceGuard dg(c->device);
+    return rk3_step(c, 1, dt, 0.0, 0.0);
+}
+
+int gbr_step_cfl(gbr_ctx* c, double cfl, double dt_max)
+{
+    if (!c || !(cfl > 0.0) || !(dt_max > 0.0)) return GBR_ERR_ARG;
+    if (!c->have_state) return GBR_ERR_STATE;
+    DeviceGuard dg(c->device);
+    return rk3_step(c, 2, 0.0, cfl, dt_max);
+}
+
+int gbr_get_time(gbr_ctx* c, double* t)
+{
+    if (!c || !t) return GBR_ERR_ARG;
+    DeviceGuard dg(c->device);
+    DevScalars h;
+    int rc = read_back_errors(c, &h);
+    *t = h.t;
+    return rc;
+}
+
+int gbr_max_wavespeed(gbr_ctx* c, double* lambda)
+{
+    if (!c || !lambda) return GBR_ERR_ARG;
+    if (!c->have_state) return GBR_ERR_STATE;
+    DeviceGuard dg(c->device);
+    DevScalars h;
+    int rc = read_back_errors(c, &h);
+    if (rc == GBR_ERR_CUDA || rc == GBR_ERR_NOMEM) return rc;
+    unsigned long long bits = h.lam[c->lam_cur];
+    double v;
+    memcpy(&v, &bits, sizeof(v));
+    *lambda = v;
+    return rc;
+}
+
+int gbr_set_option(gbr_ctx* c, int key, double val)
+{
+    if (!c) return GBR_ERR_ARG;
+    DeviceGuard dg(c->device);
+    switch (key) {
+    case GBR_OPT_PRECISION:
+        if (val != 64.0 && val != 32.0) return GBR_ERR_ARG;
+        c->precision = (int)val;
+        return GBR_OK;
+    case GBR_OPT_RECORD_FLAGS:
+        if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;
+        if (val == 1.0 && !c->sigx) {
+            GBR_TRY(cudaMalloc(&c->sigx, (size_t)c->g.ny * (c->g.nx + 1)));
+            GBR_TRY(cudaMalloc(&c->sigy, (size_t)(c->g.ny + 1) * c->g.nx));
+            GBR_TRY(cudaMemset(c->sigx, 0, (size_t)c->g.ny * (c->g.nx + 1)));
+            GBR_TRY(cudaMemset(c->sigy, 0, (size_t)(c->g.ny + 1) * c->g.nx));
+        }
+        c->record_flags = (int)val;
+        return GBR_OK;
+    case GBR_OPT_SENSOR:
+        if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;
+        if (val == 1.0) return GBR_ERR_UNSUPPORTED;
+        c->sensor = 0;
+        return GBR_OK;
+    case GBR_OPT_TIMING:
+        if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;
+        c->timing = (int)val;
+        c->ev_used = 0;
+        c->dropped = 0;
+        for (int k = 0; k < GBR_KERNEL_CLASSES; ++k) c->launches[k] = 0;
+        return GBR_OK;
+    default:
+        return GBR_ERR_ARG;
+    }
+}
+
+int gbr_get_timing(gbr_ctx* c, double* ms, int* launches, int* dropped)
+{
+    if (!c || !ms || !launches) return GBR_ERR_ARG;
+    DeviceGuard dg(c->device);
+    GBR_TRY(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < GBR_KERNEL_CLASSES; ++k) {
+        ms[k] = 0.0;
+        launches[k] = c->launches[k];
+        c->launches[k] = 0;
+    }
+    for (int s = 0; s < c->ev_used; ++s) {
+        float t = 0.f;
+        GBR_TRY(cudaEventElapsedTime(&t, c->ev[2 * s], c->ev[2 * s + 1]));
+        ms[c->ev_class[s]] += t;
+    }
+    if (dropped) *dropped = c->dropped;
+    c->ev_used = 0;
+    c->dropped = 0;
+    return GBR_OK;
+}
+
+int gbr_get_flags(gbr_ctx* c, unsigned char* sigx, unsigned char* sigy, int on_device)
+{
+    if (!c || !sigx || !sigy) return GBR_ERR_ARG;
+    if (!c->sigx) return GBR_ERR_STATE;
+    DeviceGuard dg(c->device);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    GBR_TRY(cudaMemcpyAsync(sigx, c->sigx, (size_t)c->g.ny * (c->g.nx + 1), k, c->stream));
+    GBR_TRY(cudaMemcpyAsync(sigy, c->sigy, (size_t)(c->g.ny + 1) * c->g.nx, k, c->stream));
+    if (!on_device) GBR_TRY(cudaStreamSynchronize(c->stream));
+    return GBR_OK;
+}
+
+int gbr_sync(gbr_ctx* c)
+{
+    if (!c) return GBR_ERR_ARG;
+    DeviceGuard dg(c->device);
+    DevScalars h;
+    return read_back_errors(c, &h);
+}
+
+const char* gbr_error_string(int status)
+{
+    switch (status) {
+    case GBR_OK: return "ok";
+    case GBR_ERR_ARG: return "invalid argument";
+    case GBR_ERR_CUDA: return "CUDA runtime error";
+    case GBR_ERR_NONPHYSICAL: return "non-physical state (rho <= 0, p <= 0 or non-finite)";
+    case GBR_ERR_TIMEOUT: return "bounded device wait timed out";
+    case GBR_ERR_STATE: return "call out of order (no state set)";
+    case GBR_ERR_NOMEM: return "device allocation failed";
+    case GBR_ERR_UNSUPPORTED: return "unsupported option or mode";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,69 @@
+// Internal declarations shared by the host C-ABI (gbr_api.cu) and the kernel
+// translation units. Not part of the public interface (include/gbr.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gbr {
+
+constexpr int kGhost = 6;  // ghost layers per side (Sec. 2.3, LC bound reach)
+
+// Device-resident scalars of one solver context.
+struct DevScalars {
+    unsigned long long lam[2];  // CFL wavespeed of a state, bits of a double >= 0
+    double dt;                  // step size used by the current step
+    double t;                   // simulated time since the last set_state
+    unsigned int err;           // bit 0: non-physical stage state
+    unsigned int pad;
+};
+
+// Padded state geometry: plane m of a state starts at base + m * plane; the
+// interior cell (j, i) sits at (i + 6) * pitch + (j + 6).
+struct Grid {
+    int nx, ny;
+    int pitch;        // elements per padded row (>= nx + 12)
+    long long plane;  // elements per component plane
+};
+
+struct Physics {
+    double gamma, mu, Pr, dx, dy;
+};
+
+// One fused residual (+ stage update) pass, Secs. 2.1-2.5.
+struct StageParams {
+    Grid g;
+    Physics ph;
+    const double* q;         // stage input state (padded, ghosts filled)
+    const double* qn;        // Q^n (padded) for the RK combination (may equal qout)
+    double* qout;            // output state (padded) or nullptr (residual only)
+    double* res;             // dense residual [4][ny][nx] or nullptr
+    unsigned char* sigx;     // optional x-face flags [ny][nx+1]
+    unsigned char* sigy;     // optional y-face flags [ny+1][nx]
+    unsigned long long* lam_out;  // optional wavespeed of qout (atomic max)
+    unsigned int* err;       // error word
+    const double* dt_ptr;    // device dt (used when non-null)
+    double dt;               // host dt otherwise
+    double ca, cb, cc;       // qout = ca * qn + cb * q + cc * dt * Res
+};
+
+// Ghost fill of one padded state, plus the per-step scalar bookkeeping done
+// by its first thread (mode 1: add dt to t and clear lam[next]; mode 2: form
+// dt = min(cfl / lam[cur], dt_max) on the device first).
+struct GhostParams {
+    Grid g;
+    double* q;
+    int bc[4];  // west, east, south, north
+    DevScalars* ds;
+    int mode;
+    int cur, next;
+    double dt, cfl, dt_max;
+};
+
+cudaError_t launch_ghosts(const GhostParams& p, cudaStream_t s);
+cudaError_t launch_wavespeed(const Grid& g, const Physics& ph, const double* q,
+                             unsigned long long* lam, cudaStream_t s);
+cudaError_t launch_stage_f64(const StageParams& p, cudaStream_t s);
+cudaError_t launch_stage_f32(const StageParams& p, cudaStream_t s);
+
+}  // namespace gbr

@@ -1,0 +1,13 @@
+// FP32 instantiation of the fused stage kernel: stencil, reconstruction and
+// flux arithmetic in float; state, stage combination and positivity in FP64.
+#include "stage_kernel.cuh"
+
+namespace gbr {
+
+cudaError_t launch_stage_f32(const StageParams& p, cudaStream_t s)
+{
+    if (p.ph.mu > 0.0) return launch_stage_t<float, 32, 16, 256, true>(p, s);
+    return launch_stage_t<float, 32, 16, 256, false>(p, s);
+}
+
+}  // namespace gbr

@@ -1,0 +1,12 @@
+// FP64 instantiation of the fused stage kernel (the plain method).
+#include "stage_kernel.cuh"
+
+namespace gbr {
+
+cudaError_t launch_stage_f64(const StageParams& p, cudaStream_t s)
+{
+    if (p.ph.mu > 0.0) return launch_stage_t<double, 32, 8, 256, true>(p, s);
+    return launch_stage_t<double, 32, 8, 256, false>(p, s);
+}
+
+}  // namespace gbr

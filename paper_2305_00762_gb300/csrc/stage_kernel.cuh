@@ -1,0 +1,558 @@
+// Fused MEG7-prim residual + TVD-RK3 stage update for sm_103a.
+//
+// One CTA owns a BX x BY tile of interior cells. It stages the tile plus a
+// 6-cell halo of the conservative state in shared memory as primitive
+// variables, computes every per-cell quantity once (sixth-order gradients in
+// x and y, detector flags, cell fluxes), evaluates every x and y face of the
+// tile once (characteristic MEG7 states, flux reconstruction, HLLC, viscous
+// flux), differences the face fluxes into the residual and applies the stage
+// update in FP64. References are to arXiv:2305.00762.
+//
+// T is the arithmetic type of the stencil, reconstruction and flux work
+// (double, or float for the FP32 form); the state, the stage combination and
+// the positivity check are always FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbr_internal.h"
+
+namespace gbr {
+
+template <int BX, int BY, bool VISC>
+struct TileLayout {
+    static constexpr int V = VISC ? 1 : 0;
+    static constexpr int RW = BX + 12, RH = BY + 12;  // staged region (tile + halo)
+    static constexpr int NU = RW * RH;
+    // x-gradients: rows [6-V, 6+BY+V), region columns [3, BX+9)
+    static constexpr int GXW = BX + 6, GXH = BY + 2 * V, NGX = GXW * GXH;
+    // y-gradients: region rows [3, BY+9), columns [6-V, 6+BX+V)
+    static constexpr int GYW = BX + 2 * V, GYH = BY + 6, NGY = GYW * GYH;
+    // detector flags: x at interior rows, columns [3, BX+9); y at rows [3, BY+9)
+    static constexpr int PXW = BX + 6, NPX = PXW * BY;
+    static constexpr int PYH = BY + 6, NPY = PYH * BX;
+    // cell fluxes: x at interior rows, columns [1, BX+11); y at rows [1, BY+11)
+    static constexpr int FXW = BX + 10, NFX = FXW * BY;
+    static constexpr int FYH = BY + 10, NFY = FYH * BX;
+    // face fluxes
+    static constexpr int HXW = BX + 1, NHX = HXW * BY;
+    static constexpr int HYH = BY + 1, NHY = HYH * BX;
+
+    static constexpr int oU = 0;
+    static constexpr int oGX = oU + 4 * NU;
+    static constexpr int oGY = oGX + 4 * NGX;
+    static constexpr int oFX = oGY + 4 * NGY;
+    static constexpr int oFY = oFX + 4 * NFX;
+    static constexpr int oHX = oFY + 4 * NFY;
+    static constexpr int oHY = oHX + 4 * NHX;
+    static constexpr int nT = oHY + 4 * NHY;  // elements of T
+
+    template <typename T>
+    static constexpr size_t bytes() { return sizeof(T) * (size_t)nT + (size_t)(NPX + NPY) + 16; }
+};
+
+template <typename T>
+__device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
+template <typename T>
+__device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double tabs(double x) { return fabs(x); }
+__device__ __forceinline__ float tabs(float x) { return fabsf(x); }
+
+// Eq. alpha: minmod(a, b) = 1/2 (sign a + sign b) min(|a|, |b|).
+template <typename T>
+__device__ __forceinline__ T minmod(T a, T b)
+{
+    return (a > T(0) && b > T(0)) ? tmin(a, b) : ((a < T(0) && b < T(0)) ? tmax(a, b) : T(0));
+}
+
+// Eq. six: dx-scaled sixth-order gradient at s[0] along stride st.
+template <typename T>
+__device__ __forceinline__ T grad6(const T* s, int st)
+{
+    return (T(45) * (s[st] - s[-st]) - T(9) * (s[2 * st] - s[-2 * st]) + (s[3 * st] - s[-3 * st])) *
+           T(1.0 / 60.0);
+}
+
+// Eq. detector with eps = 0.9 psi_c xi^2 / (1 - 0.9 psi_c), xi = 1e-3: returns
+// true when psi_j < psi_c = 0.5. psi = (2ab + eps)/(a^2 + b^2 + eps) and the
+// denominator is positive, so psi < 1/2 <=> 2 (2ab + eps) < a^2 + b^2 + eps.
+template <typename T>
+__device__ __forceinline__ bool trouble_cell(const T* r, int st)
+{
+    const T eps = T(0.9 * 0.5 / (1.0 - 0.9 * 0.5) * 1e-6);
+    T a = tabs(r[0] - r[-st]) + tabs(r[0] - T(2) * r[-st] + r[-2 * st]);
+    T b = tabs(r[0] - r[st]) + tabs(r[0] - T(2) * r[st] + r[2 * st]);
+    return T(2) * (T(2) * a * b + eps) < a * a + b * b + eps;
+}
+
+// Eqs. grb, mp5Condition, alpha, mp-procedure: MEG7 left value at j+1/2 from
+// Phi_{j-2..j+2} (p0..p4) and Phi'_{j-2..j+2} (d0..d4), xi = 7.
+template <typename T>
+__device__ __forceinline__ T meg7(T p0, T p1, T p2, T p3, T p4, T d0, T d1, T d2, T d3, T d4)
+{
+    const T pl = (T(420) * d2 + T(60) * (d1 - d3) + T(478) * p2 + T(178) * (p1 + p3) + T(3) * (p0 + p4)) *
+                 T(1.0 / 840.0);
+    const T pmp = p2 + minmod(p3 - p2, T(7) * (p2 - p1));
+    if ((pl - p2) * (pl - pmp) <= T(1e-40)) return pl;
+    const T dm1 = T(2) * (p2 - T(2) * p1 + p0) - T(0.5) * (d2 - d0);
+    const T dj = T(2) * (p3 - T(2) * p2 + p1) - T(0.5) * (d3 - d1);
+    const T dp1 = T(2) * (p4 - T(2) * p3 + p2) - T(0.5) * (d4 - d2);
+    const T md = T(0.5) * (p2 + p3) - T(0.5) * minmod(dj, dp1);
+    const T ul = p2 + T(7) * (p2 - p1);
+    const T lc = T(0.5) * (T(3) * p2 - p1) + T(4.0 / 3.0) * minmod(dj, dm1);
+    const T pmin = tmax(tmin(p2, tmin(p3, md)), tmin(p2, tmin(ul, lc)));
+    const T pmax = tmin(tmax(p2, tmax(p3, md)), tmax(p2, tmax(ul, lc)));
+    return pl + minmod(pmin - pl, pmax - pl);
+}
+
+// Eq. flux-full (left) and Eq. flux-right at the face after cell f[0].
+template <typename T>
+__device__ __forceinline__ T recon_left(const T* f, int s)
+{
+    return (T(568) * f[0] - T(146) * f[-s] + T(22) * f[-2 * s] + T(2) * f[-3 * s] - f[-4 * s] + T(484) * f[s] -
+            T(104) * f[2 * s] + T(16) * f[3 * s] - f[4 * s]) *
+           T(1.0 / 840.0);
+}
+template <typename T>
+__device__ __forceinline__ T recon_right(const T* f, int s)
+{
+    return (-f[5 * s] + T(2) * f[4 * s] + T(22) * f[3 * s] - T(146) * f[2 * s] + T(568) * f[s] + T(484) * f[0] -
+            T(104) * f[-s] + T(16) * f[-2 * s] - f[-3 * s]) *
+           T(1.0 / 840.0);
+}
+
+template <typename T>
+struct FaceIn {
+    const T* u[4];  // primitive planes in face-normal order (rho, un, ut, p) at cell j
+    int su;
+    const T* g[4];  // dx-scaled normal gradients, same order, at cell j
+    int sg;
+    const unsigned char* tr;  // detector trouble flags at cell j
+    int st;
+    const T* f[4];  // cell convective fluxes in face-normal order at cell j
+    int sf;
+    const T* tun;  // tangential derivative (dx-scaled) of un at cell j
+    const T* tut;  // ... of ut
+    int stq;       // step from cell j to cell j+1 in the tangential arrays
+};
+
+template <typename T>
+struct PhysT {
+    T gamma, gm1, igm1, mu, kq;  // kq = mu / (Pr (gamma - 1))
+};
+
+// The whole interface procedure of Secs. 2.1-2.4 at face j+1/2. Returns the
+// total flux in face-normal order and the detector flag sigma.
+template <typename T, bool VISC>
+__device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P, T inv_dn, T inv_dt, T out[4],
+                                          bool& smooth)
+{
+    // Eq. buffer: sigma = 0 if psi_k < psi_c for any k in j-2..j+3.
+    bool tr = false;
+#pragma unroll
+    for (int k = -2; k <= 3; ++k) tr |= (in.tr[k * in.st] != 0);
+    smooth = !tr;
+
+    const int su = in.su, sg = in.sg;
+    // Characteristic projection at the arithmetic-mean state.
+    const T rb = T(0.5) * (in.u[0][0] + in.u[0][su]);
+    const T pb = T(0.5) * (in.u[3][0] + in.u[3][su]);
+    const T cb = tsqrt(P.gamma * pb / rb);
+    const T icb = T(1) / cb;
+    const T al = T(0.5) * rb * icb;  // rho / (2 c)
+    const T ic2 = icb * icb;         // 1 / c^2
+    const T be = T(0.5) * ic2;       // 1 / (2 c^2)
+
+    T wL[4], wR[4];
+    {  // fields 1 and 4 (u - c and u + c) share un and p
+        T w0[6], w3[6], e0[6], e3[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int o = (k - 2);
+            const T tu = al * in.u[1][o * su], tp = be * in.u[3][o * su];
+            w0[k] = tp - tu;
+            w3[k] = tp + tu;
+            const T gu = al * in.g[1][o * sg], gp = be * in.g[3][o * sg];
+            e0[k] = gp - gu;
+            e3[k] = gp + gu;
+        }
+        wL[0] = meg7(w0[0], w0[1], w0[2], w0[3], w0[4], e0[0], e0[1], e0[2], e0[3], e0[4]);
+        wR[0] = meg7(w0[5], w0[4], w0[3], w0[2], w0[1], -e0[5], -e0[4], -e0[3], -e0[2], -e0[1]);
+        wL[3] = meg7(w3[0], w3[1], w3[2], w3[3], w3[4], e3[0], e3[1], e3[2], e3[3], e3[4]);
+        wR[3] = meg7(w3[5], w3[4], w3[3], w3[2], w3[1], -e3[5], -e3[4], -e3[3], -e3[2], -e3[1]);
+    }
+    {  // field 2 (entropy): rho - p / c^2
+        T w[6], e[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int o = (k - 2);
+            w[k] = in.u[0][o * su] - ic2 * in.u[3][o * su];
+            e[k] = in.g[0][o * sg] - ic2 * in.g[3][o * sg];
+        }
+        wL[1] = meg7(w[0], w[1], w[2], w[3], w[4], e[0], e[1], e[2], e[3], e[4]);
+        wR[1] = meg7(w[5], w[4], w[3], w[2], w[1], -e[5], -e[4], -e[3], -e[2], -e[1]);
+    }
+    {  // field 3 (shear): ut
+        T w[6], e[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int o = (k - 2);
+            w[k] = in.u[2][o * su];
+            e[k] = in.g[2][o * sg];
+        }
+        wL[2] = meg7(w[0], w[1], w[2], w[3], w[4], e[0], e[1], e[2], e[3], e[4]);
+        wR[2] = meg7(w[5], w[4], w[3], w[2], w[1], -e[5], -e[4], -e[3], -e[2], -e[1]);
+    }
+    // Back to primitive variables with the right eigenvectors.
+    const T crb = cb / rb, c2 = cb * cb;
+    const T rL = wL[0] + wL[1] + wL[3], unL = crb * (wL[3] - wL[0]), utL = wL[2], pL = c2 * (wL[0] + wL[3]);
+    const T rR = wR[0] + wR[1] + wR[3], unR = crb * (wR[3] - wR[0]), utR = wR[2], pR = c2 * (wR[0] + wR[3]);
+    const T EL = pL * P.igm1 + T(0.5) * rL * (unL * unL + utL * utL);
+    const T ER = pR * P.igm1 + T(0.5) * rR * (unR * unR + utR * utR);
+    const T QL[4] = {rL, rL * unL, rL * utL, EL};
+    const T QR[4] = {rR, rR * unR, rR * utR, ER};
+
+    // Hybrid face fluxes (Sec. 2.4): sigma F(f) + (1 - sigma) F(Q).
+    T FL[4], FR[4];
+    if (smooth) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            FL[m] = recon_left(in.f[m], in.sf);
+            FR[m] = recon_right(in.f[m], in.sf);
+        }
+    } else {
+        FL[0] = QL[1];
+        FL[1] = QL[1] * unL + pL;
+        FL[2] = QL[1] * utL;
+        FL[3] = unL * (EL + pL);
+        FR[0] = QR[1];
+        FR[1] = QR[1] * unR + pR;
+        FR[2] = QR[1] * utR;
+        FR[3] = unR * (ER + pR);
+    }
+
+    // HLLC in the form 1/2 (F_L + F_R) - 1/2 |A| (Q_R - Q_L), Eq. Riemann_revisit.
+    {
+        const T irL = T(1) / rL, irR = T(1) / rR;
+        const T cL = tsqrt(P.gamma * pL * irL), cR = tsqrt(P.gamma * pR * irR);
+        const T HL = (EL + pL) * irL, HR = (ER + pR) * irR;
+        const T sL = tsqrt(rL), sR = tsqrt(rR), isum = T(1) / (sL + sR);
+        const T ut = (sL * unL + sR * unR) * isum;
+        const T vt = (sL * utL + sR * utR) * isum;
+        const T Ht = (sL * HL + sR * HR) * isum;
+        const T ct = tsqrt(P.gm1 * (Ht - T(0.5) * (ut * ut + vt * vt)));
+        const T SL = tmin(unL - cL, ut - ct);
+        const T SR = tmax(unR + cR, ut + ct);
+        const T mL = rL * (SL - unL), mR = rR * (SR - unR);
+        const T Ss = (pR - pL + mL * unL - mR * unR) / (mL - mR);
+        const T kL = mL / (SL - Ss), kR = mR / (SR - Ss);
+        const T QsL[4] = {kL, kL * Ss, kL * utL, kL * (EL * irL + (Ss - unL) * (Ss + pL / mL))};
+        const T QsR[4] = {kR, kR * Ss, kR * utR, kR * (ER * irR + (Ss - unR) * (Ss + pR / mR))};
+        const T aL = tabs(SL), aS = tabs(Ss), aR = tabs(SR);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const T adq = aL * (QsL[m] - QL[m]) + aS * (QsR[m] - QsL[m]) + aR * (QR[m] - QsR[m]);
+            out[m] = T(0.5) * (FL[m] + FR[m]) - T(0.5) * adq;
+        }
+    }
+
+    if constexpr (VISC) {
+        // Sec. 2.1: alpha-damping (Eq. alphad, alpha_v = 4) on the shared
+        // gradients; T = gamma p / rho with T' by the chain rule.
+        const T r0 = in.u[0][0], r1 = in.u[0][su];
+        const T n0 = in.u[1][0], n1 = in.u[1][su];
+        const T t0 = in.u[2][0], t1 = in.u[2][su];
+        const T p0 = in.u[3][0], p1 = in.u[3][su];
+        const T dr0 = in.g[0][0], dr1 = in.g[0][sg];
+        const T dn0 = in.g[1][0], dn1 = in.g[1][sg];
+        const T dt0 = in.g[2][0], dt1 = in.g[2][sg];
+        const T dp0 = in.g[3][0], dp1 = in.g[3][sg];
+        const T ir0 = T(1) / r0, ir1 = T(1) / r1;
+        const T T0 = P.gamma * p0 * ir0, T1 = P.gamma * p1 * ir1;
+        const T dT0 = P.gamma * (dp0 * ir0 - p0 * dr0 * ir0 * ir0);
+        const T dT1 = P.gamma * (dp1 * ir1 - p1 * dr1 * ir1 * ir1);
+        const T un_n = (T(0.5) * (dn0 + dn1) + T(2) * (n1 - T(0.5) * dn1 - n0 - T(0.5) * dn0)) * inv_dn;
+        const T ut_n = (T(0.5) * (dt0 + dt1) + T(2) * (t1 - T(0.5) * dt1 - t0 - T(0.5) * dt0)) * inv_dn;
+        const T T_n = (T(0.5) * (dT0 + dT1) + T(2) * (T1 - T(0.5) * dT1 - T0 - T(0.5) * dT0)) * inv_dn;
+        const T un_t = T(0.5) * (in.tun[0] + in.tun[in.stq]) * inv_dt;
+        const T ut_t = T(0.5) * (in.tut[0] + in.tut[in.stq]) * inv_dt;
+        const T unf = T(0.5) * (n0 + n1), utf = T(0.5) * (t0 + t1);
+        const T tau_nn = T(2.0 / 3.0) * P.mu * (T(2) * un_n - ut_t);
+        const T tau_nt = P.mu * (un_t + ut_n);
+        const T q_n = -P.kq * T_n;
+        out[1] -= tau_nn;
+        out[2] -= tau_nt;
+        out[3] += -(tau_nn * unf + tau_nt * utf) + q_n;
+    }
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <typename T, int BX, int BY, int NT, bool VISC>
+__global__ void __launch_bounds__(NT) stage_kernel(const StageParams P)
+{
+    using L = TileLayout<BX, BY, VISC>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* const sm = reinterpret_cast<T*>(smem_raw);
+    T* const sU = sm + L::oU;
+    T* const sGX = sm + L::oGX;
+    T* const sGY = sm + L::oGY;
+    T* const sFX = sm + L::oFX;
+    T* const sFY = sm + L::oFY;
+    T* const sHX = sm + L::oHX;
+    T* const sHY = sm + L::oHY;
+    unsigned char* const sPX = reinterpret_cast<unsigned char*>(sm + L::nT);
+    unsigned char* const sPY = sPX + L::NPX;
+    constexpr int RW = L::RW, NU = L::NU, V = L::V;
+
+    const int nx = P.g.nx, ny = P.g.ny, pitch = P.g.pitch;
+    const long long plane = P.g.plane;
+    const int tx0 = blockIdx.x * BX, ty0 = blockIdx.y * BY;
+    const int tid = threadIdx.x;
+
+    PhysT<T> ph;
+    ph.gamma = T(P.ph.gamma);
+    ph.gm1 = T(P.ph.gamma - 1.0);
+    ph.igm1 = T(1.0 / (P.ph.gamma - 1.0));
+    ph.mu = T(P.ph.mu);
+    ph.kq = T(P.ph.mu / (P.ph.Pr * (P.ph.gamma - 1.0)));
+    const T inv_dx = T(1.0 / P.ph.dx), inv_dy = T(1.0 / P.ph.dy);
+
+    // Phase 0: stage the tile + halo as primitive variables (Eq. pressure).
+    // Region cell (rx, ry) is padded cell (tx0 + rx, ty0 + ry); beyond the
+    // padded extent (ragged last tiles) the load is clamped to a valid cell
+    // whose results are never stored.
+    for (int idx = tid; idx < NU; idx += NT) {
+        const int ry = idx / RW, rx = idx - ry * RW;
+        const int gx = min(tx0 + rx, nx + 2 * kGhost - 1);
+        const int gy = min(ty0 + ry, ny + 2 * kGhost - 1);
+        const long long o = (long long)gy * pitch + gx;
+        const T r = T(P.q[o]);
+        const T ir = T(1) / r;
+        const T u = T(P.q[o + plane]) * ir;
+        const T v = T(P.q[o + 2 * plane]) * ir;
+        const T p = ph.gm1 * (T(P.q[o + 3 * plane]) - T(0.5) * r * (u * u + v * v));
+        sU[idx] = r;
+        sU[NU + idx] = u;
+        sU[2 * NU + idx] = v;
+        sU[3 * NU + idx] = p;
+    }
+    __syncthreads();
+
+    // Phase 1: per-cell quantities, each computed once per tile.
+    for (int idx = tid; idx < L::NGX; idx += NT) {  // x-gradients (Eq. six)
+        const int a = idx / L::GXW, b = idx - a * L::GXW;
+        const T* s = sU + (a + 6 - V) * RW + (b + 3);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) sGX[m * L::NGX + idx] = grad6(s + m * NU, 1);
+    }
+    for (int idx = tid; idx < L::NGY; idx += NT) {  // y-gradients
+        const int a = idx / L::GYW, b = idx - a * L::GYW;
+        const T* s = sU + (a + 3) * RW + (b + 6 - V);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) sGY[m * L::NGY + idx] = grad6(s + m * NU, RW);
+    }
+    for (int idx = tid; idx < L::NPX; idx += NT) {  // x detector (Eq. detector)
+        const int a = idx / L::PXW, b = idx - a * L::PXW;
+        sPX[idx] = trouble_cell(sU + (a + 6) * RW + (b + 3), 1) ? 1 : 0;
+    }
+    for (int idx = tid; idx < L::NPY; idx += NT) {  // y detector
+        const int a = idx / BX, b = idx - a * BX;
+        sPY[idx] = trouble_cell(sU + (a + 3) * RW + (b + 6), RW) ? 1 : 0;
+    }
+    for (int idx = tid; idx < L::NFX; idx += NT) {  // cell x-fluxes F^c (Sec. 1)
+        const int a = idx / L::FXW, b = idx - a * L::FXW;
+        const int c = (a + 6) * RW + (b + 1);
+        const T r = sU[c], u = sU[NU + c], v = sU[2 * NU + c], p = sU[3 * NU + c];
+        const T E = p * ph.igm1 + T(0.5) * r * (u * u + v * v);
+        const T ru = r * u;
+        sFX[idx] = ru;
+        sFX[L::NFX + idx] = ru * u + p;
+        sFX[2 * L::NFX + idx] = ru * v;
+        sFX[3 * L::NFX + idx] = u * (E + p);
+    }
+    for (int idx = tid; idx < L::NFY; idx += NT) {  // cell y-fluxes G^c
+        const int a = idx / BX, b = idx - a * BX;
+        const int c = (a + 1) * RW + (b + 6);
+        const T r = sU[c], u = sU[NU + c], v = sU[2 * NU + c], p = sU[3 * NU + c];
+        const T E = p * ph.igm1 + T(0.5) * r * (u * u + v * v);
+        const T rv = r * v;
+        sFY[idx] = rv;
+        sFY[L::NFY + idx] = rv * u;
+        sFY[2 * L::NFY + idx] = rv * v + p;
+        sFY[3 * L::NFY + idx] = v * (E + p);
+    }
+    __syncthreads();
+
+    // Phase 2: every x face and y face of the tile, once.
+    for (int w = tid; w < L::NHX + L::NHY; w += NT) {
+        T out[4];
+        bool smooth;
+        if (w < L::NHX) {
+            const int r = w / L::HXW, f = w - r * L::HXW;
+            const int ry = r + 6, rx = f + 5;  // left cell of the face
+            FaceIn<T> in;
+            const T* u = sU + ry * RW + rx;
+            in.u[0] = u;
+            in.u[1] = u + NU;
+            in.u[2] = u + 2 * NU;
+            in.u[3] = u + 3 * NU;
+            in.su = 1;
+            const T* gx = sGX + (r + V) * L::GXW + (rx - 3);
+            in.g[0] = gx;
+            in.g[1] = gx + L::NGX;
+            in.g[2] = gx + 2 * L::NGX;
+            in.g[3] = gx + 3 * L::NGX;
+            in.sg = 1;
+            in.tr = sPX + r * L::PXW + (rx - 3);
+            in.st = 1;
+            const T* fx = sFX + r * L::FXW + (rx - 1);
+            in.f[0] = fx;
+            in.f[1] = fx + L::NFX;
+            in.f[2] = fx + 2 * L::NFX;
+            in.f[3] = fx + 3 * L::NFX;
+            in.sf = 1;
+            const T* ty = sGY + (ry - 3) * L::GYW + (rx - 6 + V);
+            in.tun = ty + L::NGY;      // d u / d y
+            in.tut = ty + 2 * L::NGY;  // d v / d y
+            in.stq = 1;
+            face_flux<T, VISC>(in, ph, inv_dx, inv_dy, out, smooth);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) sHX[m * L::NHX + w] = out[m];
+            if (P.sigx) {
+                const int i = ty0 + r, jf = tx0 + f;
+                if (i < ny && jf <= nx) P.sigx[(long long)i * (nx + 1) + jf] = smooth ? 1 : 0;
+            }
+        } else {
+            const int w2 = w - L::NHX;
+            const int f = w2 / BX, c = w2 - f * BX;
+            const int ry = f + 5, rx = c + 6;  // lower cell of the face
+            FaceIn<T> in;
+            const T* u = sU + ry * RW + rx;
+            in.u[0] = u;
+            in.u[1] = u + 2 * NU;  // normal velocity v
+            in.u[2] = u + NU;      // tangential velocity u
+            in.u[3] = u + 3 * NU;
+            in.su = RW;
+            const T* gy = sGY + (ry - 3) * L::GYW + (rx - 6 + V);
+            in.g[0] = gy;
+            in.g[1] = gy + 2 * L::NGY;
+            in.g[2] = gy + L::NGY;
+            in.g[3] = gy + 3 * L::NGY;
+            in.sg = L::GYW;
+            in.tr = sPY + (ry - 3) * BX + c;
+            in.st = BX;
+            const T* fy = sFY + (ry - 1) * BX + c;
+            in.f[0] = fy;
+            in.f[1] = fy + 2 * L::NFY;  // rho v^2 + p
+            in.f[2] = fy + L::NFY;      // rho u v
+            in.f[3] = fy + 3 * L::NFY;
+            in.sf = BX;
+            const T* tx = sGX + (ry - 6 + V) * L::GXW + (rx - 3);
+            in.tun = tx + 2 * L::NGX;  // d v / d x
+            in.tut = tx + L::NGX;      // d u / d x
+            in.stq = L::GXW;
+            face_flux<T, VISC>(in, ph, inv_dy, inv_dx, out, smooth);
+            sHY[w2] = out[0];
+            sHY[L::NHY + w2] = out[2];
+            sHY[2 * L::NHY + w2] = out[1];
+            sHY[3 * L::NHY + w2] = out[3];
+            if (P.sigy) {
+                const int j = tx0 + c, iface = ty0 + f;
+                if (j < nx && iface <= ny) P.sigy[(long long)iface * nx + j] = smooth ? 1 : 0;
+            }
+        }
+    }
+    __syncthreads();
+
+    // Phase 3: residual (Eq. deriv) and the FP64 stage update (Eq. rk).
+    const double dt = P.dt_ptr ? *P.dt_ptr : P.dt;
+    const double cdt = P.cc * dt;
+    double lam = 0.0;
+    bool bad = false;
+    for (int idx = tid; idx < BX * BY; idx += NT) {
+        const int r = idx / BX, c = idx - r * BX;
+        const int j = tx0 + c, i = ty0 + r;
+        if (j >= nx || i >= ny) continue;
+        double res[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const T dF = sHX[m * L::NHX + r * L::HXW + c + 1] - sHX[m * L::NHX + r * L::HXW + c];
+            const T dG = sHY[m * L::NHY + (r + 1) * BX + c] - sHY[m * L::NHY + r * BX + c];
+            res[m] = double(-dF * inv_dx - dG * inv_dy);
+        }
+        if (P.res) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) P.res[(long long)m * nx * ny + (long long)i * nx + j] = res[m];
+        }
+        if (P.qout) {
+            const long long o = (long long)(i + kGhost) * pitch + (j + kGhost);
+            double qv[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                double v = P.cb * P.q[o + m * plane] + cdt * res[m];
+                if (P.ca != 0.0) v += P.ca * P.qn[o + m * plane];
+                qv[m] = v;
+            }
+#pragma unroll
+            for (int m = 0; m < 4; ++m) P.qout[o + m * plane] = qv[m];
+            // Positivity in FP64: rho > 0 and p > 0 <=> 2 rho E > |rho u|^2.
+            const bool ok = isfinite(qv[0]) && isfinite(qv[1]) && isfinite(qv[2]) && isfinite(qv[3]) &&
+                            qv[0] > 0.0 && 2.0 * qv[0] * qv[3] - (qv[1] * qv[1] + qv[2] * qv[2]) > 0.0;
+            bad |= !ok;
+            if (P.lam_out) {  // Sec. 2.5 wavespeed of the new state
+                const T r = T(qv[0]), ir = T(1) / r;
+                const T u = T(qv[1]) * ir, v = T(qv[2]) * ir;
+                const T p = ph.gm1 * (T(qv[3]) - T(0.5) * r * (u * u + v * v));
+                const T cs = tsqrt(ph.gamma * p * ir);
+                T l = tmax((tabs(u) + cs) * inv_dx, (tabs(v) + cs) * inv_dy);
+                if (P.ph.mu > 0.0) {
+                    const T nu4 = T(4) * ph.mu * ir;
+                    l = tmax(l, tmax(nu4 * inv_dx * inv_dx, nu4 * inv_dy * inv_dy));
+                }
+                lam = fmax(lam, double(l));
+            }
+        }
+    }
+    if (P.qout) {
+        if (__syncthreads_or(bad) && tid == 0) atomicOr(P.err, 1u);
+    }
+    if (P.lam_out) {
+        __shared__ double red[NT / 32];
+        lam = warp_max(lam);
+        if ((tid & 31) == 0) red[tid >> 5] = lam;
+        __syncthreads();
+        if (tid < 32) {
+            double v = (tid < NT / 32) ? red[tid] : 0.0;
+            v = warp_max(v);
+            if (tid == 0) atomicMax(P.lam_out, (unsigned long long)__double_as_longlong(v));
+        }
+    }
+}
+
+template <typename T, int BX, int BY, int NT, bool VISC>
+cudaError_t launch_stage_t(const StageParams& p, cudaStream_t s)
+{
+    using L = TileLayout<BX, BY, VISC>;
+    constexpr size_t smem = L::template bytes<T>();
+    static bool configured = false;
+    auto kern = stage_kernel<T, BX, BY, NT, VISC>;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((p.g.nx + BX - 1) / BX, (p.g.ny + BY - 1) / BY);
+    kern<<<grid, NT, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace gbr

@@ -1,0 +1,263 @@
+"""Thin ctypes binding of the C ABI in include/gbr.h (argument marshalling
+only; every step of the method runs in the CUDA library libgbr.so).
+
+Functions keep the C names. Array arguments may be numpy arrays (host) or
+torch CUDA tensors (device); the binding passes their pointers and the
+matching on_device flag. The library must have been built
+(``paper_2305_00762_gb300.build.build()``); there is no fallback path, so a
+missing library raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+GBR_OK, GBR_ERR_ARG, GBR_ERR_CUDA, GBR_ERR_NONPHYSICAL = 0, -1, -2, -3
+GBR_ERR_TIMEOUT, GBR_ERR_STATE, GBR_ERR_NOMEM, GBR_ERR_UNSUPPORTED = -4, -5, -6, -7
+GBR_BC_PERIODIC, GBR_BC_TRANSMISSIVE, GBR_BC_NOSLIP_WALL, GBR_BC_SYMMETRY = 0, 1, 2, 3
+GBR_OPT_PRECISION, GBR_OPT_RECORD_FLAGS, GBR_OPT_SENSOR, GBR_OPT_TIMING = 0, 1, 2, 3
+GBR_KERNEL_STAGE, GBR_KERNEL_GHOST, GBR_KERNEL_WAVESPEED, GBR_KERNEL_CLASSES = 0, 1, 2, 3
+GBR_GHOST = 6
+
+_lib = None
+
+
+class GbrError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {error_string(status)} ({status})")
+
+
+class gbr_bc(ctypes.Structure):
+    _fields_ = [("west", ctypes.c_int), ("east", ctypes.c_int), ("south", ctypes.c_int),
+                ("north", ctypes.c_int), ("dx", ctypes.c_double), ("dy", ctypes.c_double)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libgbr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} missing (run paper_2305_00762_gb300.build.build())")
+    L = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+    sig = {
+        "gbr_create": (ip, [ip, ip, dp, dp, dp, ctypes.POINTER(gbr_bc), ctypes.POINTER(vp)]),
+        "gbr_destroy": (ip, [vp]),
+        "gbr_set_stream": (ip, [vp, vp]),
+        "gbr_set_state": (ip, [vp, vp, ip]),
+        "gbr_get_state": (ip, [vp, vp, ip]),
+        "gbr_residual": (ip, [vp, vp, ip]),
+        "gbr_step": (ip, [vp, dp]),
+        "gbr_step_cfl": (ip, [vp, dp, dp]),
+        "gbr_get_time": (ip, [vp, ctypes.POINTER(dp)]),
+        "gbr_max_wavespeed": (ip, [vp, ctypes.POINTER(dp)]),
+        "gbr_set_option": (ip, [vp, ip, dp]),
+        "gbr_get_flags": (ip, [vp, vp, vp, ip]),
+        "gbr_get_timing": (ip, [vp, ctypes.POINTER(dp), ctypes.POINTER(ip), ctypes.POINTER(ip)]),
+        "gbr_sync": (ip, [vp]),
+        "gbr_error_string": (ctypes.c_char_p, [ip]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def error_string(status: int) -> str:
+    return load().gbr_error_string(int(status)).decode()
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("host arrays must be C-contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _check(rc: int, what: str, allow=()):
+    if rc != GBR_OK and rc not in allow:
+        raise GbrError(rc, what)
+    return rc
+
+
+def gbr_create(nx, ny, gamma, mu, Pr, bc, dx, dy):
+    b = gbr_bc(*[int(k) for k in bc], float(dx), float(dy))
+    out = ctypes.c_void_p()
+    _check(load().gbr_create(int(nx), int(ny), float(gamma), float(mu), float(Pr), ctypes.byref(b),
+                             ctypes.byref(out)), "gbr_create")
+    return out
+
+
+def gbr_destroy(ctx):
+    return _check(load().gbr_destroy(ctx), "gbr_destroy")
+
+
+def gbr_set_stream(ctx, stream):
+    return _check(load().gbr_set_stream(ctx, ctypes.c_void_p(int(stream or 0))), "gbr_set_stream")
+
+
+def _expect(a, dtype, shape):
+    if tuple(a.shape) != tuple(shape):
+        raise ValueError(f"expected shape {shape}, got {tuple(a.shape)}")
+    name = str(a.dtype)
+    if dtype not in name:
+        raise ValueError(f"expected {dtype} data, got {name}")
+
+
+def gbr_set_state(ctx, Q, nx, ny):
+    _expect(Q, "float64", (4, ny, nx))
+    p, dev = _ptr(Q)
+    return _check(load().gbr_set_state(ctx, p, dev), "gbr_set_state")
+
+
+def gbr_get_state(ctx, Q, nx, ny, allow=()):
+    _expect(Q, "float64", (4, ny, nx))
+    p, dev = _ptr(Q)
+    return _check(load().gbr_get_state(ctx, p, dev), "gbr_get_state", allow)
+
+
+def gbr_residual(ctx, R, nx, ny):
+    _expect(R, "float64", (4, ny, nx))
+    p, dev = _ptr(R)
+    return _check(load().gbr_residual(ctx, p, dev), "gbr_residual")
+
+
+def gbr_step(ctx, dt):
+    return _check(load().gbr_step(ctx, float(dt)), "gbr_step")
+
+
+def gbr_step_cfl(ctx, cfl, dt_max):
+    return _check(load().gbr_step_cfl(ctx, float(cfl), float(dt_max)), "gbr_step_cfl")
+
+
+def gbr_get_time(ctx, allow=()):
+    t = ctypes.c_double()
+    _check(load().gbr_get_time(ctx, ctypes.byref(t)), "gbr_get_time", allow)
+    return t.value
+
+
+def gbr_max_wavespeed(ctx, allow=()):
+    lam = ctypes.c_double()
+    rc = _check(load().gbr_max_wavespeed(ctx, ctypes.byref(lam)), "gbr_max_wavespeed", allow)
+    return lam.value, rc
+
+
+def gbr_set_option(ctx, key, val):
+    return _check(load().gbr_set_option(ctx, int(key), float(val)), "gbr_set_option")
+
+
+def gbr_get_flags(ctx, sigx, sigy, nx, ny):
+    _expect(sigx, "uint8", (ny, nx + 1))
+    _expect(sigy, "uint8", (ny + 1, nx))
+    px, dx_ = _ptr(sigx)
+    py, dy_ = _ptr(sigy)
+    if dx_ != dy_:
+        raise ValueError("flag buffers must both be host or both device")
+    return _check(load().gbr_get_flags(ctx, px, py, dx_), "gbr_get_flags")
+
+
+def gbr_get_timing(ctx):
+    """{class: (total_ms, launches)} since the last call, and the number of
+    launches that were counted but not timed."""
+    ms = (ctypes.c_double * GBR_KERNEL_CLASSES)()
+    n = (ctypes.c_int * GBR_KERNEL_CLASSES)()
+    dropped = ctypes.c_int()
+    _check(load().gbr_get_timing(ctx, ms, n, ctypes.byref(dropped)), "gbr_get_timing")
+    names = ("stage", "ghost", "wavespeed")
+    return {names[k]: (ms[k], n[k]) for k in range(GBR_KERNEL_CLASSES)}, dropped.value
+
+
+def gbr_sync(ctx, allow=()):
+    return _check(load().gbr_sync(ctx), "gbr_sync", allow)
+
+
+class Solver:
+    """Convenience owner of one gbr context (marshalling only)."""
+
+    def __init__(self, nx, ny, dx, dy, gamma=1.4, mu=0.0, Pr=0.72, bc=(GBR_BC_PERIODIC,) * 4,
+                 precision=64, stream=None):
+        self.nx, self.ny = int(nx), int(ny)
+        self.ctx = gbr_create(nx, ny, gamma, mu, Pr, bc, dx, dy)
+        if stream is not None:
+            gbr_set_stream(self.ctx, stream)
+        if precision != 64:
+            gbr_set_option(self.ctx, GBR_OPT_PRECISION, precision)
+
+    @classmethod
+    def for_case(cls, case, **kw):
+        return cls(case.nx, case.ny, case.dx, case.dy, case.gamma, case.mu, case.Pr, case.bc, **kw)
+
+    def close(self):
+        if self.ctx is not None:
+            gbr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, Q):
+        gbr_set_state(self.ctx, Q, self.nx, self.ny)
+
+    def get_state(self, out=None, allow=()):
+        if out is None:
+            out = np.empty((4, self.ny, self.nx))
+        gbr_get_state(self.ctx, out, self.nx, self.ny, allow)
+        return out
+
+    def residual(self, out=None):
+        if out is None:
+            out = np.empty((4, self.ny, self.nx))
+        gbr_residual(self.ctx, out, self.nx, self.ny)
+        return out
+
+    def step(self, dt):
+        gbr_step(self.ctx, dt)
+
+    def step_cfl(self, cfl, dt_max=1e300):
+        gbr_step_cfl(self.ctx, cfl, dt_max)
+
+    def time(self):
+        return gbr_get_time(self.ctx)
+
+    def max_wavespeed(self, allow=()):
+        return gbr_max_wavespeed(self.ctx, allow)[0]
+
+    def record_flags(self, on=True):
+        gbr_set_option(self.ctx, GBR_OPT_RECORD_FLAGS, 1 if on else 0)
+
+    def flags(self):
+        sx = np.empty((self.ny, self.nx + 1), np.uint8)
+        sy = np.empty((self.ny + 1, self.nx), np.uint8)
+        gbr_get_flags(self.ctx, sx, sy, self.nx, self.ny)
+        return sx, sy
+
+    def timing(self, on=True):
+        gbr_set_option(self.ctx, GBR_OPT_TIMING, 1 if on else 0)
+
+    def get_timing(self):
+        return gbr_get_timing(self.ctx)
+
+    def sync(self, allow=()):
+        return gbr_sync(self.ctx, allow)

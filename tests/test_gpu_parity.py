@@ -1,0 +1,208 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on
+the same seeded inputs, element by element (FP64: 1e-12 relative per field;
+detector flags identical except at psi ties)."""
+import numpy as np
+import pytest
+
+from paper_2305_00762_gb300 import cases as C
+
+from .parity import TOL64, assert_close, field_errors, tie_faces_ok
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle as O
+    from paper_2305_00762_gb300 import build, gbr
+    build.build()
+    O.build()
+    gbr.load()
+    return torch, O, gbr
+
+
+def cfg_of(O, c):
+    return O.Config(c.nx, c.ny, c.dx, c.dy, c.gamma, c.mu, c.Pr, c.bc)
+
+
+SMALL = [
+    ("vortex64", lambda: C.isentropic_vortex(64)),
+    ("vortex_ragged", lambda: C.isentropic_vortex(50, 37)),
+    ("riemann96", lambda: C.riemann_2d(96)),
+    ("riemann_ragged", lambda: C.riemann_2d(70, 45)),
+    ("vst64x32", lambda: C.viscous_shock_tube(64, 32)),
+    ("vst_ragged", lambda: C.viscous_shock_tube(45, 29)),
+    ("kh48", lambda: C.kelvin_helmholtz(48, np.random.default_rng(5))),
+    ("tiny6", lambda: C.riemann_2d(6, 7)),
+]
+
+
+@pytest.mark.parametrize("name,make", SMALL, ids=[s[0] for s in SMALL])
+def test_residual_and_flags(env, name, make):
+    torch, O, gbr = env
+    c = make()
+    s = gbr.Solver.for_case(c)
+    s.record_flags(True)
+    s.set_state(c.Q)
+    R = s.residual()
+    sx, sy = s.flags()
+    Ro, sxo, syo = O.residual(cfg_of(O, c), c.Q, want_flags=True)
+    excl = tie_faces_ok(O, cfg_of(O, c), c.Q, sx, sxo, sy, syo)
+    assert_close(R, Ro, exclude=excl, what=f"{name} residual")
+    s.close()
+
+
+@pytest.mark.parametrize("name,make", SMALL, ids=[s[0] for s in SMALL])
+def test_one_rk3_step(env, name, make):
+    torch, O, gbr = env
+    c = make()
+    s = gbr.Solver.for_case(c)
+    s.set_state(c.Q)
+    lam = s.max_wavespeed()
+    lam_o = O.max_wavespeed(cfg_of(O, c), c.Q)
+    assert abs(lam - lam_o) <= 1e-14 * lam_o
+    dt = c.cfl / lam_o
+    s.step(dt)
+    Q1 = s.get_state()
+    Qo, rc = O.rk3_step(cfg_of(O, c), c.Q, dt)
+    assert rc == 0
+    assert_close(Q1, Qo, what=f"{name} step")
+    lam1 = s.max_wavespeed()
+    assert abs(lam1 - O.max_wavespeed(cfg_of(O, c), Qo)) <= 1e-12 * lam1
+    s.close()
+
+
+def test_vortex_100_stages(env):
+    """Config 1: 64^2 vortex, 100 RK stages at CFL 0.5 through the
+    device-side dt path; every step matches the oracle."""
+    torch, O, gbr = env
+    c = C.isentropic_vortex(64)
+    cfg = cfg_of(O, c)
+    s = gbr.Solver.for_case(c)
+    s.set_state(c.Q)
+    Q = c.Q.copy()
+    worst = 0.0
+    for k in range(34):   # 34 steps = 102 stages
+        dt = 0.5 / O.max_wavespeed(cfg, Q)
+        s.step_cfl(0.5)
+        Q, rc = O.rk3_step(cfg, Q, dt)
+        assert rc == 0
+        if k % 11 == 10 or k == 33:
+            worst = max(worst, max(field_errors(s.get_state(), Q)))
+    assert worst <= TOL64 * 10, worst   # 34 steps of roundoff growth
+    t = s.time()
+    assert t > 0
+    s.close()
+
+
+def test_device_buffers_and_streams(env):
+    """Device tensors in and out (on_device = 1) on a torch stream."""
+    torch, O, gbr = env
+    c = C.riemann_2d(64, 48)
+    st = torch.cuda.Stream()
+    s = gbr.Solver.for_case(c, stream=st.cuda_stream)
+    Qd = torch.from_numpy(c.Q).cuda()
+    with torch.cuda.stream(st):
+        s.set_state(Qd)
+        Rd = torch.empty_like(Qd)
+        gbr.gbr_residual(s.ctx, Rd, c.nx, c.ny)
+        s.step(1e-4)
+        Qout = torch.empty_like(Qd)
+        gbr.gbr_get_state(s.ctx, Qout, c.nx, c.ny)
+    st.synchronize()
+    Ro = O.residual(cfg_of(O, c), c.Q)
+    assert_close(Rd.cpu().numpy(), Ro, what="device residual")
+    Qo, _ = O.rk3_step(cfg_of(O, c), c.Q, 1e-4)
+    assert_close(Qout.cpu().numpy(), Qo, what="device step")
+    s.close()
+
+
+def test_checkpoint_resume_bitwise(env):
+    """get_state / set_state round trip: a resumed run is bitwise identical."""
+    torch, O, gbr = env
+    c = C.kelvin_helmholtz(64, np.random.default_rng(1))
+    a = gbr.Solver.for_case(c)
+    a.set_state(c.Q)
+    for _ in range(3):
+        a.step_cfl(0.5)
+    mid = a.get_state()
+    b = gbr.Solver.for_case(c)
+    b.set_state(mid)
+    for _ in range(3):
+        a.step(1e-3)
+        b.step(1e-3)
+    assert np.array_equal(a.get_state(), b.get_state())
+    a.close()
+    b.close()
+
+
+def test_nonphysical_state_reported(env):
+    """A negative-pressure cell makes the next synchronising call report
+    GBR_ERR_NONPHYSICAL (no trap, the context stays usable)."""
+    torch, O, gbr = env
+    c = C.riemann_2d(32)
+    Q = c.Q.copy()
+    Q[3, 10, 10] = 0.5 * (Q[1, 10, 10] ** 2 + Q[2, 10, 10] ** 2) / Q[0, 10, 10] - 0.05
+    s = gbr.Solver.for_case(c)
+    s.set_state(Q)
+    s.step(1e-4)
+    assert s.sync(allow=(gbr.GBR_ERR_NONPHYSICAL,)) == gbr.GBR_ERR_NONPHYSICAL
+    s.set_state(c.Q)          # a fresh state clears the error word
+    s.step(1e-4)
+    assert s.sync() == gbr.GBR_OK
+    s.close()
+
+
+def test_full_size_riemann_1024(env):
+    """Config 2 at full size (1024^2, transmissive), in the launch
+    configuration the benchmark times: whole-grid residual parity and one
+    RK3 step."""
+    torch, O, gbr = env
+    c = C.riemann_2d(1024)
+    cfg = cfg_of(O, c)
+    s = gbr.Solver.for_case(c)
+    s.record_flags(True)
+    s.set_state(c.Q)
+    R = s.residual()
+    sx, sy = s.flags()
+    Ro, sxo, syo = O.residual(cfg, c.Q, want_flags=True)
+    excl = tie_faces_ok(O, cfg, c.Q, sx, sxo, sy, syo)
+    assert_close(R, Ro, exclude=excl, what="riemann1024 residual")
+    dt = 0.5 / O.max_wavespeed(cfg, c.Q)
+    s.step(dt)
+    Qo, rc = O.rk3_step(cfg, c.Q, dt)
+    assert rc == 0
+    assert_close(s.get_state(), Qo, what="riemann1024 step")
+    s.close()
+
+
+def _sample_mask(ny, nx, rng, n=4000):
+    m = np.zeros((ny, nx), np.uint8)
+    m[rng.integers(0, ny, n), rng.integers(0, nx, n)] = 1
+    m[0, :] = 1
+    m[-1, :] = 1
+    m[:, 0] = 1
+    m[:, -1] = 1
+    return m
+
+
+@pytest.mark.parametrize("which", ["riemann4096", "vst2048x1024"])
+def test_full_size_sampled(env, which):
+    """Configs 3 and 4 at full size: the residual at sampled cells (all
+    boundary cells plus random interior ones), computed one by one by the
+    oracle from the same state."""
+    torch, O, gbr = env
+    c = C.riemann_2d(4096) if which == "riemann4096" else C.viscous_shock_tube(2048, 1024)
+    cfg = cfg_of(O, c)
+    s = gbr.Solver.for_case(c)
+    s.set_state(c.Q)
+    R = s.residual()
+    mask = _sample_mask(c.ny, c.nx, np.random.default_rng(7))
+    Ro = O.residual(cfg, c.Q, mask=mask)
+    sel = mask.astype(bool)
+    errs = [np.abs(R[m][sel] - Ro[m][sel]).max() / max(np.abs(Ro[m][sel]).max(), 1e-300) for m in range(4)]
+    assert max(errs) <= TOL64, errs
+    s.close()
