@@ -174,6 +174,39 @@ int gbr_get_timing(gbr_ctx *ctx, double *ms, int *launches, int *dropped);
 /* Wait for the context's stream and report pending device errors. */
 int gbr_sync(gbr_ctx *ctx);
 
+/* Capacity of the scratch array of gbr_step_static, in doubles (8 MiB). */
+#define GBR_STATIC_SCRATCH_DOUBLES (1 << 20)
+
+/* One TVD-RK3 step of size dt (the same kernels and result as gbr_step) of a
+ * caller-owned device state, without allocating any device memory. The paper
+ * has no counterpart to this entry point; it is for callers that cannot
+ * call cudaMalloc at run time -- a host application that owns all device
+ * memory through its own pool and forbids plugins to allocate, a real-time
+ * loop that must not enter the driver's allocator (cudaMalloc may
+ * synchronise the device and take unbounded time), a process running close
+ * to its memory limit.
+ *
+ * Q_in, Q_out: device pointers, [4][ny][nx] float64 (layout as above); they
+ * may be the same buffer. The grid, gas and boundary arguments mean what they
+ * mean for gbr_create; dt > 0; stream: a cudaStream_t (NULL = legacy default
+ * stream). The call is synchronous: it waits for the stream and returns
+ * GBR_ERR_NONPHYSICAL if a stage produced rho <= 0, p <= 0 or a non-finite
+ * value (the step is still completed and written).
+ *
+ * Scratch: a file-scope __device__ array of GBR_STATIC_SCRATCH_DOUBLES
+ * doubles, held by every GPU that loads the library until the process exits.
+ * A grid needs 32 + 12 * roundup16(roundup16(nx + 12) * (ny + 12)) doubles of
+ * it, which admits up to about 270 x 270 cells (256 x 256 fits); a larger
+ * grid returns GBR_ERR_ARG and nothing runs. The first call on a device looks
+ * up the array's device address for that device (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture. All
+ * calls share the one array and each clears what must start at zero; calls
+ * that overlap on the GPU (several host threads or streams at once) race on
+ * it, so serialise them. Allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine is called. */
+int gbr_step_static(const double *Q_in, double *Q_out, int nx, int ny, double gamma, double mu, double Pr,
+                    const gbr_bc *bc, double dt, void *stream);
+
 /* Static text for a gbr_status value. */
 const char *gbr_error_string(int status);
 

@@ -22,6 +22,7 @@ GBR_BC_PERIODIC, GBR_BC_TRANSMISSIVE, GBR_BC_NOSLIP_WALL, GBR_BC_SYMMETRY = 0, 1
 GBR_OPT_PRECISION, GBR_OPT_RECORD_FLAGS, GBR_OPT_SENSOR, GBR_OPT_TIMING = 0, 1, 2, 3
 GBR_KERNEL_STAGE, GBR_KERNEL_GHOST, GBR_KERNEL_WAVESPEED, GBR_KERNEL_CLASSES = 0, 1, 2, 3
 GBR_GHOST = 6
+GBR_STATIC_SCRATCH_DOUBLES = 1 << 20
 
 _lib = None
 
@@ -66,6 +67,7 @@ def load():
         "gbr_get_flags": (ip, [vp, vp, vp, ip]),
         "gbr_get_timing": (ip, [vp, ctypes.POINTER(dp), ctypes.POINTER(ip), ctypes.POINTER(ip)]),
         "gbr_sync": (ip, [vp]),
+        "gbr_step_static": (ip, [vp, vp, ip, ip, dp, dp, dp, ctypes.POINTER(gbr_bc), dp, vp]),
         "gbr_error_string": (ctypes.c_char_p, [ip]),
     }
     for name, (res, args) in sig.items():
@@ -188,6 +190,34 @@ def gbr_get_timing(ctx):
 
 def gbr_sync(ctx, allow=()):
     return _check(load().gbr_sync(ctx), "gbr_sync", allow)
+
+
+def static_scratch_doubles(nx, ny):
+    """Doubles of the static scratch array gbr_step_static needs for an
+    nx x ny grid (it rejects grids above GBR_STATIC_SCRATCH_DOUBLES)."""
+    pitch = (nx + 2 * GBR_GHOST + 15) // 16 * 16
+    plane = (pitch * (ny + 2 * GBR_GHOST) + 15) // 16 * 16
+    return 32 + 12 * plane
+
+
+def gbr_step_static(Q_in, Q_out, nx, ny, gamma, mu, Pr, bc, dx, dy, dt, stream=0, allow=()):
+    """One RK3 step of device tensors Q_in -> Q_out ([4][ny][nx] float64)
+    that allocates no device memory (scratch in the library's static array).
+    Raises ValueError for a grid beyond the array's capacity."""
+    _expect(Q_in, "float64", (4, ny, nx))
+    _expect(Q_out, "float64", (4, ny, nx))
+    pin, din = _ptr(Q_in)
+    pout, dout = _ptr(Q_out)
+    if not (din and dout):
+        raise ValueError("gbr_step_static takes device buffers")
+    need = static_scratch_doubles(nx, ny)
+    if need > GBR_STATIC_SCRATCH_DOUBLES:
+        raise ValueError(f"grid {nx}x{ny} needs {need} doubles of static scratch; the library holds "
+                         f"{GBR_STATIC_SCRATCH_DOUBLES} (about 270 x 270 cells at most)")
+    b = gbr_bc(*[int(k) for k in bc], float(dx), float(dy))
+    rc = load().gbr_step_static(pin, pout, int(nx), int(ny), float(gamma), float(mu), float(Pr),
+                                ctypes.byref(b), float(dt), ctypes.c_void_p(int(stream or 0)))
+    return _check(rc, "gbr_step_static", allow)
 
 
 class Solver:
