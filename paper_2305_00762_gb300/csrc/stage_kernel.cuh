@@ -58,6 +58,8 @@ template <typename T>
 __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 __device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double trsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float trsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double tabs(double x) { return fabs(x); }
 __device__ __forceinline__ float tabs(float x) { return fabsf(x); }
 
@@ -90,11 +92,16 @@ __device__ __forceinline__ bool trouble_cell(const T* r, int st)
 
 // Eqs. grb, mp5Condition, alpha, mp-procedure: MEG7 left value at j+1/2 from
 // Phi_{j-2..j+2} (p0..p4) and Phi'_{j-2..j+2} (d0..d4), xi = 7.
+// The GRB weights of Phi sum to one (478 + 2*178 + 2*3 = 840), so Eq. grb is
+// evaluated as Phi_j plus weighted differences: on flat data Phi^L equals
+// Phi_j exactly and the MP test passes without entering the limiter (whose
+// result there is Phi_j as well).
 template <typename T>
 __device__ __forceinline__ T meg7(T p0, T p1, T p2, T p3, T p4, T d0, T d1, T d2, T d3, T d4)
 {
-    const T pl = (T(420) * d2 + T(60) * (d1 - d3) + T(478) * p2 + T(178) * (p1 + p3) + T(3) * (p0 + p4)) *
-                 T(1.0 / 840.0);
+    const T pl = p2 + (T(420) * d2 + T(60) * (d1 - d3) + T(178) * ((p1 - p2) + (p3 - p2)) +
+                       T(3) * ((p0 - p2) + (p4 - p2))) *
+                          T(1.0 / 840.0);
     const T pmp = p2 + minmod(p3 - p2, T(7) * (p2 - p1));
     if ((pl - p2) * (pl - pmp) <= T(1e-40)) return pl;
     const T dm1 = T(2) * (p2 - T(2) * p1 + p0) - T(0.5) * (d2 - d0);
@@ -108,20 +115,15 @@ __device__ __forceinline__ T meg7(T p0, T p1, T p2, T p3, T p4, T d0, T d1, T d2
     return pl + minmod(pmin - pl, pmax - pl);
 }
 
-// Eq. flux-full (left) and Eq. flux-right at the face after cell f[0].
+// 1/2 (F(f_L) + F(f_R)) at the face after cell f[0]: the sum of Eq.
+// flux-full and its mirror Eq. flux-right is the symmetric 10-point stencil
+// (-1, 1, 38, -250, 1052 | 1052, -250, 38, 1, -1) / 840 over f_{j-4..j+5}.
 template <typename T>
-__device__ __forceinline__ T recon_left(const T* f, int s)
+__device__ __forceinline__ T recon_mean(const T* f, int s)
 {
-    return (T(568) * f[0] - T(146) * f[-s] + T(22) * f[-2 * s] + T(2) * f[-3 * s] - f[-4 * s] + T(484) * f[s] -
-            T(104) * f[2 * s] + T(16) * f[3 * s] - f[4 * s]) *
-           T(1.0 / 840.0);
-}
-template <typename T>
-__device__ __forceinline__ T recon_right(const T* f, int s)
-{
-    return (-f[5 * s] + T(2) * f[4 * s] + T(22) * f[3 * s] - T(146) * f[2 * s] + T(568) * f[s] + T(484) * f[0] -
-            T(104) * f[-s] + T(16) * f[-2 * s] - f[-3 * s]) *
-           T(1.0 / 840.0);
+    return (T(1052) * (f[0] + f[s]) - T(250) * (f[-s] + f[2 * s]) + T(38) * (f[-2 * s] + f[3 * s]) +
+            (f[-3 * s] + f[4 * s]) - (f[-4 * s] + f[5 * s])) *
+           T(1.0 / 1680.0);
 }
 
 template <typename T>
@@ -160,8 +162,10 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
     // Characteristic projection at the arithmetic-mean state.
     const T rb = T(0.5) * (in.u[0][0] + in.u[0][su]);
     const T pb = T(0.5) * (in.u[3][0] + in.u[3][su]);
-    const T cb = tsqrt(P.gamma * pb / rb);
-    const T icb = T(1) / cb;
+    const T irb = T(1) / rb;
+    const T c2 = P.gamma * pb * irb;  // c^2
+    const T icb = trsqrt(c2);         // 1 / c
+    const T cb = c2 * icb;
     const T al = T(0.5) * rb * icb;  // rho / (2 c)
     const T ic2 = icb * icb;         // 1 / c^2
     const T be = T(0.5) * ic2;       // 1 / (2 c^2)
@@ -207,7 +211,7 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
         wR[2] = meg7(w[5], w[4], w[3], w[2], w[1], -e[5], -e[4], -e[3], -e[2], -e[1]);
     }
     // Back to primitive variables with the right eigenvectors.
-    const T crb = cb / rb, c2 = cb * cb;
+    const T crb = cb * irb;
     const T rL = wL[0] + wL[1] + wL[3], unL = crb * (wL[3] - wL[0]), utL = wL[2], pL = c2 * (wL[0] + wL[3]);
     const T rR = wR[0] + wR[1] + wR[3], unR = crb * (wR[3] - wR[0]), utR = wR[2], pR = c2 * (wR[0] + wR[3]);
     const T EL = pL * P.igm1 + T(0.5) * rL * (unL * unL + utL * utL);
@@ -215,31 +219,30 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
     const T QL[4] = {rL, rL * unL, rL * utL, EL};
     const T QR[4] = {rR, rR * unR, rR * utR, ER};
 
-    // Hybrid face fluxes (Sec. 2.4): sigma F(f) + (1 - sigma) F(Q).
-    T FL[4], FR[4];
+    // Central part 1/2 (F_L + F_R) of the hybrid face fluxes (Sec. 2.4):
+    // flux reconstruction where sigma = 1, F(Q_L), F(Q_R) where sigma = 0.
+    T Fc[4];
     if (smooth) {
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            FL[m] = recon_left(in.f[m], in.sf);
-            FR[m] = recon_right(in.f[m], in.sf);
-        }
+        for (int m = 0; m < 4; ++m) Fc[m] = recon_mean(in.f[m], in.sf);
     } else {
-        FL[0] = QL[1];
-        FL[1] = QL[1] * unL + pL;
-        FL[2] = QL[1] * utL;
-        FL[3] = unL * (EL + pL);
-        FR[0] = QR[1];
-        FR[1] = QR[1] * unR + pR;
-        FR[2] = QR[1] * utR;
-        FR[3] = unR * (ER + pR);
+        Fc[0] = T(0.5) * (QL[1] + QR[1]);
+        Fc[1] = T(0.5) * ((QL[1] * unL + pL) + (QR[1] * unR + pR));
+        Fc[2] = T(0.5) * (QL[1] * utL + QR[1] * utR);
+        Fc[3] = T(0.5) * (unL * (EL + pL) + unR * (ER + pR));
     }
 
-    // HLLC in the form 1/2 (F_L + F_R) - 1/2 |A| (Q_R - Q_L), Eq. Riemann_revisit.
+    // HLLC in the form 1/2 (F_L + F_R) - 1/2 |A| (Q_R - Q_L), Eq. Riemann_revisit,
+    // with Toro's star states; k (E/rho + (S*-u)(S* + p/(rho (S-u)))) is
+    // expanded so that the only divisions are 1/(S_K - S*), S* and the Roe
+    // weight.
     {
-        const T irL = T(1) / rL, irR = T(1) / rR;
+        const T rsL = trsqrt(rL), rsR = trsqrt(rR);  // 1/sqrt(rho)
+        const T sL = rL * rsL, sR = rR * rsR;        // sqrt(rho)
+        const T irL = rsL * rsL, irR = rsR * rsR;    // 1/rho
         const T cL = tsqrt(P.gamma * pL * irL), cR = tsqrt(P.gamma * pR * irR);
         const T HL = (EL + pL) * irL, HR = (ER + pR) * irR;
-        const T sL = tsqrt(rL), sR = tsqrt(rR), isum = T(1) / (sL + sR);
+        const T isum = T(1) / (sL + sR);
         const T ut = (sL * unL + sR * unR) * isum;
         const T vt = (sL * utL + sR * utR) * isum;
         const T Ht = (sL * HL + sR * HR) * isum;
@@ -248,14 +251,15 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
         const T SR = tmax(unR + cR, ut + ct);
         const T mL = rL * (SL - unL), mR = rR * (SR - unR);
         const T Ss = (pR - pL + mL * unL - mR * unR) / (mL - mR);
-        const T kL = mL / (SL - Ss), kR = mR / (SR - Ss);
-        const T QsL[4] = {kL, kL * Ss, kL * utL, kL * (EL * irL + (Ss - unL) * (Ss + pL / mL))};
-        const T QsR[4] = {kR, kR * Ss, kR * utR, kR * (ER * irR + (Ss - unR) * (Ss + pR / mR))};
+        const T iL = T(1) / (SL - Ss), iR = T(1) / (SR - Ss);
+        const T kL = mL * iL, kR = mR * iR;
+        const T QsL[4] = {kL, kL * Ss, kL * utL, kL * (EL * irL + (Ss - unL) * Ss) + (Ss - unL) * pL * iL};
+        const T QsR[4] = {kR, kR * Ss, kR * utR, kR * (ER * irR + (Ss - unR) * Ss) + (Ss - unR) * pR * iR};
         const T aL = tabs(SL), aS = tabs(Ss), aR = tabs(SR);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const T adq = aL * (QsL[m] - QL[m]) + aS * (QsR[m] - QsL[m]) + aR * (QR[m] - QsR[m]);
-            out[m] = T(0.5) * (FL[m] + FR[m]) - T(0.5) * adq;
+            out[m] = Fc[m] - T(0.5) * adq;
         }
     }
 
