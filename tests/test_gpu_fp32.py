@@ -39,11 +39,11 @@ def test_fp32_density_l1_vs_oracle(env, name, make, steps):
     torch, O, gbr = env
     c = make()
     cfg = O.Config(c.nx, c.ny, c.dx, c.dy, c.gamma, c.mu, c.Pr, c.bc)
-    dt = c.cfl / O.max_wavespeed(cfg, c.Q) * 0.8
     s = gbr.Solver.for_case(c, precision=32)
     s.set_state(c.Q)
     Q = c.Q.copy()
     for _ in range(steps):
+        dt = 0.8 * c.cfl / O.max_wavespeed(cfg, Q)   # same dt on both sides
         s.step(dt)
         Q, rc = O.rk3_step(cfg, Q, dt)
         assert rc == 0
