@@ -174,6 +174,65 @@ int gbr_get_timing(gbr_ctx *ctx, double *ms, int *launches, int *dropped);
 /* Wait for the context's stream and report pending device errors. */
 int gbr_sync(gbr_ctx *ctx);
 
+/* ----------------------------------------------------------------------
+ * Batches: many independent inviscid grids of uneven size stepped together.
+ * Every RK stage of every grid runs in one persistent kernel launch (each CTA
+ * walks the batch's tile list); each grid advances with its own
+ * dt = min(cfl / lambda_k, t_end_k - t_k) formed on the device, so a call to
+ * gbr_batch_step_cfl replays a CUDA graph of its nsteps steps without any
+ * host synchronisation. Grids, gas and the scheme are as for gbr_create with
+ * mu = 0; each grid's state is set and read like gbr_set_state /
+ * gbr_get_state. Device memory: about 96 (nx+12)(ny+12) bytes per grid.
+ * ---------------------------------------------------------------------- */
+typedef struct gbr_batch gbr_batch; /* opaque, library-owned */
+
+/* Create a batch of n >= 1 grids: grid k has nx[k] x ny[k] interior cells
+ * (>= GBR_GHOST), cell sizes dx[k], dy[k] > 0 and boundary kinds
+ * bc[4k .. 4k+3] (west, east, south, north); all share gamma > 1 (inviscid).
+ * Host arrays, read during the call only. Precision defaults to 64. */
+int gbr_batch_create(int n, const int *nx, const int *ny, const double *dx, const double *dy, const int *bc,
+                     double gamma, gbr_batch **out);
+
+/* Free the batch and its device memory (NULL accepted). */
+int gbr_batch_destroy(gbr_batch *b);
+
+/* Issue all later work of the batch on `stream` (NULL = legacy default). */
+int gbr_batch_set_stream(gbr_batch *b, void *stream);
+
+/* GBR_OPT_PRECISION (64 or 32, as for a single grid) or GBR_OPT_TIMING. */
+int gbr_batch_set_option(gbr_batch *b, int key, double val);
+
+/* Set grid k's state ([4][ny_k][nx_k] float64); resets its time to 0 and
+ * computes its CFL wavespeed on the device. */
+int gbr_batch_set_state(gbr_batch *b, int k, const double *Q, int on_device);
+
+/* Copy grid k's state out (synchronises for host buffers). */
+int gbr_batch_get_state(gbr_batch *b, int k, double *Q, int on_device);
+
+/* Per-grid end times t_end[0..n-1] (host array; default: unbounded). A grid
+ * whose time reached its t_end takes no further steps (dt = 0, no work). */
+int gbr_batch_set_end_times(gbr_batch *b, const double *t_end);
+
+/* nsteps >= 1 TVD-RK3 steps of every grid at its own CFL time step
+ * (cfl > 0). The launch sequence (batched ghost fills and persistent stage
+ * kernels) is captured once into a CUDA graph per (nsteps, cfl, precision,
+ * tile shape) and replayed. Asynchronous. */
+int gbr_batch_step_cfl(gbr_batch *b, double cfl, int nsteps);
+
+/* Per-grid time t[k] and last step size dt[k] (host arrays of n entries, either
+ * may be NULL). Synchronises; returns GBR_ERR_NONPHYSICAL if any grid's stage
+ * produced rho <= 0, p <= 0 or a non-finite value. */
+int gbr_batch_get_times(gbr_batch *b, double *t, double *dt);
+
+/* Time every candidate tile shape of the current precision on the batch's
+ * own grids (`trials` launches of the first RK stage each, which leave the
+ * states untouched) and keep the fastest; *choice (may be NULL) receives its
+ * index and *bx, *by (may be NULL) its shape. */
+int gbr_batch_autotune(gbr_batch *b, int trials, int *choice, int *bx, int *by);
+
+/* Wait for the batch's stream; reports pending device errors. */
+int gbr_batch_sync(gbr_batch *b);
+
 /* Capacity of the scratch array of gbr_step_static, in doubles (8 MiB). */
 #define GBR_STATIC_SCRATCH_DOUBLES (1 << 20)
 

@@ -2,34 +2,16 @@
 // ghost-cell boundaries; Sec. 2.5 time step).
 #include <cuda_runtime.h>
 
+#include "ghost.cuh"
 #include "gbr_internal.h"
 
 namespace gbr {
 
-// Source index of ghost coordinate k on an axis of n interior cells, and
-// whether the normal / tangential velocity changes sign (GBR_BC_* kinds:
-// 0 periodic, 1 transmissive, 2 no-slip wall, 3 symmetry).
-__device__ __forceinline__ int ghost_src(int k, int n, int lo, int hi, bool& flip_n, bool& flip_t)
-{
-    flip_n = false;
-    flip_t = false;
-    if (k >= 0 && k < n) return k;
-    const int bc = k < 0 ? lo : hi;
-    if (bc == 0) return ((k % n) + n) % n;
-    if (bc == 1) return k < 0 ? 0 : n - 1;
-    flip_n = true;
-    flip_t = (bc == 2);
-    return k < 0 ? -1 - k : 2 * n - 1 - k;
-}
-
-// One thread per ghost cell of the padded frame. A corner ghost takes the y
-// image of the x image of an interior cell, so the velocity sign flips of
-// both axes compose.
+// One thread per ghost cell of the padded frame; its first thread also does
+// the per-step scalar bookkeeping of GhostParams::mode.
 __global__ void ghost_kernel(const GhostParams P)
 {
-    const int nx = P.g.nx, ny = P.g.ny, W = nx + 2 * kGhost;
-    const long long band = (long long)kGhost * W;
-    const long long total = 2 * band + 2LL * kGhost * ny;
+    const long long total = ghost_count(P.g);
     const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id == 0 && P.mode != 0) {
         DevScalars* d = P.ds;
@@ -43,42 +25,51 @@ __global__ void ghost_kernel(const GhostParams P)
         d->lam[P.next] = 0ull;
     }
     if (id >= total) return;
-    int gx, gy;
-    if (id < band) {
-        gy = (int)(id / W);
-        gx = (int)(id - (long long)gy * W);
-    } else if (id < 2 * band) {
-        const long long k = id - band;
-        gy = ny + kGhost + (int)(k / W);
-        gx = (int)(k - (long long)(k / W) * W);
-    } else {
-        const long long k = id - 2 * band;
-        gy = kGhost + (int)(k / (2 * kGhost));
-        const int c = (int)(k - (long long)(k / (2 * kGhost)) * (2 * kGhost));
-        gx = c < kGhost ? c : nx + c;
-    }
-    const int j = gx - kGhost, i = gy - kGhost;
-    bool fnx, ftx, fny, fty;
-    const int js = ghost_src(j, nx, P.bc[0], P.bc[1], fnx, ftx);
-    const int is = ghost_src(i, ny, P.bc[2], P.bc[3], fny, fty);
-    const bool flip_u = fnx != fty;  // x momentum: normal to x faces, tangential to y faces
-    const bool flip_v = ftx != fny;
-    const long long d = (long long)gy * P.g.pitch + gx;
-    const long long s = (long long)(is + kGhost) * P.g.pitch + (js + kGhost);
-    const long long pl = P.g.plane;
-    double* q = P.q;
-    q[d] = q[s];
-    q[d + pl] = flip_u ? -q[s + pl] : q[s + pl];
-    q[d + 2 * pl] = flip_v ? -q[s + 2 * pl] : q[s + 2 * pl];
-    q[d + 3 * pl] = q[s + 3 * pl];
+    fill_ghost(P.g, P.q, P.bc, id);
 }
 
 cudaError_t launch_ghosts(const GhostParams& p, cudaStream_t s)
 {
-    const long long total = 2LL * kGhost * (p.g.nx + 2 * kGhost) + 2LL * kGhost * p.g.ny;
+    const long long total = ghost_count(p.g);
     const int nt = 256;
     const unsigned nb = (unsigned)((total + nt - 1) / nt);
     ghost_kernel<<<nb, nt, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// Ghost cells of buffer `buf` of every grid of a batch (one thread per ghost
+// cell of the whole batch); with mode 2 the first ncases threads also form
+// each grid's dt, advance its time and clear its wavespeed slot.
+__global__ void batch_ghost_kernel(const BatchCase* __restrict__ cases, int ncases, long long total, int buf,
+                                   int mode, double cfl)
+{
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (mode == 2 && id < ncases) {
+        DevScalars* d = cases[id].ds;
+        const double lam = __longlong_as_double((long long)d->lam[0]);
+        const double rem = cases[id].t_end - d->t;
+        const double dt = rem > 0.0 ? fmin(cfl / lam, rem) : 0.0;
+        d->dt = dt;
+        d->t += dt;
+        d->lam[0] = 0ull;
+    }
+    if (id >= total) return;
+    int lo = 0, hi = ncases - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cases[mid].ghost_begin <= id) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchCase& C = cases[lo];
+    fill_ghost(C.g, C.q[buf], C.bc, id - C.ghost_begin);
+}
+
+cudaError_t launch_batch_ghosts(const BatchCase* cases, int ncases, long long total_ghosts, int buf, int mode,
+                                double cfl, cudaStream_t s)
+{
+    long long n = total_ghosts > ncases ? total_ghosts : ncases;
+    const int nt = 256;
+    batch_ghost_kernel<<<(unsigned)((n + nt - 1) / nt), nt, 0, s>>>(cases, ncases, total_ghosts, buf, mode, cfl);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,25 @@
+// FP32-arithmetic instantiations of the persistent batch stage kernel
+// (candidate tile shapes picked by the batch autotuner).
+#include "batch_stage.cuh"
+
+namespace gbr {
+
+static const TileShape kShapesF32[] = {{32, 16}, {32, 8}, {64, 8}};
+
+int batch_tile_shapes_f32(const TileShape** shapes)
+{
+    *shapes = kShapesF32;
+    return 3;
+}
+
+cudaError_t launch_batch_stage_f32(int shape, const BatchCase* cases, int ncases, int total_tiles, int stage,
+                                   cudaStream_t s)
+{
+    switch (shape) {
+    case 0: return launch_batch_t<float, 32, 16, 256>(cases, ncases, total_tiles, stage, s);
+    case 1: return launch_batch_t<float, 32, 8, 256>(cases, ncases, total_tiles, stage, s);
+    default: return launch_batch_t<float, 64, 8, 256>(cases, ncases, total_tiles, stage, s);
+    }
+}
+
+}  // namespace gbr

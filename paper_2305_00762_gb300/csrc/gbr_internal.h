@@ -60,7 +60,39 @@ struct GhostParams {
     double dt, cfl, dt_max;
 };
 
+// One grid of a batch, as the device sees it. tiles_x / tile_begin describe
+// the current tile shape: tile t of the batch belongs to the case with the
+// largest tile_begin <= t.
+struct BatchCase {
+    Grid g;
+    Physics ph;
+    int bc[4];
+    double* q[3];        // Q^n, Q^(1), Q^(2) (padded)
+    DevScalars* ds;      // lam[0] = wavespeed of Q^n, dt, t, err
+    double t_end;        // the case stops (dt = 0) once t reaches t_end
+    int tiles_x, tiles;  // tiles of this case for the current tile shape
+    int tile_begin;      // first batch tile of this case
+    long long ghost_begin;  // first batch ghost cell of this case
+};
+
+struct TileShape {
+    int bx, by;
+};
+
 cudaError_t launch_ghosts(const GhostParams& p, cudaStream_t s);
+// Ghost cells of buffer `buf` (0, 1, 2) of every case; with mode 2 the first
+// ncases threads also form each case's dt = min(cfl / lam, t_end - t), advance
+// its time and clear its wavespeed slot.
+cudaError_t launch_batch_ghosts(const BatchCase* cases, int ncases, long long total_ghosts, int buf, int mode,
+                                double cfl, cudaStream_t s);
+// Candidate tile shapes of the persistent batch kernel (returns the count).
+int batch_tile_shapes_f64(const TileShape** shapes);
+int batch_tile_shapes_f32(const TileShape** shapes);
+// Persistent kernel over all tiles of all cases for RK stage `stage` (0, 1, 2).
+cudaError_t launch_batch_stage_f64(int shape, const BatchCase* cases, int ncases, int total_tiles, int stage,
+                                   cudaStream_t s);
+cudaError_t launch_batch_stage_f32(int shape, const BatchCase* cases, int ncases, int total_tiles, int stage,
+                                   cudaStream_t s);
 cudaError_t launch_wavespeed(const Grid& g, const Physics& ph, const double* q,
                              unsigned long long* lam, cudaStream_t s);
 cudaError_t launch_stage_f64(const StageParams& p, cudaStream_t s);

@@ -300,11 +300,16 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
+// One tile of one stage: phases 0-3 for the BX x BY cells whose first cell is
+// (tx0, ty0), including the tile's wavespeed max and error word. Shared by
+// the single-grid kernel (one CTA per tile) and the persistent batch kernel
+// (a CTA walks many tiles of many grids). Starts and ends with all threads
+// synchronised, so consecutive calls may reuse the shared memory.
 template <typename T, int BX, int BY, int NT, bool VISC>
-__global__ void __launch_bounds__(NT) stage_kernel(const StageParams P)
+__device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, const int ty0,
+                                           unsigned char* smem_raw)
 {
     using L = TileLayout<BX, BY, VISC>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* const sm = reinterpret_cast<T*>(smem_raw);
     T* const sU = sm + L::oU;
     T* const sGX = sm + L::oGX;
@@ -319,7 +324,6 @@ __global__ void __launch_bounds__(NT) stage_kernel(const StageParams P)
 
     const int nx = P.g.nx, ny = P.g.ny, pitch = P.g.pitch;
     const long long plane = P.g.plane;
-    const int tx0 = blockIdx.x * BX, ty0 = blockIdx.y * BY;
     const int tid = threadIdx.x;
 
     PhysT<T> ph;
@@ -540,6 +544,14 @@ __global__ void __launch_bounds__(NT) stage_kernel(const StageParams P)
             if (tid == 0) atomicMax(P.lam_out, (unsigned long long)__double_as_longlong(v));
         }
     }
+    __syncthreads();
+}
+
+template <typename T, int BX, int BY, int NT, bool VISC>
+__global__ void __launch_bounds__(NT) stage_kernel(const StageParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    stage_tile<T, BX, BY, NT, VISC>(P, blockIdx.x * BX, blockIdx.y * BY, smem_raw);
 }
 
 template <typename T, int BX, int BY, int NT, bool VISC>

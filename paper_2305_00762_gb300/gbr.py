@@ -68,6 +68,18 @@ def load():
         "gbr_get_timing": (ip, [vp, ctypes.POINTER(dp), ctypes.POINTER(ip), ctypes.POINTER(ip)]),
         "gbr_sync": (ip, [vp]),
         "gbr_step_static": (ip, [vp, vp, ip, ip, dp, dp, dp, ctypes.POINTER(gbr_bc), dp, vp]),
+        "gbr_batch_create": (ip, [ip, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(dp),
+                                  ctypes.POINTER(dp), ctypes.POINTER(ip), dp, ctypes.POINTER(vp)]),
+        "gbr_batch_destroy": (ip, [vp]),
+        "gbr_batch_set_stream": (ip, [vp, vp]),
+        "gbr_batch_set_option": (ip, [vp, ip, dp]),
+        "gbr_batch_set_state": (ip, [vp, ip, vp, ip]),
+        "gbr_batch_get_state": (ip, [vp, ip, vp, ip]),
+        "gbr_batch_set_end_times": (ip, [vp, ctypes.POINTER(dp)]),
+        "gbr_batch_step_cfl": (ip, [vp, dp, ip]),
+        "gbr_batch_get_times": (ip, [vp, ctypes.POINTER(dp), ctypes.POINTER(dp)]),
+        "gbr_batch_autotune": (ip, [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip)]),
+        "gbr_batch_sync": (ip, [vp]),
         "gbr_error_string": (ctypes.c_char_p, [ip]),
     }
     for name, (res, args) in sig.items():
@@ -291,3 +303,79 @@ class Solver:
 
     def sync(self, allow=()):
         return gbr_sync(self.ctx, allow)
+
+
+class Batch:
+    """Owner of one gbr batch of independent grids (marshalling only)."""
+
+    def __init__(self, cases, precision=64, stream=None):
+        L = load()
+        n = len(cases)
+        self.shapes = [(c.nx, c.ny) for c in cases]
+        arr = lambda t, v: (t * len(v))(*v)
+        nx = arr(ctypes.c_int, [c.nx for c in cases])
+        ny = arr(ctypes.c_int, [c.ny for c in cases])
+        dx = arr(ctypes.c_double, [c.dx for c in cases])
+        dy = arr(ctypes.c_double, [c.dy for c in cases])
+        bc = arr(ctypes.c_int, [int(k) for c in cases for k in c.bc])
+        gamma = cases[0].gamma
+        if any(c.gamma != gamma for c in cases) or any(c.mu != 0.0 for c in cases):
+            raise ValueError("a batch shares one gamma and is inviscid")
+        self.b = ctypes.c_void_p()
+        _check(L.gbr_batch_create(n, nx, ny, dx, dy, bc, float(gamma), ctypes.byref(self.b)), "gbr_batch_create")
+        self.n = n
+        if stream is not None:
+            _check(L.gbr_batch_set_stream(self.b, ctypes.c_void_p(int(stream))), "gbr_batch_set_stream")
+        if precision != 64:
+            self.set_option(GBR_OPT_PRECISION, precision)
+
+    def set_option(self, key, val):
+        _check(load().gbr_batch_set_option(self.b, int(key), float(val)), "gbr_batch_set_option")
+
+    def close(self):
+        if self.b is not None and self.b.value:
+            load().gbr_batch_destroy(self.b)
+        self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, k, Q):
+        nx, ny = self.shapes[k]
+        _expect(Q, "float64", (4, ny, nx))
+        p, dev = _ptr(Q)
+        _check(load().gbr_batch_set_state(self.b, int(k), p, dev), "gbr_batch_set_state")
+
+    def get_state(self, k, out=None):
+        nx, ny = self.shapes[k]
+        if out is None:
+            out = np.empty((4, ny, nx))
+        _expect(out, "float64", (4, ny, nx))
+        p, dev = _ptr(out)
+        _check(load().gbr_batch_get_state(self.b, int(k), p, dev), "gbr_batch_get_state")
+        return out
+
+    def set_end_times(self, t_end):
+        a = (ctypes.c_double * self.n)(*[float(x) for x in t_end])
+        _check(load().gbr_batch_set_end_times(self.b, a), "gbr_batch_set_end_times")
+
+    def step_cfl(self, cfl, nsteps=1):
+        _check(load().gbr_batch_step_cfl(self.b, float(cfl), int(nsteps)), "gbr_batch_step_cfl")
+
+    def times(self, allow=()):
+        t = (ctypes.c_double * self.n)()
+        dt = (ctypes.c_double * self.n)()
+        _check(load().gbr_batch_get_times(self.b, t, dt), "gbr_batch_get_times", allow)
+        return np.array(t[:]), np.array(dt[:])
+
+    def autotune(self, trials=3):
+        c, bx, by = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().gbr_batch_autotune(self.b, int(trials), ctypes.byref(c), ctypes.byref(bx), ctypes.byref(by)),
+               "gbr_batch_autotune")
+        return c.value, (bx.value, by.value)
+
+    def sync(self, allow=()):
+        return _check(load().gbr_batch_sync(self.b), "gbr_batch_sync", allow)

@@ -1,0 +1,127 @@
+"""Batched ensemble: many independent grids of uneven size stepped by one
+persistent kernel per RK stage, replayed from a CUDA graph, each grid at its
+own device-side dt. The FP64 batch must reproduce single-grid runs bitwise
+(same tile body, same dt) and the oracle to 1e-12; the FP32 batch is held to
+the density-L1 gate against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_2305_00762_gb300 import cases as C
+
+from .parity import TOL64, assert_state_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle as O
+    from paper_2305_00762_gb300 import build, gbr
+    build.build()
+    O.build()
+    gbr.load()
+    return torch, O, gbr
+
+
+def small_ensemble():
+    rng = np.random.default_rng(762)
+    return [
+        C.isentropic_vortex(48, eps=float(rng.uniform(1, 5))),
+        C.kelvin_helmholtz(40, rng, ny=56),
+        C.riemann_2d(64, 40),
+        C.isentropic_vortex(37, 51, eps=float(rng.uniform(1, 5))),
+        C.kelvin_helmholtz(64, rng),
+    ]
+
+
+def cfg_of(O, c):
+    return O.Config(c.nx, c.ny, c.dx, c.dy, c.gamma, c.mu, c.Pr, c.bc)
+
+
+def test_batch_fp64_equals_single_grids_and_oracle(env):
+    torch, O, gbr = env
+    ens = small_ensemble()
+    b = gbr.Batch(ens)
+    singles = []
+    for k, c in enumerate(ens):
+        b.set_state(k, c.Q)
+        s = gbr.Solver.for_case(c)
+        s.set_state(c.Q)
+        singles.append(s)
+    Qo = [c.Q.copy() for c in ens]
+    for step in range(4):
+        b.step_cfl(0.5, 1)
+        t, dt = b.times()
+        for k, c in enumerate(ens):
+            lam = O.max_wavespeed(cfg_of(O, c), Qo[k])
+            assert abs(dt[k] - 0.5 / lam) <= 1e-14 * dt[k]      # own dt per grid
+            singles[k].step(dt[k])
+            Qo[k], rc = O.rk3_step(cfg_of(O, c), Qo[k], dt[k])
+            assert rc == 0
+    assert len(set(np.round(dt, 12))) > 1                      # the dts differ
+    for k, c in enumerate(ens):
+        Qb = b.get_state(k)
+        assert np.array_equal(Qb, singles[k].get_state()), k
+        assert_state_close(Qb, Qo[k], TOL64 * 4, what=f"batch case {k}")
+        singles[k].close()
+    b.close()
+
+
+def test_graph_replay_and_autotune_are_bitwise_neutral(env):
+    torch, O, gbr = env
+    ens = small_ensemble()
+    a, b = gbr.Batch(ens), gbr.Batch(ens)
+    for k, c in enumerate(ens):
+        a.set_state(k, c.Q)
+        b.set_state(k, c.Q)
+    choice, shape = b.autotune(trials=2)
+    assert choice in (0, 1, 2) and shape[0] > 0
+    for _ in range(6):
+        a.step_cfl(0.5, 1)
+    b.step_cfl(0.5, 3)
+    b.step_cfl(0.5, 3)
+    for k in range(len(ens)):
+        assert np.array_equal(a.get_state(k), b.get_state(k)), k
+    ta, _ = a.times()
+    tb, _ = b.times()
+    assert np.array_equal(ta, tb)
+    a.close()
+    b.close()
+
+
+def test_end_times_stop_each_grid(env):
+    torch, O, gbr = env
+    ens = small_ensemble()
+    b = gbr.Batch(ens)
+    for k, c in enumerate(ens):
+        b.set_state(k, c.Q)
+    t_end = [0.01, 0.02, 1e-3, 0.015, 0.0]
+    b.set_end_times(t_end)
+    b.step_cfl(0.5, 40)
+    t, dt = b.times()
+    assert np.allclose(t, t_end, rtol=0, atol=1e-15)
+    assert np.array_equal(b.get_state(4), ens[4].Q)   # t_end = 0: untouched
+    b.close()
+
+
+def test_batch_fp32_density_l1(env):
+    torch, O, gbr = env
+    ens = small_ensemble()
+    b = gbr.Batch(ens, precision=32)
+    for k, c in enumerate(ens):
+        b.set_state(k, c.Q)
+    Qo = [c.Q.copy() for c in ens]
+    for _ in range(20):
+        b.step_cfl(0.5, 1)
+        _, dt = b.times()
+        for k, c in enumerate(ens):
+            Qo[k], rc = O.rk3_step(cfg_of(O, c), Qo[k], dt[k])
+            assert rc == 0
+    for k, c in enumerate(ens):
+        err = np.abs(b.get_state(k)[0] - Qo[k][0]).sum() / np.abs(Qo[k][0]).sum()
+        print(f"batch FP32 case {k} ({c.name} {c.nx}x{c.ny}): density L1 rel err {err:.3e}")
+        assert err <= 1e-5
+    b.close()
