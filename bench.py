@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", choices=["gbr", "reference"], default="gbr")
     ap.add_argument("--n", type=int, default=N_DEFAULT, help="grid size (cells per side)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--ensemble-cases", type=int, default=64)
     return ap.parse_args()
 
 
@@ -201,6 +203,39 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ensemble(args, torch, gbr, cases, st):
+    """The batched form: the seeded ensemble of independent vortex / shear
+    layer grids (sizes from {256^2, 512^2, 1024^2, 2048^2}), FP32 arithmetic,
+    autotuned tile shape, every step replayed from one CUDA graph. The states
+    (about 2.8 GB for 64 grids) exceed L2, so no flush is needed."""
+    table = cases.ensemble(args.ensemble_cases)
+    ens = [cases.make_ensemble_case(kind, n, prm) for kind, n, prm in table]
+    b = gbr.Batch(ens, precision=32, stream=st.cuda_stream)
+    for k, c in enumerate(ens):
+        b.set_state(k, torch.from_numpy(c.Q).cuda())
+    del ens
+    choice, shape = b.autotune(trials=3)
+    b.step_cfl(CFL, args.warmup)
+    b.step_cfl(CFL, args.steps)   # capture now, replay below
+    b.sync()
+    cells = sum(n * n for _, n, _ in table)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    b.step_cfl(CFL, args.steps)
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    rc = b.sync(allow=(gbr.GBR_ERR_NONPHYSICAL,))
+    t, dt = b.times(allow=(gbr.GBR_ERR_NONPHYSICAL,))
+    b.close()
+    return {"value": 3.0 * cells * args.steps / (ms * 1e-3), "unit": METRIC, "grids": len(table),
+            "cells": cells, "ms_per_step": ms / args.steps, "precision": "fp32",
+            "tile": list(shape), "graph": True, "dt_min": float(dt.min()), "dt_max": float(dt.max()),
+            "status": gbr.error_string(rc),
+            "sizes": {str(n): sum(1 for _, m, _ in table if m == n) for n in (256, 512, 1024, 2048)}}
+
+
 def time_steps(torch, solver, steps, flush):
     """Device time of `steps` RK3 steps, L2 flushed between steps (outside
     the events); per-step events on the library's stream."""
@@ -333,6 +368,8 @@ def main():
         "clocks": r64["clocks"],
         "status": gbr.error_string(r64["status"]),
     }
+    if not args.no_ensemble:
+        line["ensemble"] = run_ensemble(args, torch, gbr, cases, st)
     if not args.no_cpu_baseline:
         mid = cases.Case(case.name, start_host, case.dx, case.dy, case.gamma, case.mu, case.Pr, case.bc)
         line["cpu_baseline"] = cpu_baseline(mid)
