@@ -83,8 +83,9 @@ typedef enum {
      * or stage evaluation (read back with gbr_get_flags); 0: off (default). */
     GBR_OPT_RECORD_FLAGS = 1,
     /* Discontinuity sensor: 0 = the density detector of Sec. 2.4 (default);
-     * 1 = the learned sensor (requires gbr_set_sensor_weights and
-     * precision 32), with the density detector as fallback. */
+     * 1 = the learned sensor (needs gbr_set_sensor_weights first, else
+     * GBR_ERR_STATE; used in precision 32 only), with the density detector as
+     * fallback. */
     GBR_OPT_SENSOR = 2,
     /* 1: bracket every kernel launch with CUDA events on the context's
      * stream (read back with gbr_get_timing); 0: off (default). */
@@ -171,6 +172,46 @@ int gbr_get_flags(gbr_ctx *ctx, unsigned char *sigx, unsigned char *sigy, int on
  * later ones are counted in launches[] but not timed (*dropped > 0). */
 int gbr_get_timing(gbr_ctx *ctx, double *ms, int *launches, int *dropped);
 
+/* ----------------------------------------------------------------------
+ * Learned discontinuity sensor. A perceptron 50 -> 32 -> 32 -> 1 (ReLU, ReLU,
+ * sigmoid) on the 5 x 5 stencil of density and pressure differences of a
+ * cell, each field divided by (its largest absolute difference + 1e-3),
+ * replaces the per-cell density-detector test of Sec. 2.4 (Eq. detector) in
+ * the FP32 form: output > 0.7 marks a discontinuity, < 0.3 smooth flow, and
+ * in between the plain detector decides (per direction). The buffer of
+ * Eq. buffer is unchanged. The network runs on the tensor cores with BF16
+ * operands and FP32 accumulation, fused into the stage kernel.
+ * Weight vector (GBR_SENSOR_PARAMS floats): W1[50][32], b1[32], W2[32][32],
+ * b2[32], w3[32], b3, with h1 = relu(x W1 + b1) rounded to BF16,
+ * h2 = relu(h1 W2 + b2), p = 1/(1 + exp(-(h2 . w3 + b3))).
+ * ---------------------------------------------------------------------- */
+#define GBR_SENSOR_PARAMS 2721
+
+/* Load sensor weights (host array of n = GBR_SENSOR_PARAMS floats). Enable
+ * them with gbr_set_option(ctx, GBR_OPT_SENSOR, 1) (FP32 precision). */
+int gbr_set_sensor_weights(gbr_ctx *ctx, const float *w, int n);
+
+/* Network output p per interior cell of the current state ([ny][nx] float32),
+ * computed from FP32 primitives exactly as the fused stage kernel does. */
+int gbr_sensor_eval(gbr_ctx *ctx, float *prob, int on_device);
+
+/* Training data from the current state (device buffers): features[ny*nx][64]
+ * BF16 (row-major cells, zero-padded past 50) and labels[ny*nx] = 1 where the
+ * plain detector marks the cell (psi_x < 0.5 or psi_y < 0.5, FP64). Either
+ * may be NULL. Asynchronous. */
+int gbr_sensor_dataset(gbr_ctx *ctx, void *features, unsigned char *labels);
+
+/* Train the sensor on n samples (device buffers as written by
+ * gbr_sensor_dataset): `steps` Adam steps (learning rate lr) on mini-batches
+ * of `batch` samples drawn with replacement by a counter-based hash of
+ * (seed, step, slot); binary cross-entropy with label-1 samples weighted by
+ * pos_weight; BF16 operands, FP32 accumulation. w (host, GBR_SENSOR_PARAMS
+ * floats) holds the initial weights on entry and the trained ones on return;
+ * loss (host, `steps` floats, may be NULL) receives each step's summed loss.
+ * Allocates temporary device memory; synchronises `stream`. */
+int gbr_sensor_train(const void *features, const unsigned char *labels, long long n, int steps, int batch,
+                     double lr, double pos_weight, unsigned long long seed, float *w, float *loss, void *stream);
+
 /* Wait for the context's stream and report pending device errors. */
 int gbr_sync(gbr_ctx *ctx);
 
@@ -199,7 +240,8 @@ int gbr_batch_destroy(gbr_batch *b);
 /* Issue all later work of the batch on `stream` (NULL = legacy default). */
 int gbr_batch_set_stream(gbr_batch *b, void *stream);
 
-/* GBR_OPT_PRECISION (64 or 32, as for a single grid) or GBR_OPT_TIMING. */
+/* GBR_OPT_PRECISION (64 or 32, as for a single grid), GBR_OPT_SENSOR or
+ * GBR_OPT_TIMING. */
 int gbr_batch_set_option(gbr_batch *b, int key, double val);
 
 /* Set grid k's state ([4][ny_k][nx_k] float64); resets its time to 0 and
@@ -229,6 +271,10 @@ int gbr_batch_get_times(gbr_batch *b, double *t, double *dt);
  * states untouched) and keep the fastest; *choice (may be NULL) receives its
  * index and *bx, *by (may be NULL) its shape. */
 int gbr_batch_autotune(gbr_batch *b, int trials, int *choice, int *bx, int *by);
+
+/* Sensor weights of the batch (as gbr_set_sensor_weights); enable with
+ * gbr_batch_set_option(b, GBR_OPT_SENSOR, 1) in FP32 precision. */
+int gbr_batch_set_sensor_weights(gbr_batch *b, const float *w, int n);
 
 /* Wait for the batch's stream; reports pending device errors. */
 int gbr_batch_sync(gbr_batch *b);

@@ -22,7 +22,7 @@ import ctypes
 import os
 import subprocess
 import threading
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 
@@ -96,6 +96,8 @@ def lib():
             L.or_max_wavespeed.argtypes = [cp, dp]
             L.or_fill_ghosts_padded.restype = ctypes.c_int
             L.or_fill_ghosts_padded.argtypes = [cp, dp]
+            L.or_trouble_labels.restype = ctypes.c_int
+            L.or_trouble_labels.argtypes = [cp, dp, u8]
             L.or_num_threads.restype = ctypes.c_int
             L.or_set_num_threads.argtypes = [ctypes.c_int]
             _lib = L
@@ -235,6 +237,16 @@ def fill_ghosts_padded(cfg: Config, Qp) -> np.ndarray:
     if rc != 0:
         raise RuntimeError(f"oracle ghost fill failed: {rc}")
     return Qp
+
+
+def trouble_labels(cfg: Config, Q) -> np.ndarray:
+    """Plain-detector label per interior cell: psi_x < 0.5 or psi_y < 0.5."""
+    Q = _state(cfg, Q)
+    out = np.zeros((cfg.ny, cfg.nx), np.uint8)
+    rc = lib().or_trouble_labels(ctypes.byref(cfg.c()), _dp(Q), _u8(out))
+    if rc != 0:
+        raise RuntimeError(f"oracle labels failed: {rc}")
+    return out
 
 
 def num_threads() -> int:

@@ -706,6 +706,38 @@ double or_max_wavespeed(const or_cfg *c, const double *Q)
     return lam;
 }
 
+/* Training labels of the learned sensor: label[i][j] = 1 if the density
+ * detector (Eq. detector with reading R4) marks interior cell (j, i) in x or
+ * in y, i.e. psi_x < 0.5 or psi_y < 0.5 (the per-cell test before the buffer
+ * of Eq. buffer). Q: interior state [4][ny][nx]. */
+int or_trouble_labels(const or_cfg *c, const double *Q, unsigned char *label)
+{
+    if (!cfg_ok(c) || !Q || !label)
+        return OR_ERR_ARG;
+    const int nx = c->nx, ny = c->ny, W = nx + 2 * OR_G;
+    const ptrdiff_t N = (ptrdiff_t)W * (ny + 2 * OR_G);
+    double *Qp = (double *)malloc(sizeof(double) * 4 * N);
+    if (!Qp)
+        return OR_ERR_NOMEM;
+    for (int m = 0; m < 4; ++m)
+        for (int i = 0; i < ny; ++i)
+            for (int j = 0; j < nx; ++j)
+                Qp[m * N + pidx(c, j, i)] = Q[((size_t)m * ny + i) * nx + j];
+    or_fill_ghosts(c, Qp);
+    for (int i = 0; i < ny; ++i) {
+        for (int j = 0; j < nx; ++j) {
+            double rx[5], ry[5];
+            for (int l = 0; l < 5; ++l) {
+                rx[l] = Qp[pidx(c, j + l - 2, i)];
+                ry[l] = Qp[pidx(c, j, i + l - 2)];
+            }
+            label[(size_t)i * nx + j] = (or_psi(rx) < 0.5 || or_psi(ry) < 0.5) ? 1 : 0;
+        }
+    }
+    free(Qp);
+    return OR_OK;
+}
+
 /* Pin helper: fill ghosts of a padded state given as 4 planes of
  * (nx+2G) x (ny+2G) (exported so tests can check the boundary conditions). */
 int or_fill_ghosts_padded(const or_cfg *c, double *Qp)

@@ -8,6 +8,7 @@
 #include "../../include/gbr.h"
 #include "ghost.cuh"
 #include "gbr_internal.h"
+#include "sensor.cuh"
 
 using namespace gbr;
 
@@ -29,7 +30,10 @@ struct gbr_batch {
     cudaGraphExec_t graph;
     int g_nsteps, g_precision, g_shape;
     double g_cfl;
+    int g_sensor;
     int timing;
+    SensorDev* d_sensor;      // learned-sensor weights (null until set)
+    int sensor;               // 1: use them (FP32 only)
 };
 
 namespace {
@@ -90,10 +94,13 @@ int upload(gbr_batch* b)
     return GBR_OK;
 }
 
+const SensorDev* sensor_of(gbr_batch* b) { return (b->precision == 32 && b->sensor) ? b->d_sensor : nullptr; }
+
 int stage(gbr_batch* b, int k, cudaStream_t s)
 {
-    cudaError_t e = b->precision == 32 ? launch_batch_stage_f32(b->shape, b->d_cases, b->n, b->total_tiles, k, s)
-                                       : launch_batch_stage_f64(b->shape, b->d_cases, b->n, b->total_tiles, k, s);
+    cudaError_t e = b->precision == 32
+                        ? launch_batch_stage_f32(b->shape, b->d_cases, b->n, b->total_tiles, k, s, sensor_of(b))
+                        : launch_batch_stage_f64(b->shape, b->d_cases, b->n, b->total_tiles, k, s);
     return st(e);
 }
 
@@ -206,6 +213,7 @@ int gbr_batch_destroy(gbr_batch* b)
     cudaFree(b->pool);
     cudaFree(b->d_scal);
     cudaFree(b->d_cases);
+    cudaFree(b->d_sensor);
     cudaGetLastError();
     delete b;
     return GBR_OK;
@@ -228,6 +236,12 @@ int gbr_batch_set_option(gbr_batch* b, int key, double val)
             b->shape = 0;
             retile(b);
         }
+        return GBR_OK;
+    }
+    if (key == GBR_OPT_SENSOR) {
+        if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;
+        if (val == 1.0 && !b->d_sensor) return GBR_ERR_STATE;
+        b->sensor = (int)val;
         return GBR_OK;
     }
     if (key == GBR_OPT_TIMING) {
@@ -285,11 +299,11 @@ int gbr_batch_step_cfl(gbr_batch* b, double cfl, int nsteps)
     int rc = upload(b);
     if (rc != GBR_OK) return rc;
     if (!b->graph || b->g_nsteps != nsteps || b->g_cfl != cfl || b->g_precision != b->precision ||
-        b->g_shape != b->shape) {
+        b->g_shape != b->shape || b->g_sensor != (sensor_of(b) != nullptr)) {
         drop_graph(b);
         // first-use kernel setup outside the capture (a negative tile count
         // prepares the persistent kernel without launching it)
-        TRY(b->precision == 32 ? launch_batch_stage_f32(b->shape, b->d_cases, b->n, -1, 0, b->stream)
+        TRY(b->precision == 32 ? launch_batch_stage_f32(b->shape, b->d_cases, b->n, -1, 0, b->stream, sensor_of(b))
                                : launch_batch_stage_f64(b->shape, b->d_cases, b->n, -1, 0, b->stream));
         // The descriptors must be on the device before the capture stream
         // replays anything: order the capture stream after the caller's.
@@ -314,6 +328,7 @@ int gbr_batch_step_cfl(gbr_batch* b, double cfl, int nsteps)
         b->g_cfl = cfl;
         b->g_precision = b->precision;
         b->g_shape = b->shape;
+        b->g_sensor = sensor_of(b) != nullptr;
     }
     return st(cudaGraphLaunch(b->graph, b->stream));
 }
@@ -387,6 +402,18 @@ int gbr_batch_autotune(gbr_batch* b, int trials, int* choice, int* bx, int* by)
     if (bx) *bx = sh[best].bx;
     if (by) *by = sh[best].by;
     return rc;
+}
+
+int gbr_batch_set_sensor_weights(gbr_batch* b, const float* w, int n)
+{
+    if (!b || !w || n != kSensorParams) return GBR_ERR_ARG;
+    DeviceGuard dg(b->device);
+    SensorDev h;
+    pack_sensor(w, &h);
+    if (!b->d_sensor) TRY(cudaMalloc(&b->d_sensor, sizeof(SensorDev)));
+    TRY(cudaMemcpyAsync(b->d_sensor, &h, sizeof(SensorDev), cudaMemcpyHostToDevice, b->stream));
+    TRY(cudaStreamSynchronize(b->stream));
+    return GBR_OK;
 }
 
 int gbr_batch_sync(gbr_batch* b)

@@ -13,8 +13,15 @@ int batch_tile_shapes_f32(const TileShape** shapes)
 }
 
 cudaError_t launch_batch_stage_f32(int shape, const BatchCase* cases, int ncases, int total_tiles, int stage,
-                                   cudaStream_t s)
+                                   cudaStream_t s, const SensorDev* sensor)
 {
+    if (sensor) {
+        switch (shape) {
+        case 0: return launch_batch_t<float, 32, 16, 256, true>(cases, ncases, total_tiles, stage, s, sensor);
+        case 1: return launch_batch_t<float, 32, 8, 256, true>(cases, ncases, total_tiles, stage, s, sensor);
+        default: return launch_batch_t<float, 64, 8, 256, true>(cases, ncases, total_tiles, stage, s, sensor);
+        }
+    }
     switch (shape) {
     case 0: return launch_batch_t<float, 32, 16, 256>(cases, ncases, total_tiles, stage, s);
     case 1: return launch_batch_t<float, 32, 8, 256>(cases, ncases, total_tiles, stage, s);

@@ -20,9 +20,9 @@ __device__ __forceinline__ int batch_case_of(const BatchCase* cases, int ncases,
     return lo;
 }
 
-template <typename T, int BX, int BY, int NT>
+template <typename T, int BX, int BY, int NT, bool LEARNED>
 __global__ void __launch_bounds__(NT) batch_stage_kernel(const BatchCase* __restrict__ cases, int ncases,
-                                                         int total_tiles, int stage)
+                                                         int total_tiles, int stage, const SensorDev* sensor)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const double ca = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
@@ -48,21 +48,22 @@ __global__ void __launch_bounds__(NT) batch_stage_kernel(const BatchCase* __rest
         P.ca = ca;
         P.cb = cbc;
         P.cc = cbc;
-        stage_tile<T, BX, BY, NT, false>(P, tx * BX, ty * BY, smem_raw);
+        P.sensor = sensor;
+        stage_tile<T, BX, BY, NT, false, LEARNED>(P, tx * BX, ty * BY, smem_raw);
     }
 }
 
 // Persistent grid size: resident CTAs per SM x SMs (computed once; the first
 // call also raises the kernel's dynamic shared-memory limit, so it must
 // happen outside stream capture).
-template <typename T, int BX, int BY, int NT>
+template <typename T, int BX, int BY, int NT, bool LEARNED>
 cudaError_t batch_blocks(int* out)
 {
     using L = TileLayout<BX, BY, false>;
-    constexpr size_t smem = L::template bytes<T>();
+    constexpr size_t smem = L::template total_bytes<T, LEARNED>();
     static int blocks = 0;
     if (blocks == 0) {
-        auto kern = batch_stage_kernel<T, BX, BY, NT>;
+        auto kern = batch_stage_kernel<T, BX, BY, NT, LEARNED>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0, dev = 0, sms = 0;
@@ -76,16 +77,17 @@ cudaError_t batch_blocks(int* out)
 }
 
 // total_tiles < 0: only prepare the kernel (batch_blocks), launch nothing.
-template <typename T, int BX, int BY, int NT>
-cudaError_t launch_batch_t(const BatchCase* cases, int ncases, int total_tiles, int stage, cudaStream_t s)
+template <typename T, int BX, int BY, int NT, bool LEARNED = false>
+cudaError_t launch_batch_t(const BatchCase* cases, int ncases, int total_tiles, int stage, cudaStream_t s,
+                           const SensorDev* sensor = nullptr)
 {
     using L = TileLayout<BX, BY, false>;
-    constexpr size_t smem = L::template bytes<T>();
+    constexpr size_t smem = L::template total_bytes<T, LEARNED>();
     int blocks = 0;
-    cudaError_t e = batch_blocks<T, BX, BY, NT>(&blocks);
+    cudaError_t e = batch_blocks<T, BX, BY, NT, LEARNED>(&blocks);
     if (e != cudaSuccess || total_tiles <= 0) return e;
     const int grid = total_tiles < blocks ? total_tiles : blocks;
-    batch_stage_kernel<T, BX, BY, NT><<<grid, NT, smem, s>>>(cases, ncases, total_tiles, stage);
+    batch_stage_kernel<T, BX, BY, NT, LEARNED><<<grid, NT, smem, s>>>(cases, ncases, total_tiles, stage, sensor);
     return cudaGetLastError();
 }
 

@@ -9,6 +9,7 @@
 
 #include "../../include/gbr.h"
 #include "gbr_internal.h"
+#include "sensor.cuh"
 
 using namespace gbr;
 
@@ -37,6 +38,9 @@ struct gbr_ctx {
     int ev_used;
     int launches[GBR_KERNEL_CLASSES];
     int dropped;
+    // learned sensor
+    SensorDev* d_sensor;
+    float* prob;   // per-cell sensor output scratch
 };
 
 namespace {
@@ -158,6 +162,7 @@ StageParams stage_params(gbr_ctx* c, const double* q)
     p.err = &c->ds->err;
     p.sigx = c->record_flags ? c->sigx : nullptr;
     p.sigy = c->record_flags ? c->sigy : nullptr;
+    p.sensor = (c->sensor && c->precision == 32) ? c->d_sensor : nullptr;
     return p;
 }
 
@@ -268,6 +273,8 @@ int gbr_destroy(gbr_ctx* c)
     cudaFree(c->sigx);
     cudaFree(c->sigy);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    cudaFree(c->d_sensor);
+    cudaFree(c->prob);
     cudaGetLastError();
     delete c;
     return GBR_OK;
@@ -392,8 +399,8 @@ int gbr_set_option(gbr_ctx* c, int key, double val)
         return GBR_OK;
     case GBR_OPT_SENSOR:
         if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;
-        if (val == 1.0) return GBR_ERR_UNSUPPORTED;
-        c->sensor = 0;
+        if (val == 1.0 && !c->d_sensor) return GBR_ERR_STATE;
+        c->sensor = (int)val;
         return GBR_OK;
     case GBR_OPT_TIMING:
         if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;
@@ -438,6 +445,81 @@ int gbr_get_flags(gbr_ctx* c, unsigned char* sigx, unsigned char* sigy, int on_d
     GBR_TRY(cudaMemcpyAsync(sigy, c->sigy, (size_t)(c->g.ny + 1) * c->g.nx, k, c->stream));
     if (!on_device) GBR_TRY(cudaStreamSynchronize(c->stream));
     return GBR_OK;
+}
+
+int gbr_set_sensor_weights(gbr_ctx* c, const float* w, int n)
+{
+    if (!c || !w || n != kSensorParams) return GBR_ERR_ARG;
+    DeviceGuard dg(c->device);
+    SensorDev h;
+    pack_sensor(w, &h);
+    if (!c->d_sensor) GBR_TRY(cudaMalloc(&c->d_sensor, sizeof(SensorDev)));
+    GBR_TRY(cudaMemcpyAsync(c->d_sensor, &h, sizeof(SensorDev), cudaMemcpyHostToDevice, c->stream));
+    GBR_TRY(cudaStreamSynchronize(c->stream));
+    return GBR_OK;
+}
+
+int gbr_sensor_eval(gbr_ctx* c, float* prob, int on_device)
+{
+    if (!c || !prob) return GBR_ERR_ARG;
+    if (!c->have_state || !c->d_sensor) return GBR_ERR_STATE;
+    DeviceGuard dg(c->device);
+    int rc = ghosts(c, c->Qn, 0, 0, 0, 0);
+    if (rc != GBR_OK) return rc;
+    const size_t n = (size_t)c->g.nx * c->g.ny;
+    float* out = prob;
+    if (!on_device) {
+        if (!c->prob) GBR_TRY(cudaMalloc(&c->prob, sizeof(float) * n));
+        out = c->prob;
+    }
+    GBR_TRY(launch_sensor_tile(c->g, c->ph.gamma, c->Qn, c->d_sensor, out, nullptr, nullptr, c->stream));
+    if (!on_device) {
+        GBR_TRY(cudaMemcpyAsync(prob, c->prob, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
+        GBR_TRY(cudaStreamSynchronize(c->stream));
+    }
+    return GBR_OK;
+}
+
+int gbr_sensor_dataset(gbr_ctx* c, void* features, unsigned char* labels)
+{
+    if (!c || (!features && !labels)) return GBR_ERR_ARG;
+    if (!c->have_state) return GBR_ERR_STATE;
+    DeviceGuard dg(c->device);
+    int rc = ghosts(c, c->Qn, 0, 0, 0, 0);
+    if (rc != GBR_OK) return rc;
+    return cuda_status(launch_sensor_tile(c->g, c->ph.gamma, c->Qn, nullptr, nullptr, features, labels, c->stream));
+}
+
+int gbr_sensor_train(const void* features, const unsigned char* labels, long long n, int steps, int batch,
+                     double lr, double pos_weight, unsigned long long seed, float* w, float* loss, void* stream)
+{
+    if (!features || !labels || !w || n < 1 || steps < 1 || batch < 1 || !(lr > 0.0) || !(pos_weight > 0.0))
+        return GBR_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    float *dw = nullptr, *dg = nullptr, *dm = nullptr, *dv = nullptr, *dl = nullptr;
+    const size_t pb = sizeof(float) * kSensorParams;
+    int rc = cuda_status(cudaMalloc(&dw, pb));
+    if (rc == GBR_OK) rc = cuda_status(cudaMalloc(&dg, pb));
+    if (rc == GBR_OK) rc = cuda_status(cudaMalloc(&dm, pb));
+    if (rc == GBR_OK) rc = cuda_status(cudaMalloc(&dv, pb));
+    if (rc == GBR_OK) rc = cuda_status(cudaMalloc(&dl, sizeof(float) * steps));
+    if (rc == GBR_OK) rc = cuda_status(cudaMemcpyAsync(dw, w, pb, cudaMemcpyHostToDevice, s));
+    if (rc == GBR_OK) rc = cuda_status(cudaMemsetAsync(dg, 0, pb, s));
+    if (rc == GBR_OK) rc = cuda_status(cudaMemsetAsync(dm, 0, pb, s));
+    if (rc == GBR_OK) rc = cuda_status(cudaMemsetAsync(dv, 0, pb, s));
+    if (rc == GBR_OK) rc = cuda_status(cudaMemsetAsync(dl, 0, sizeof(float) * steps, s));
+    if (rc == GBR_OK)
+        rc = cuda_status(launch_sensor_train(features, labels, n, steps, batch, (float)lr, (float)pos_weight, seed,
+                                             dw, dg, dm, dv, dl, s));
+    if (rc == GBR_OK) rc = cuda_status(cudaMemcpyAsync(w, dw, pb, cudaMemcpyDeviceToHost, s));
+    if (rc == GBR_OK && loss) rc = cuda_status(cudaMemcpyAsync(loss, dl, sizeof(float) * steps, cudaMemcpyDeviceToHost, s));
+    if (rc == GBR_OK) rc = cuda_status(cudaStreamSynchronize(s));
+    cudaFree(dw);
+    cudaFree(dg);
+    cudaFree(dm);
+    cudaFree(dv);
+    cudaFree(dl);
+    return rc;
 }
 
 int gbr_sync(gbr_ctx* c)

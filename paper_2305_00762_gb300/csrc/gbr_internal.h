@@ -30,6 +30,8 @@ struct Physics {
     double gamma, mu, Pr, dx, dy;
 };
 
+struct SensorDev;
+
 // One fused residual (+ stage update) pass, Secs. 2.1-2.5.
 struct StageParams {
     Grid g;
@@ -45,6 +47,7 @@ struct StageParams {
     const double* dt_ptr;    // device dt (used when non-null)
     double dt;               // host dt otherwise
     double ca, cb, cc;       // qout = ca * qn + cb * q + cc * dt * Res
+    const SensorDev* sensor; // learned-sensor weights (FP32 form) or nullptr
 };
 
 // Ghost fill of one padded state, plus the per-step scalar bookkeeping done
@@ -92,7 +95,15 @@ int batch_tile_shapes_f32(const TileShape** shapes);
 cudaError_t launch_batch_stage_f64(int shape, const BatchCase* cases, int ncases, int total_tiles, int stage,
                                    cudaStream_t s);
 cudaError_t launch_batch_stage_f32(int shape, const BatchCase* cases, int ncases, int total_tiles, int stage,
-                                   cudaStream_t s);
+                                   cudaStream_t s, const SensorDev* sensor = nullptr);
+// Learned sensor (sensor.cu): host packing of the weight vector, per-cell
+// evaluation / dataset extraction on a padded state, training.
+void pack_sensor(const float* w, SensorDev* out);
+cudaError_t launch_sensor_tile(const Grid& g, double gamma, const double* q, const SensorDev* w, float* prob,
+                               void* feat_bf16, unsigned char* label, cudaStream_t s);
+cudaError_t launch_sensor_train(const void* X_bf16, const unsigned char* y, long long n, int steps, int batch,
+                                float lr, float pos_weight, unsigned long long seed, float* w, float* grad, float* m,
+                                float* v, float* loss, cudaStream_t s);
 cudaError_t launch_wavespeed(const Grid& g, const Physics& ph, const double* q,
                              unsigned long long* lam, cudaStream_t s);
 cudaError_t launch_stage_f64(const StageParams& p, cudaStream_t s);

@@ -1,0 +1,340 @@
+// Learned discontinuity sensor: per-cell evaluation and dataset extraction on
+// a padded state, and the hand-written training kernels (BF16 operands, FP32
+// accumulation, binary cross-entropy, Adam).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include "gbr_internal.h"
+#include "sensor.cuh"
+#include "stage_kernel.cuh"
+
+namespace gbr {
+
+// ---------------------------------------------------------------------------
+// Weight packing (host): W1[50][32], b1[32], W2[32][32], b2[32], w3[32], b3.
+// ---------------------------------------------------------------------------
+void pack_sensor(const float* w, SensorDev* out)
+{
+    memset(out, 0, sizeof(*out));
+    const float* W1 = w;
+    const float* b1 = W1 + kSensorIn * kSensorH;
+    const float* W2 = b1 + kSensorH;
+    const float* b2 = W2 + kSensorH * kSensorH;
+    const float* w3 = b2 + kSensorH;
+    const float b3 = w3[kSensorH];
+    for (int n = 0; n < kSensorH; ++n) {
+        for (int k = 0; k < kSensorK; ++k)
+            out->w1t[n * kW1Pitch + k] = __float2bfloat16_rn(k < kSensorIn ? W1[k * kSensorH + n] : 0.f);
+        for (int k = 0; k < kSensorH; ++k) out->w2t[n * kW2Pitch + k] = __float2bfloat16_rn(W2[k * kSensorH + n]);
+        out->b1[n] = b1[n];
+        out->b2[n] = b2[n];
+        out->w3[n] = w3[n];
+    }
+    out->b3 = b3;
+}
+
+// ---------------------------------------------------------------------------
+// Per-cell sensor output, features and plain labels of a padded state.
+// ---------------------------------------------------------------------------
+constexpr int kTX = 32, kTY = 16, kH = 2, kRW = kTX + 2 * kH, kRH = kTY + 2 * kH;
+
+struct SensorTileParams {
+    Grid g;
+    double gamma;
+    const double* q;        // padded state, ghosts filled
+    const SensorDev* w;     // weights (eval) or nullptr
+    float* prob;            // [ny][nx] network output, or nullptr
+    __nv_bfloat16* feat;    // [ny*nx][64] features, or nullptr
+    unsigned char* label;   // [ny*nx] plain-detector label, or nullptr
+};
+
+__global__ void __launch_bounds__(256) sensor_tile_kernel(const SensorTileParams P)
+{
+    __shared__ float sr[kRH * kRW], sp[kRH * kRW];
+    __shared__ SensorDev sw;
+    const int tx0 = blockIdx.x * kTX, ty0 = blockIdx.y * kTY;
+    const int nx = P.g.nx, ny = P.g.ny;
+    const float gm1 = (float)(P.gamma - 1.0);
+    // stage the region as FP32 primitives exactly as the FP32 stage kernel does
+    for (int idx = threadIdx.x; idx < kRH * kRW; idx += blockDim.x) {
+        const int ry = idx / kRW, rx = idx - ry * kRW;
+        const int gx = min(tx0 + rx + kGhost - kH, nx + 2 * kGhost - 1);
+        const int gy = min(ty0 + ry + kGhost - kH, ny + 2 * kGhost - 1);
+        const long long o = (long long)gy * P.g.pitch + gx;
+        const float r = (float)P.q[o], ir = 1.f / r;
+        const float u = (float)P.q[o + P.g.plane] * ir, v = (float)P.q[o + 2 * P.g.plane] * ir;
+        sr[idx] = r;
+        sp[idx] = gm1 * ((float)P.q[o + 3 * P.g.plane] - 0.5f * r * (u * u + v * v));
+    }
+    if (P.w) load_sensor(&sw, P.w);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    for (int chunk = warp; chunk < kTX * kTY / 16; chunk += blockDim.x >> 5) {
+        auto cells = [&](int i, const float*& r, const float*& p) {
+            const int c = chunk * 16 + i, cy = c / kTX, cx = c - cy * kTX;
+            r = sr + (cy + kH) * kRW + (cx + kH);
+            p = sp + (cy + kH) * kRW + (cx + kH);
+        };
+        if (P.prob) {
+            float plo, phi;
+            sensor_warp16(sw, cells, kRW, plo, phi);
+            if (t == 0) {
+                for (int h = 0; h < 2; ++h) {
+                    const int c = chunk * 16 + g + 8 * h, cy = c / kTX, cx = c - cy * kTX;
+                    const int i = ty0 + cy, j = tx0 + cx;
+                    if (i < ny && j < nx) P.prob[(long long)i * nx + j] = h ? phi : plo;
+                }
+            }
+        }
+        if (P.feat) {  // one cell per lane pair: lanes 0..15 write 64 features each
+            if (lane < 16) {
+                const int c = chunk * 16 + lane, cy = c / kTX, cx = c - cy * kTX;
+                const int i = ty0 + cy, j = tx0 + cx;
+                if (i < ny && j < nx) {
+                    const float* r;
+                    const float* p;
+                    cells(lane, r, p);
+                    float s1, s2;
+                    sensor_scales(r, p, kRW, s1, s2);
+                    uint32_t* out = reinterpret_cast<uint32_t*>(P.feat + ((long long)i * nx + j) * kSensorK);
+                    for (int k = 0; k < kSensorK; k += 2)
+                        out[k / 2] = pack_bf16(sensor_feature(r, p, kRW, s1, s2, k),
+                                               sensor_feature(r, p, kRW, s1, s2, k + 1));
+                }
+            }
+        }
+    }
+    if (P.label) {  // plain detector in FP64 on the density (Eq. detector)
+        for (int c = threadIdx.x; c < kTX * kTY; c += blockDim.x) {
+            const int cy = c / kTX, cx = c - cy * kTX, i = ty0 + cy, j = tx0 + cx;
+            if (i >= ny || j >= nx) continue;
+            const double* r = P.q + (long long)(i + kGhost) * P.g.pitch + (j + kGhost);
+            const bool tr = trouble_cell<double>(r, 1) || trouble_cell<double>(r, P.g.pitch);
+            P.label[(long long)i * nx + j] = tr ? 1 : 0;
+        }
+    }
+}
+
+cudaError_t launch_sensor_tile(const Grid& g, double gamma, const double* q, const SensorDev* w, float* prob,
+                               void* feat_bf16, unsigned char* label, cudaStream_t s)
+{
+    __nv_bfloat16* feat = static_cast<__nv_bfloat16*>(feat_bf16);
+    SensorTileParams P;
+    P.g = g;
+    P.gamma = gamma;
+    P.q = q;
+    P.w = w;
+    P.prob = prob;
+    P.feat = feat;
+    P.label = label;
+    dim3 grid((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY);
+    sensor_tile_kernel<<<grid, 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Training: one kernel accumulates the gradient of a mini-batch, one applies
+// Adam. Operands are BF16-rounded (features as stored, weights and the first
+// hidden layer rounded), products accumulate in FP32.
+// ---------------------------------------------------------------------------
+constexpr int kTrainWarps = 4;
+constexpr int kXP = kSensorIn + 1;  // row pitches of the per-warp scratch (odd: no bank conflicts)
+constexpr int kHP = kSensorH + 1;
+// dynamic shared memory of the gradient kernel, in floats
+constexpr int kOffW1 = 0;
+constexpr int kOffW2 = kOffW1 + kSensorIn * kSensorH;
+constexpr int kOffB1 = kOffW2 + kSensorH * kSensorH;
+constexpr int kOffB2 = kOffB1 + kSensorH;
+constexpr int kOffW3 = kOffB2 + kSensorH;
+constexpr int kOffB3 = kOffW3 + kSensorH;
+constexpr int kOffG = kOffB3 + 4;
+constexpr int kOffWarp = kOffG + ((kSensorParams + 3) / 4) * 4;
+constexpr int kWarpFloats = 32 * kXP + 4 * 32 * kHP + 32;  // x, h1, dh1, dh2, h2, dz
+constexpr int kTrainSmemFloats = kOffWarp + kTrainWarps * kWarpFloats;
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+struct TrainParams {
+    const __nv_bfloat16* X;  // [n][64]
+    const unsigned char* y;  // [n]
+    long long n;
+    int batch;               // samples per step
+    unsigned long long seed;
+    int step;
+    float pos_weight;        // loss weight of label-1 samples
+    const float* w;          // FP32 master parameters (host layout)
+    float* grad;             // accumulated gradient (host layout), zeroed by Adam
+    float* loss;             // [steps] summed loss of each step
+};
+
+__global__ void __launch_bounds__(kTrainWarps * 32) sensor_grad_kernel(const TrainParams P)
+{
+    extern __shared__ float sm[];
+    float* const W1 = sm + kOffW1;
+    float* const W2 = sm + kOffW2;
+    float* const b1 = sm + kOffB1;
+    float* const b2 = sm + kOffB2;
+    float* const w3 = sm + kOffW3;
+    float* const gacc = sm + kOffG;
+    const float* pw = P.w;
+    for (int i = threadIdx.x; i < kSensorIn * kSensorH; i += blockDim.x) W1[i] = bf16r(pw[i]);
+    for (int i = threadIdx.x; i < kSensorH * kSensorH; i += blockDim.x)
+        W2[i] = bf16r(pw[kSensorIn * kSensorH + kSensorH + i]);
+    for (int i = threadIdx.x; i < kSensorH; i += blockDim.x) {
+        b1[i] = pw[kSensorIn * kSensorH + i];
+        b2[i] = pw[kSensorIn * kSensorH + kSensorH + kSensorH * kSensorH + i];
+        w3[i] = pw[kSensorIn * kSensorH + 2 * kSensorH + kSensorH * kSensorH + i];
+    }
+    if (threadIdx.x == 0) sm[kOffB3] = pw[kSensorParams - 1];
+    for (int i = threadIdx.x; i < kSensorParams; i += blockDim.x) gacc[i] = 0.f;
+    __syncthreads();
+    const float b3s = sm[kOffB3];
+    float* const wbase = sm + kOffWarp + (threadIdx.x >> 5) * kWarpFloats;
+    float* const xsw = wbase;                       // [32][kXP]
+    float* const h1sw = xsw + 32 * kXP;             // [32][kHP]
+    float* const d1sw = h1sw + 32 * kHP;
+    float* const d2sw = d1sw + 32 * kHP;
+    float* const h2sw = d2sw + 32 * kHP;
+    float* const dzsw = h2sw + 32 * kHP;            // [32]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* xr = xsw + lane * kXP;
+    float* h1r = h1sw + lane * kHP;
+    float* d1r = d1sw + lane * kHP;
+    float* d2r = d2sw + lane * kHP;
+    float* h2r = h2sw + lane * kHP;
+    float aW1[kSensorIn], aW2[kSensorH], ab1 = 0.f, ab2 = 0.f, aw3 = 0.f, ab3 = 0.f, lsum = 0.f;
+#pragma unroll
+    for (int k = 0; k < kSensorIn; ++k) aW1[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < kSensorH; ++k) aW2[k] = 0.f;
+
+    const int per_block = kTrainWarps * 32;
+    for (int base = blockIdx.x * per_block; base < P.batch; base += gridDim.x * per_block) {
+        const int s_id = base + warp * 32 + lane;
+        const bool valid = s_id < P.batch;
+        // sample (with replacement) by a counter-based hash of (seed, step, s_id)
+        const unsigned long long hsh = splitmix64(P.seed ^ ((unsigned long long)P.step * 0x100000001ull + s_id));
+        const long long idx = (long long)(hsh % (unsigned long long)P.n);
+        const __nv_bfloat16* xin = P.X + idx * kSensorK;
+        for (int k = 0; k < kSensorIn; ++k) xr[k] = valid ? __bfloat162float(xin[k]) : 0.f;
+        const float yv = valid ? (float)P.y[idx] : 0.f;
+        // forward
+        for (int n = 0; n < kSensorH; ++n) {
+            float a = b1[n];
+            for (int k = 0; k < kSensorIn; ++k) a = fmaf(xr[k], W1[k * kSensorH + n], a);
+            h1r[n] = bf16r(fmaxf(a, 0.f));
+        }
+        float z = b3s;
+        for (int n = 0; n < kSensorH; ++n) {
+            float a = b2[n];
+            for (int k = 0; k < kSensorH; ++k) a = fmaf(h1r[k], W2[k * kSensorH + n], a);
+            a = fmaxf(a, 0.f);
+            h2r[n] = a;
+            z = fmaf(a, w3[n], z);
+        }
+        const float p = 1.f / (1.f + expf(-z));
+        const float wt = valid ? (yv > 0.5f ? P.pos_weight : 1.f) : 0.f;
+        // binary cross-entropy from the logit: softplus(z) - y z
+        const float l = fmaxf(z, 0.f) - yv * z + log1pf(expf(-fabsf(z)));
+        lsum += wt * l;
+        const float dz = wt * (p - yv);
+        // backward
+        for (int n = 0; n < kSensorH; ++n) d2r[n] = h2r[n] > 0.f ? dz * w3[n] : 0.f;
+        for (int k = 0; k < kSensorH; ++k) {
+            float a = 0.f;
+            for (int n = 0; n < kSensorH; ++n) a = fmaf(d2r[n], W2[k * kSensorH + n], a);
+            d1r[k] = h1r[k] > 0.f ? a : 0.f;
+        }
+        dzsw[lane] = dz;
+        __syncwarp();
+        // lane n accumulates column n of every weight gradient over the 32 samples
+        const int n = lane;
+        for (int s = 0; s < 32; ++s) {
+            const float* xs_s = xsw + s * kXP;
+            const float* h1_s = h1sw + s * kHP;
+            const float d1 = d1sw[s * kHP + n], d2 = d2sw[s * kHP + n];
+#pragma unroll
+            for (int k = 0; k < kSensorIn; ++k) aW1[k] = fmaf(xs_s[k], d1, aW1[k]);
+#pragma unroll
+            for (int k = 0; k < kSensorH; ++k) aW2[k] = fmaf(h1_s[k], d2, aW2[k]);
+            ab1 += d1;
+            ab2 += d2;
+            aw3 = fmaf(h2sw[s * kHP + n], dzsw[s], aw3);
+            ab3 += dzsw[s];
+        }
+        __syncwarp();
+    }
+    // block reduction in shared memory, then one global add per parameter
+    const int n = lane;
+#pragma unroll
+    for (int k = 0; k < kSensorIn; ++k) atomicAdd(&gacc[k * kSensorH + n], aW1[k]);
+    atomicAdd(&gacc[kSensorIn * kSensorH + n], ab1);
+#pragma unroll
+    for (int k = 0; k < kSensorH; ++k) atomicAdd(&gacc[kSensorIn * kSensorH + kSensorH + k * kSensorH + n], aW2[k]);
+    atomicAdd(&gacc[kSensorIn * kSensorH + kSensorH + kSensorH * kSensorH + n], ab2);
+    atomicAdd(&gacc[kSensorIn * kSensorH + 2 * kSensorH + kSensorH * kSensorH + n], aw3);
+    if (lane == 0) atomicAdd(&gacc[kSensorParams - 1], ab3);
+    // the loss of the step
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSensorParams; i += blockDim.x) atomicAdd(&P.grad[i], gacc[i]);
+    if (lane == 0) atomicAdd(&P.loss[P.step], lsum);
+}
+
+// Adam (Kingma and Ba, 2015) on the mean gradient of the step; clears it.
+__global__ void sensor_adam_kernel(float* w, float* grad, float* m, float* v, int step, float lr, float inv_batch)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kSensorParams) return;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float g = grad[i] * inv_batch;
+    grad[i] = 0.f;
+    const float mi = b1 * m[i] + (1.f - b1) * g;
+    const float vi = b2 * v[i] + (1.f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / (1.f - powf(b1, (float)(step + 1)));
+    const float vh = vi / (1.f - powf(b2, (float)(step + 1)));
+    w[i] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+cudaError_t launch_sensor_train(const void* X_bf16, const unsigned char* y, long long n, int steps, int batch,
+                                float lr, float pos_weight, unsigned long long seed, float* w, float* grad,
+                                float* m, float* v, float* loss, cudaStream_t s)
+{
+    const __nv_bfloat16* X = static_cast<const __nv_bfloat16*>(X_bf16);
+    const int per_block = kTrainWarps * 32;
+    const int blocks = (batch + per_block - 1) / per_block;
+    const size_t smem = sizeof(float) * kTrainSmemFloats;
+    cudaError_t e = cudaFuncSetAttribute(sensor_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < steps; ++k) {
+        TrainParams P;
+        P.X = X;
+        P.y = y;
+        P.n = n;
+        P.batch = batch;
+        P.seed = seed;
+        P.step = k;
+        P.pos_weight = pos_weight;
+        P.w = w;
+        P.grad = grad;
+        P.loss = loss;
+        sensor_grad_kernel<<<blocks, per_block, smem, s>>>(P);
+        sensor_adam_kernel<<<(kSensorParams + 255) / 256, 256, 0, s>>>(w, grad, m, v, k, lr, 1.f / batch);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gbr

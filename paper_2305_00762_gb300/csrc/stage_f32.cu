@@ -6,6 +6,10 @@ namespace gbr {
 
 cudaError_t launch_stage_f32(const StageParams& p, cudaStream_t s)
 {
+    if (p.sensor) {
+        if (p.ph.mu > 0.0) return launch_stage_t<float, 32, 16, 256, true, true>(p, s);
+        return launch_stage_t<float, 32, 16, 256, false, true>(p, s);
+    }
     if (p.ph.mu > 0.0) return launch_stage_t<float, 32, 16, 256, true>(p, s);
     return launch_stage_t<float, 32, 16, 256, false>(p, s);
 }

@@ -17,6 +17,7 @@
 #include <stdint.h>
 
 #include "gbr_internal.h"
+#include "sensor.cuh"
 
 namespace gbr {
 
@@ -48,8 +49,16 @@ struct TileLayout {
     static constexpr int oHY = oHX + 4 * NHX;
     static constexpr int nT = oHY + 4 * NHY;  // elements of T
 
+    // learned sensor: per-cell decisions on the bounding box of both
+    // detector regions, rows and columns [3, B+9), and the weights
+    static constexpr int BOXW = BX + 6, BOXH = BY + 6, NBOX = BOXW * BOXH;
+
     template <typename T>
     static constexpr size_t bytes() { return sizeof(T) * (size_t)nT + (size_t)(NPX + NPY) + 16; }
+    template <typename T>
+    static constexpr size_t sensor_offset() { return (bytes<T>() + NBOX + 15) / 16 * 16; }
+    template <typename T, bool LEARNED>
+    static constexpr size_t total_bytes() { return LEARNED ? sensor_offset<T>() + sizeof(SensorDev) : bytes<T>(); }
 };
 
 template <typename T>
@@ -305,7 +314,7 @@ __device__ __forceinline__ double warp_max(double v)
 // the single-grid kernel (one CTA per tile) and the persistent batch kernel
 // (a CTA walks many tiles of many grids). Starts and ends with all threads
 // synchronised, so consecutive calls may reuse the shared memory.
-template <typename T, int BX, int BY, int NT, bool VISC>
+template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED = false>
 __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, const int ty0,
                                            unsigned char* smem_raw)
 {
@@ -353,6 +362,8 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         sU[2 * NU + idx] = v;
         sU[3 * NU + idx] = p;
     }
+    if constexpr (LEARNED)
+        load_sensor(reinterpret_cast<SensorDev*>(smem_raw + L::template sensor_offset<T>()), P.sensor);
     __syncthreads();
 
     // Phase 1: per-cell quantities, each computed once per tile.
@@ -368,13 +379,37 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
 #pragma unroll
         for (int m = 0; m < 4; ++m) sGY[m * L::NGY + idx] = grad6(s + m * NU, RW);
     }
-    for (int idx = tid; idx < L::NPX; idx += NT) {  // x detector (Eq. detector)
-        const int a = idx / L::PXW, b = idx - a * L::PXW;
-        sPX[idx] = trouble_cell(sU + (a + 6) * RW + (b + 3), 1) ? 1 : 0;
-    }
-    for (int idx = tid; idx < L::NPY; idx += NT) {  // y detector
-        const int a = idx / BX, b = idx - a * BX;
-        sPY[idx] = trouble_cell(sU + (a + 3) * RW + (b + 6), RW) ? 1 : 0;
+    if constexpr (!LEARNED) {
+        for (int idx = tid; idx < L::NPX; idx += NT) {  // x detector (Eq. detector)
+            const int a = idx / L::PXW, b = idx - a * L::PXW;
+            sPX[idx] = trouble_cell(sU + (a + 6) * RW + (b + 3), 1) ? 1 : 0;
+        }
+        for (int idx = tid; idx < L::NPY; idx += NT) {  // y detector
+            const int a = idx / BX, b = idx - a * BX;
+            sPY[idx] = trouble_cell(sU + (a + 3) * RW + (b + 6), RW) ? 1 : 0;
+        }
+    } else {
+        // Learned sensor on the tensor cores, 16 cells per warp: 1 = trouble,
+        // 0 = smooth, 2 = unsure (the plain detector decides below).
+        unsigned char* const sT = sPY + L::NPY;
+        const SensorDev& W = *reinterpret_cast<const SensorDev*>(smem_raw + L::template sensor_offset<T>());
+        const int nchunks = (L::NBOX + 15) / 16;
+        for (int chunk = tid >> 5; chunk < nchunks; chunk += NT / 32) {
+            auto cells = [&](int i, const float*& r, const float*& p) {
+                const int c = min(chunk * 16 + i, L::NBOX - 1);
+                const int by = c / L::BOXW, bx = c - by * L::BOXW;
+                r = reinterpret_cast<const float*>(sU) + (by + 3) * RW + (bx + 3);
+                p = reinterpret_cast<const float*>(sU) + 3 * NU + (by + 3) * RW + (bx + 3);
+            };
+            float plo, phi;
+            sensor_warp16(W, cells, RW, plo, phi);
+            if ((tid & 3) == 0) {
+                const int g = (tid & 31) >> 2;
+                const int c0 = chunk * 16 + g, c1 = c0 + 8;
+                if (c0 < L::NBOX) sT[c0] = plo > kSensorHi ? 1 : (plo < kSensorLo ? 0 : 2);
+                if (c1 < L::NBOX) sT[c1] = phi > kSensorHi ? 1 : (phi < kSensorLo ? 0 : 2);
+            }
+        }
     }
     for (int idx = tid; idx < L::NFX; idx += NT) {  // cell x-fluxes F^c (Sec. 1)
         const int a = idx / L::FXW, b = idx - a * L::FXW;
@@ -399,6 +434,20 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         sFY[3 * L::NFY + idx] = v * (E + p);
     }
     __syncthreads();
+    if constexpr (LEARNED) {  // per-direction flags from the sensor's decisions
+        const unsigned char* const sT = sPY + L::NPY;
+        for (int idx = tid; idx < L::NPX; idx += NT) {
+            const int a = idx / L::PXW, b = idx - a * L::PXW;
+            const unsigned char d = sT[(a + 3) * L::BOXW + b];
+            sPX[idx] = d == 2 ? (trouble_cell(sU + (a + 6) * RW + (b + 3), 1) ? 1 : 0) : d;
+        }
+        for (int idx = tid; idx < L::NPY; idx += NT) {
+            const int a = idx / BX, b = idx - a * BX;
+            const unsigned char d = sT[a * L::BOXW + b + 3];
+            sPY[idx] = d == 2 ? (trouble_cell(sU + (a + 3) * RW + (b + 6), RW) ? 1 : 0) : d;
+        }
+        __syncthreads();
+    }
 
     // Phase 2: every x face and y face of the tile, once.
     for (int w = tid; w < L::NHX + L::NHY; w += NT) {
@@ -547,20 +596,20 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
     __syncthreads();
 }
 
-template <typename T, int BX, int BY, int NT, bool VISC>
+template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED>
 __global__ void __launch_bounds__(NT) stage_kernel(const StageParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    stage_tile<T, BX, BY, NT, VISC>(P, blockIdx.x * BX, blockIdx.y * BY, smem_raw);
+    stage_tile<T, BX, BY, NT, VISC, LEARNED>(P, blockIdx.x * BX, blockIdx.y * BY, smem_raw);
 }
 
-template <typename T, int BX, int BY, int NT, bool VISC>
+template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED = false>
 cudaError_t launch_stage_t(const StageParams& p, cudaStream_t s)
 {
     using L = TileLayout<BX, BY, VISC>;
-    constexpr size_t smem = L::template bytes<T>();
+    constexpr size_t smem = L::template total_bytes<T, LEARNED>();
     static bool configured = false;
-    auto kern = stage_kernel<T, BX, BY, NT, VISC>;
+    auto kern = stage_kernel<T, BX, BY, NT, VISC, LEARNED>;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -23,6 +23,7 @@ GBR_OPT_PRECISION, GBR_OPT_RECORD_FLAGS, GBR_OPT_SENSOR, GBR_OPT_TIMING = 0, 1, 
 GBR_KERNEL_STAGE, GBR_KERNEL_GHOST, GBR_KERNEL_WAVESPEED, GBR_KERNEL_CLASSES = 0, 1, 2, 3
 GBR_GHOST = 6
 GBR_STATIC_SCRATCH_DOUBLES = 1 << 20
+GBR_SENSOR_PARAMS = 2721
 
 _lib = None
 
@@ -80,6 +81,12 @@ def load():
         "gbr_batch_get_times": (ip, [vp, ctypes.POINTER(dp), ctypes.POINTER(dp)]),
         "gbr_batch_autotune": (ip, [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip)]),
         "gbr_batch_sync": (ip, [vp]),
+        "gbr_batch_set_sensor_weights": (ip, [vp, ctypes.POINTER(ctypes.c_float), ip]),
+        "gbr_set_sensor_weights": (ip, [vp, ctypes.POINTER(ctypes.c_float), ip]),
+        "gbr_sensor_eval": (ip, [vp, vp, ip]),
+        "gbr_sensor_dataset": (ip, [vp, vp, vp]),
+        "gbr_sensor_train": (ip, [vp, vp, ctypes.c_longlong, ip, ip, dp, dp, ctypes.c_ulonglong,
+                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), vp]),
         "gbr_error_string": (ctypes.c_char_p, [ip]),
     }
     for name, (res, args) in sig.items():
@@ -232,6 +239,52 @@ def gbr_step_static(Q_in, Q_out, nx, ny, gamma, mu, Pr, bc, dx, dy, dt, stream=0
     return _check(rc, "gbr_step_static", allow)
 
 
+def _fvec(w, n):
+    a = np.ascontiguousarray(np.asarray(w, dtype=np.float32)).reshape(-1)
+    if a.size != n:
+        raise ValueError(f"expected {n} weights, got {a.size}")
+    return a
+
+
+def gbr_set_sensor_weights(ctx, w):
+    a = _fvec(w, GBR_SENSOR_PARAMS)
+    return _check(load().gbr_set_sensor_weights(ctx, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size),
+                  "gbr_set_sensor_weights")
+
+
+def gbr_sensor_eval(ctx, prob, nx, ny):
+    _expect(prob, "float32", (ny, nx))
+    p, dev = _ptr(prob)
+    return _check(load().gbr_sensor_eval(ctx, p, dev), "gbr_sensor_eval")
+
+
+def gbr_sensor_dataset(ctx, features, labels):
+    """features: device bfloat16 tensor [ncells, 64] (or None); labels:
+    device uint8 tensor [ncells] (or None)."""
+    pf = _ptr(features)[0] if features is not None else None
+    pl = _ptr(labels)[0] if labels is not None else None
+    for a in (features, labels):
+        if a is not None and not _ptr(a)[1]:
+            raise ValueError("gbr_sensor_dataset writes device buffers")
+    return _check(load().gbr_sensor_dataset(ctx, pf, pl), "gbr_sensor_dataset")
+
+
+def gbr_sensor_train(features, labels, steps, batch, lr, pos_weight, seed, w0, stream=0):
+    """Train from device features [n, 64] bf16 and labels [n] uint8; returns
+    (trained weights, per-step loss)."""
+    n = int(labels.shape[0])
+    if tuple(features.shape) != (n, 64):
+        raise ValueError("features must be [n, 64]")
+    w = _fvec(w0, GBR_SENSOR_PARAMS).copy()
+    loss = np.zeros(int(steps), np.float32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    _check(load().gbr_sensor_train(_ptr(features)[0], _ptr(labels)[0], n, int(steps), int(batch), float(lr),
+                                   float(pos_weight), int(seed) & (2**64 - 1), w.ctypes.data_as(fp),
+                                   loss.ctypes.data_as(fp), ctypes.c_void_p(int(stream or 0))),
+           "gbr_sensor_train")
+    return w, loss
+
+
 class Solver:
     """Convenience owner of one gbr context (marshalling only)."""
 
@@ -297,6 +350,16 @@ class Solver:
 
     def timing(self, on=True):
         gbr_set_option(self.ctx, GBR_OPT_TIMING, 1 if on else 0)
+
+    def set_sensor(self, w):
+        """Load learned-sensor weights and switch the sensor on."""
+        gbr_set_sensor_weights(self.ctx, w)
+        gbr_set_option(self.ctx, GBR_OPT_SENSOR, 1)
+
+    def sensor_eval(self):
+        out = np.empty((self.ny, self.nx), np.float32)
+        gbr_sensor_eval(self.ctx, out, self.nx, self.ny)
+        return out
 
     def get_timing(self):
         return gbr_get_timing(self.ctx)
@@ -370,6 +433,12 @@ class Batch:
         dt = (ctypes.c_double * self.n)()
         _check(load().gbr_batch_get_times(self.b, t, dt), "gbr_batch_get_times", allow)
         return np.array(t[:]), np.array(dt[:])
+
+    def set_sensor(self, w):
+        a = _fvec(w, GBR_SENSOR_PARAMS)
+        _check(load().gbr_batch_set_sensor_weights(self.b, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                   a.size), "gbr_batch_set_sensor_weights")
+        self.set_option(GBR_OPT_SENSOR, 1)
 
     def autotune(self, trials=3):
         c, bx, by = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

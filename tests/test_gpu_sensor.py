@@ -1,0 +1,123 @@
+"""Learned discontinuity sensor: dataset extraction, tensor-core inference,
+hand-written training and the FP32 + learned-sensor solution, against the
+oracle (plain-detector labels in C, features and network in numpy)."""
+import numpy as np
+import pytest
+
+from paper_2305_00762_gb300 import cases as C
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle as O
+    import oracle.sensor as OS
+    from paper_2305_00762_gb300 import build, gbr
+    build.build()
+    O.build()
+    gbr.load()
+    return torch, O, OS, gbr
+
+
+def cfg_of(O, c):
+    return O.Config(c.nx, c.ny, c.dx, c.dy, c.gamma, c.mu, c.Pr, c.bc)
+
+
+def seeded_weights(OS, seed=11, scale=1.0):
+    rng = np.random.default_rng(seed)
+    w = np.concatenate([rng.normal(0, scale * np.sqrt(2 / 50), 50 * 32), rng.normal(0, 0.1, 32),
+                        rng.normal(0, scale * np.sqrt(2 / 32), 32 * 32), rng.normal(0, 0.1, 32),
+                        rng.normal(0, 1.0, 32), [0.2]])
+    return w.astype(np.float32)
+
+
+def test_dataset_labels_and_features(env):
+    torch, O, OS, gbr = env
+    c = C.riemann_2d(96, 80)
+    s = gbr.Solver.for_case(c)
+    s.set_state(c.Q)
+    n = c.nx * c.ny
+    f = torch.empty((n, 64), dtype=torch.bfloat16, device="cuda")
+    y = torch.empty(n, dtype=torch.uint8, device="cuda")
+    gbr.gbr_sensor_dataset(s.ctx, f, y)
+    torch.cuda.synchronize()
+    lab = O.trouble_labels(cfg_of(O, c), c.Q).reshape(-1)
+    assert np.array_equal(y.cpu().numpy(), lab)          # no psi ties in this data
+    assert lab.sum() > 100
+    fg = f.float().cpu().numpy()
+    assert np.all(fg[:, 50:] == 0)
+    fo = OS.bf16_round(OS.features(cfg_of(O, c), c.Q))
+    # the FP32 primitives may round differently by an ulp: one BF16 step
+    assert np.all(np.abs(fg[:, :50] - fo) <= np.abs(fo) * 2.0 ** -7 + 1e-6)
+    assert np.mean(fg[:, :50] == fo) > 0.999
+    s.close()
+
+
+@pytest.mark.parametrize("make", [lambda: C.riemann_2d(64), lambda: C.isentropic_vortex(48),
+                                  lambda: C.kelvin_helmholtz(40, np.random.default_rng(4))],
+                         ids=["riemann64", "vortex48", "kh40"])
+def test_tensor_core_inference_matches_oracle_network(env, make):
+    torch, O, OS, gbr = env
+    c = make()
+    w = seeded_weights(OS)
+    s = gbr.Solver.for_case(c, precision=32)
+    s.set_state(c.Q)
+    gbr.gbr_set_sensor_weights(s.ctx, w)
+    p = s.sensor_eval().reshape(-1)
+    po = OS.forward(OS.features(cfg_of(O, c), c.Q), w)
+    assert po.std() > 0.01                               # outputs span a range
+    err = np.abs(p - po)
+    # BF16 rounding of inputs and of the first hidden layer may flip by one
+    # step between the two summation orders
+    assert err.max() < 2e-2, err.max()
+    assert np.mean(err < 1e-4) > 0.9
+    d, do = OS.decision(p), OS.decision(po)
+    near = (np.abs(po - 0.3) < 2e-2) | (np.abs(po - 0.7) < 2e-2)
+    assert np.all((d == do) | near)
+    s.close()
+
+
+def test_training_learns_the_detector(env):
+    torch, O, OS, gbr = env
+    from paper_2305_00762_gb300 import sensor_train as T
+    rng = np.random.default_rng(5)
+    X, y = T.dataset(torch, rng, 600_000, n=256)
+    w0 = T.init_weights(np.random.default_rng(6))
+    w, loss = gbr.gbr_sensor_train(X, y, 400, 4096, 2e-3, 3.0, 7, w0)
+    first, last = loss[:20].mean(), loss[-20:].mean()
+    assert np.all(np.isfinite(loss)) and last < 0.5 * first, (first, last)
+    held = T.agreement(torch, np.random.default_rng(8), w, count=4, n=256)
+    print("held-out:", held)
+    assert held["confident_agreement"] > 0.97
+    assert held["unsure_fraction"] < 0.1
+
+
+def test_fp32_learned_solution_error(env):
+    """The FP32 form with the learned sensor against the FP64 oracle (plain
+    detector): density L1 error after 30 steps of the 128^2 Riemann problem
+    and of a shear layer, with the committed trained weights."""
+    torch, O, OS, gbr = env
+    from paper_2305_00762_gb300 import sensor_train as T
+    import os
+    if not os.path.exists(T.DEFAULT_WEIGHTS):
+        pytest.skip("no trained sensor weights committed yet")
+    w = T.load_weights()
+    for c in (C.riemann_2d(128), C.kelvin_helmholtz(128, np.random.default_rng(3))):
+        cfg = cfg_of(O, c)
+        s = gbr.Solver.for_case(c, precision=32)
+        s.set_state(c.Q)
+        s.set_sensor(w)
+        Q = c.Q.copy()
+        for _ in range(30):
+            dt = 0.4 / O.max_wavespeed(cfg, Q)
+            s.step(dt)
+            Q, rc = O.rk3_step(cfg, Q, dt)
+            assert rc == 0
+        err = np.abs(s.get_state()[0] - Q[0]).sum() / np.abs(Q[0]).sum()
+        print(f"{c.name}: FP32+learned density L1 rel err {err:.3e}")
+        assert err <= 1e-5
+        s.close()
