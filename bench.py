@@ -203,14 +203,17 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_ensemble(args, torch, gbr, cases, st):
+def run_ensemble(args, torch, gbr, cases, st, sensor_w=None):
     """The batched form: the seeded ensemble of independent vortex / shear
-    layer grids (sizes from {256^2, 512^2, 1024^2, 2048^2}), FP32 arithmetic,
-    autotuned tile shape, every step replayed from one CUDA graph. The states
+    layer grids (sizes from {256^2, 512^2, 1024^2, 2048^2}), FP32 arithmetic
+    with the learned sensor, autotuned tile shape, every step replayed from
+    one CUDA graph. The states
     (about 2.8 GB for 64 grids) exceed L2, so no flush is needed."""
     table = cases.ensemble(args.ensemble_cases)
     ens = [cases.make_ensemble_case(kind, n, prm) for kind, n, prm in table]
     b = gbr.Batch(ens, precision=32, stream=st.cuda_stream)
+    if sensor_w is not None:
+        b.set_sensor(sensor_w)
     for k, c in enumerate(ens):
         b.set_state(k, torch.from_numpy(c.Q).cuda())
     del ens
@@ -231,6 +234,7 @@ def run_ensemble(args, torch, gbr, cases, st):
     b.close()
     return {"value": 3.0 * cells * args.steps / (ms * 1e-3), "unit": METRIC, "grids": len(table),
             "cells": cells, "ms_per_step": ms / args.steps, "precision": "fp32",
+            "learned_sensor": sensor_w is not None,
             "tile": list(shape), "graph": True, "dt_min": float(dt.min()), "dt_max": float(dt.max()),
             "status": gbr.error_string(rc),
             "sizes": {str(n): sum(1 for _, m, _ in table if m == n) for n in (256, 512, 1024, 2048)}}
@@ -286,14 +290,23 @@ def main():
     torch.cuda.synchronize()
     start_host = q_start.cpu().numpy()
 
-    def make(precision):
+    from paper_2305_00762_gb300 import sensor_train
+    try:
+        sensor_w = sensor_train.load_weights()
+    except OSError:
+        sensor_w = None
+
+    def make(precision, learned=False):
         s = gbr.Solver.for_case(case, stream=st.cuda_stream, precision=precision)
         s.set_state(q_start)
+        if learned:
+            s.set_sensor(sensor_w)
         return s
 
+    forms = [(64, False), (32, False)] + ([(32, True)] if sensor_w is not None else [])
     results = {}
-    for prec in (64, 32):
-        s = make(prec)
+    for prec, learned in forms:
+        s = make(prec, learned)
         for _ in range(args.warmup):
             s.step_cfl(CFL)
         s.sync()
@@ -306,8 +319,26 @@ def main():
         s.timing(False)
         ms = allmax(dist, torch, ms)
         rc = s.sync(allow=(gbr.GBR_ERR_NONPHYSICAL,))
-        results[prec] = {"ms": ms, "timing": tm, "clocks": clk.summary(), "status": rc}
+        results[(prec, learned)] = {"ms": ms, "timing": tm, "clocks": clk.summary(), "status": rc}
         s.close()
+
+    # Accuracy of each form against the FP64 path (which matches the oracle
+    # to 1e-12 per step): the same 20 fixed-dt steps from the window start.
+    acc = {}
+    ref = None
+    dt_fix = None
+    for prec, learned in forms:
+        s = make(prec, learned)
+        if dt_fix is None:
+            dt_fix = 0.8 * CFL / s.max_wavespeed()
+        for _ in range(20):
+            s.step(dt_fix)
+        rho = s.get_state()[0]
+        s.close()
+        if ref is None:
+            ref = rho
+        else:
+            acc[(prec, learned)] = float(np.abs(rho - ref).sum() / np.abs(ref).sum())
 
     # End to end through the public API with host buffers: every step copies
     # the state in from pinned host memory and the new state back out.
@@ -332,7 +363,7 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return
-    r64, r32 = results[64], results[32]
+    r64, r32 = results[(64, False)], results[(32, False)]
     upd = 3.0 * cells * args.steps * ws
     value = upd / (r64["ms"] * 1e-3)
     stage_ms, stage_n = r64["timing"]["stage"]
@@ -361,15 +392,24 @@ def main():
                       "stage_ms_avg": r32["timing"]["stage"][0] / max(r32["timing"]["stage"][1], 1),
                       "hbm_frac": bytes_cell * cells / (r32["timing"]["stage"][0] /
                                                         max(r32["timing"]["stage"][1], 1) * 1e-3) / 1e9 / hbm_peak,
-                      "clocks": r32["clocks"]},
+                      "clocks": r32["clocks"],
+                      "density_l1_vs_fp64_20_steps": acc.get((32, False))},
         "e2e": {"value": 3.0 * cells * args.steps * ws / e2e_s, "unit": METRIC,
                 "h2d_bytes_per_step": 32 * cells, "d2h_bytes_per_step": 32 * cells},
         "gpu_launches": int(sum(n for _, n in r64["timing"].values())),
         "clocks": r64["clocks"],
         "status": gbr.error_string(r64["status"]),
     }
+    if (32, True) in results:
+        rl = results[(32, True)]
+        line["fp32_learned_form"] = {
+            "value": upd / (rl["ms"] * 1e-3), "ms_per_step": rl["ms"] / args.steps,
+            "speedup_vs_fp64": r64["ms"] / rl["ms"],
+            "stage_ms_avg": rl["timing"]["stage"][0] / max(rl["timing"]["stage"][1], 1),
+            "sensor": "MLP 50-32-32-1, BF16 mma.sync, fallback band [0.3, 0.7]",
+            "density_l1_vs_fp64_20_steps": acc.get((32, True)), "clocks": rl["clocks"]}
     if not args.no_ensemble:
-        line["ensemble"] = run_ensemble(args, torch, gbr, cases, st)
+        line["ensemble"] = run_ensemble(args, torch, gbr, cases, st, sensor_w)
     if not args.no_cpu_baseline:
         mid = cases.Case(case.name, start_host, case.dx, case.dy, case.gamma, case.mu, case.Pr, case.bc)
         line["cpu_baseline"] = cpu_baseline(mid)
