@@ -177,9 +177,11 @@ int gbr_get_timing(gbr_ctx *ctx, double *ms, int *launches, int *dropped);
  * sigmoid) on the 5 x 5 stencil of density and pressure differences of a
  * cell, each field divided by (its largest absolute difference + 1e-3),
  * replaces the per-cell density-detector test of Sec. 2.4 (Eq. detector) in
- * the FP32 form: output > 0.7 marks a discontinuity, < 0.3 smooth flow, and
- * in between the plain detector decides (per direction). The buffer of
- * Eq. buffer is unchanged. The network runs on the tensor cores with BF16
+ * the FP32 form: output < 0.3 marks smooth flow (no plain test is run), in
+ * [0.3, 0.7] the plain detector decides (per direction), and > 0.7 marks a
+ * discontinuity whose direction the plain per-direction tests assign (both
+ * directions if neither test marks the cell). The buffer of Eq. buffer is
+ * unchanged. The network runs on the tensor cores with BF16
  * operands and FP32 accumulation, fused into the stage kernel.
  * Weight vector (GBR_SENSOR_PARAMS floats): W1[50][32], b1[32], W2[32][32],
  * b2[32], w3[32], b3, with h1 = relu(x W1 + b1) rounded to BF16,

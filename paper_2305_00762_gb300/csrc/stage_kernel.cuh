@@ -434,17 +434,34 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         sFY[3 * L::NFY + idx] = v * (E + p);
     }
     __syncthreads();
-    if constexpr (LEARNED) {  // per-direction flags from the sensor's decisions
+    if constexpr (LEARNED) {
+        // Per-direction flags from the sensor's per-cell decision. Smooth (0):
+        // no flag. Unsure (2): the plain detector of that direction. Trouble
+        // (1): the single output does not say along which axis the jump lies,
+        // so the plain tests assign the direction, and a cell neither of them
+        // marks keeps the network's flag in both directions.
         const unsigned char* const sT = sPY + L::NPY;
         for (int idx = tid; idx < L::NPX; idx += NT) {
             const int a = idx / L::PXW, b = idx - a * L::PXW;
             const unsigned char d = sT[(a + 3) * L::BOXW + b];
-            sPX[idx] = d == 2 ? (trouble_cell(sU + (a + 6) * RW + (b + 3), 1) ? 1 : 0) : d;
+            unsigned char f = 0;
+            if (d != 0) {
+                const T* c = sU + (a + 6) * RW + (b + 3);
+                const bool tx = trouble_cell(c, 1);
+                f = (tx || (d == 1 && !trouble_cell(c, RW))) ? 1 : 0;
+            }
+            sPX[idx] = f;
         }
         for (int idx = tid; idx < L::NPY; idx += NT) {
             const int a = idx / BX, b = idx - a * BX;
             const unsigned char d = sT[a * L::BOXW + b + 3];
-            sPY[idx] = d == 2 ? (trouble_cell(sU + (a + 3) * RW + (b + 6), RW) ? 1 : 0) : d;
+            unsigned char f = 0;
+            if (d != 0) {
+                const T* c = sU + (a + 3) * RW + (b + 6);
+                const bool ty = trouble_cell(c, RW);
+                f = (ty || (d == 1 && !trouble_cell(c, 1))) ? 1 : 0;
+            }
+            sPY[idx] = f;
         }
         __syncthreads();
     }
