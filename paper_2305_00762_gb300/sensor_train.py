@@ -55,8 +55,13 @@ def init_weights(rng):
     return w.astype(np.float32)
 
 
-def snapshots(torch, rng, n, count, steps_between=8, cfl=0.5):
-    """Yield (case, device state after some steps) of seeded runs."""
+# Snapshot schedule of every run: after about 8, 32, 96 and 224 steps (each
+# jittered), so that early, developing and developed flows are all sampled.
+SCHEDULE = (8, 24, 64, 128)
+
+
+def snapshots(torch, rng, n, count, cfl=0.5):
+    """Yield a solver positioned at successive snapshots of seeded runs."""
     made = 0
     while made < count:
         if made % 4 == 3:
@@ -66,7 +71,7 @@ def snapshots(torch, rng, n, count, steps_between=8, cfl=0.5):
         s = gbr.Solver.for_case(c, precision=32)
         s.set_state(torch.from_numpy(c.Q).cuda())
         for k in range(4):
-            for _ in range(int(rng.integers(1, 2 * steps_between))):
+            for _ in range(int(rng.integers(SCHEDULE[k] // 2, SCHEDULE[k] * 3 // 2))):
                 s.step_cfl(cfl)
             if s.sync(allow=(gbr.GBR_ERR_NONPHYSICAL,)) != gbr.GBR_OK:
                 break
@@ -115,7 +120,7 @@ def agreement(torch, rng, w, count=8, n=512):
     return stats
 
 
-def train(samples=20_000_000, epochs=2.0, batch=8192, lr=2e-3, pos_weight=3.0, seed=SEED, out=DEFAULT_WEIGHTS,
+def train(samples=20_000_000, epochs=4.0, batch=8192, lr=2e-3, pos_weight=6.0, seed=SEED, out=DEFAULT_WEIGHTS,
           verbose=True):
     import torch
     rng = np.random.default_rng(seed)
@@ -148,9 +153,10 @@ def load_weights(path=DEFAULT_WEIGHTS):
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--samples", type=int, default=20_000_000)
-    ap.add_argument("--epochs", type=float, default=2.0)
+    ap.add_argument("--epochs", type=float, default=4.0)
+    ap.add_argument("--pos-weight", type=float, default=6.0)
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     a = ap.parse_args()
     from . import build
     build.build()
-    train(a.samples, a.epochs, out=a.out)
+    train(a.samples, a.epochs, pos_weight=a.pos_weight, out=a.out)
