@@ -60,7 +60,7 @@ template <typename T, int BX, int BY, int NT, bool LEARNED>
 cudaError_t batch_blocks(int* out)
 {
     using L = TileLayout<BX, BY, false>;
-    constexpr size_t smem = L::template total_bytes<T, LEARNED>();
+    constexpr size_t smem = L::template total_bytes<T, NT, LEARNED>();
     static int blocks = 0;
     if (blocks == 0) {
         auto kern = batch_stage_kernel<T, BX, BY, NT, LEARNED>;
@@ -82,7 +82,7 @@ cudaError_t launch_batch_t(const BatchCase* cases, int ncases, int total_tiles, 
                            const SensorDev* sensor = nullptr)
 {
     using L = TileLayout<BX, BY, false>;
-    constexpr size_t smem = L::template total_bytes<T, LEARNED>();
+    constexpr size_t smem = L::template total_bytes<T, NT, LEARNED>();
     int blocks = 0;
     cudaError_t e = batch_blocks<T, BX, BY, NT, LEARNED>(&blocks);
     if (e != cudaSuccess || total_tiles <= 0) return e;

@@ -40,6 +40,8 @@ struct TileLayout {
     static constexpr int HXW = BX + 1, NHX = HXW * BY;
     static constexpr int HYH = BY + 1, NHY = HYH * BX;
 
+    static constexpr int NF = NHX + NHY;  // faces of the tile
+
     static constexpr int oU = 0;
     static constexpr int oGX = oU + 4 * NU;
     static constexpr int oGY = oGX + 4 * NGX;
@@ -47,18 +49,26 @@ struct TileLayout {
     static constexpr int oFY = oFX + 4 * NFX;
     static constexpr int oHX = oFY + 4 * NFY;
     static constexpr int oHY = oHX + 4 * NHX;
-    static constexpr int nT = oHY + 4 * NHY;  // elements of T
+    static constexpr int oQ = oHY + 4 * NHY;  // MP-limiter work queues, one per warp
 
     // learned sensor: per-cell decisions on the bounding box of both
     // detector regions, rows and columns [3, B+9), and the weights
     static constexpr int BOXW = BX + 6, BOXH = BY + 6, NBOX = BOXW * BOXH;
 
+    // Work-queue capacity per warp (items of 10 stencil values + the GRB value).
     template <typename T>
-    static constexpr size_t bytes() { return sizeof(T) * (size_t)nT + (size_t)(NPX + NPY) + 16; }
-    template <typename T>
-    static constexpr size_t sensor_offset() { return (bytes<T>() + NBOX + 15) / 16 * 16; }
-    template <typename T, bool LEARNED>
-    static constexpr size_t total_bytes() { return LEARNED ? sensor_offset<T>() + sizeof(SensorDev) : bytes<T>(); }
+    static constexpr int qcap() { return sizeof(T) == 8 ? 16 : 32; }
+    template <typename T, int NT>
+    static constexpr int nT() { return oQ + (NT / 32) * qcap<T>() * 11; }  // elements of T
+    template <typename T, int NT>
+    static constexpr size_t bytes() { return sizeof(T) * (size_t)nT<T, NT>() + (size_t)(NPX + NPY) + 16; }
+    template <typename T, int NT>
+    static constexpr size_t sensor_offset() { return (bytes<T, NT>() + NBOX + 15) / 16 * 16; }
+    template <typename T, int NT, bool LEARNED>
+    static constexpr size_t total_bytes()
+    {
+        return LEARNED ? sensor_offset<T, NT>() + sizeof(SensorDev) : bytes<T, NT>();
+    }
 };
 
 template <typename T>
@@ -99,30 +109,59 @@ __device__ __forceinline__ bool trouble_cell(const T* r, int st)
     return T(2) * (T(2) * a * b + eps) < a * a + b * b + eps;
 }
 
-// Eqs. grb, mp5Condition, alpha, mp-procedure: MEG7 left value at j+1/2 from
-// Phi_{j-2..j+2} (p0..p4) and Phi'_{j-2..j+2} (d0..d4), xi = 7.
-// The GRB weights of Phi sum to one (478 + 2*178 + 2*3 = 840), so Eq. grb is
-// evaluated as Phi_j plus weighted differences: on flat data Phi^L equals
-// Phi_j exactly and the MP test passes without entering the limiter (whose
-// result there is Phi_j as well).
+// Eq. grb and the MP test of Eqs. mp5Condition and alpha for the left value
+// at j+1/2 from Phi_{j-2..j+2} (p[0..4]) and Phi'_{j-2..j+2} (d[0..4]),
+// xi = 7. Returns the GRB value; `need` is set when the MP limiter must be
+// applied. The GRB weights of Phi sum to one (478 + 2*178 + 2*3 = 840), so
+// Eq. grb is evaluated as Phi_j plus weighted differences: on flat data Phi^L
+// equals Phi_j exactly and the test passes (the limiter would return Phi_j).
 template <typename T>
-__device__ __forceinline__ T meg7(T p0, T p1, T p2, T p3, T p4, T d0, T d1, T d2, T d3, T d4)
+__device__ __forceinline__ T grb_check(const T* p, const T* d, bool& need)
 {
-    const T pl = p2 + (T(420) * d2 + T(60) * (d1 - d3) + T(178) * ((p1 - p2) + (p3 - p2)) +
-                       T(3) * ((p0 - p2) + (p4 - p2))) *
-                          T(1.0 / 840.0);
-    const T pmp = p2 + minmod(p3 - p2, T(7) * (p2 - p1));
-    if ((pl - p2) * (pl - pmp) <= T(1e-40)) return pl;
-    const T dm1 = T(2) * (p2 - T(2) * p1 + p0) - T(0.5) * (d2 - d0);
-    const T dj = T(2) * (p3 - T(2) * p2 + p1) - T(0.5) * (d3 - d1);
-    const T dp1 = T(2) * (p4 - T(2) * p3 + p2) - T(0.5) * (d4 - d2);
-    const T md = T(0.5) * (p2 + p3) - T(0.5) * minmod(dj, dp1);
-    const T ul = p2 + T(7) * (p2 - p1);
-    const T lc = T(0.5) * (T(3) * p2 - p1) + T(4.0 / 3.0) * minmod(dj, dm1);
-    const T pmin = tmax(tmin(p2, tmin(p3, md)), tmin(p2, tmin(ul, lc)));
-    const T pmax = tmin(tmax(p2, tmax(p3, md)), tmax(p2, tmax(ul, lc)));
+    const T pl = p[2] + (T(420) * d[2] + T(60) * (d[1] - d[3]) + T(178) * ((p[1] - p[2]) + (p[3] - p[2])) +
+                         T(3) * ((p[0] - p[2]) + (p[4] - p[2]))) *
+                            T(1.0 / 840.0);
+    const T pmp = p[2] + minmod(p[3] - p[2], T(7) * (p[2] - p[1]));
+    need = !((pl - p[2]) * (pl - pmp) <= T(1e-40));
+    return pl;
+}
+
+// Eq. mp-procedure: the MP-limited value given the GRB value pl.
+template <typename T>
+__device__ __forceinline__ T mp_limit(const T* p, const T* d, T pl)
+{
+    const T dm1 = T(2) * (p[2] - T(2) * p[1] + p[0]) - T(0.5) * (d[2] - d[0]);
+    const T dj = T(2) * (p[3] - T(2) * p[2] + p[1]) - T(0.5) * (d[3] - d[1]);
+    const T dp1 = T(2) * (p[4] - T(2) * p[3] + p[2]) - T(0.5) * (d[4] - d[2]);
+    const T md = T(0.5) * (p[2] + p[3]) - T(0.5) * minmod(dj, dp1);
+    const T ul = p[2] + T(7) * (p[2] - p[1]);
+    const T lc = T(0.5) * (T(3) * p[2] - p[1]) + T(4.0 / 3.0) * minmod(dj, dm1);
+    const T pmin = tmax(tmin(p[2], tmin(p[3], md)), tmin(p[2], tmin(ul, lc)));
+    const T pmax = tmin(tmax(p[2], tmax(p[3], md)), tmax(p[2], tmax(ul, lc)));
     return pl + minmod(pmin - pl, pmax - pl);
 }
+
+// Per-warp queue of MP-limiter work (Eq. mp-procedure). Lanes add only the
+// (field, side) values that fail the MP test; a flush evaluates up to QCAP of
+// them at once, one per lane, so the warp pays for the limiter once per batch
+// of failing values instead of once per field and side in which any lane
+// fails. All 32 lanes must call add() and flush() together.
+template <typename T, int QCAP>
+struct MpQueue {
+    T* buf;     // [QCAP][11]: p0..p4, d0..d4, then pl (replaced by the result)
+    int count;  // uniform over the warp
+    int lane;
+
+    __device__ __forceinline__ void flush()
+    {
+        __syncwarp();
+        if (lane < count) {
+            T* it = buf + lane * 11;
+            it[10] = mp_limit(it, it + 5, it[10]);
+        }
+        __syncwarp();
+    }
+};
 
 // 1/2 (F(f_L) + F(f_R)) at the face after cell f[0]: the sum of Eq.
 // flux-full and its mirror Eq. flux-right is the symmetric 10-point stencil
@@ -157,9 +196,9 @@ struct PhysT {
 
 // The whole interface procedure of Secs. 2.1-2.4 at face j+1/2. Returns the
 // total flux in face-normal order and the detector flag sigma.
-template <typename T, bool VISC>
+template <typename T, bool VISC, int QCAP>
 __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P, T inv_dn, T inv_dt, T out[4],
-                                          bool& smooth)
+                                          bool& smooth, MpQueue<T, QCAP>& q)
 {
     // Eq. buffer: sigma = 0 if psi_k < psi_c for any k in j-2..j+3.
     bool tr = false;
@@ -179,46 +218,90 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
     const T ic2 = icb * icb;         // 1 / c^2
     const T be = T(0.5) * ic2;       // 1 / (2 c^2)
 
-    T wL[4], wR[4];
-    {  // fields 1 and 4 (u - c and u + c) share un and p
-        T w0[6], w3[6], e0[6], e3[6];
+    // GRB + MP test for the 8 (field, side) values, one characteristic field
+    // at a time (fields: u - c, entropy rho - p/c^2, shear ut, u + c); failing
+    // values go to the warp's limiter queue. The right side is the left
+    // formula on the stencil mirrored about the face (cell j+1-k, gradient
+    // sign flipped).
+    T wv[8];
+    int qpos[8];
+    const unsigned lt = (1u << q.lane) - 1u;
+#pragma unroll
+    for (int fld = 0; fld < 4; ++fld) {
+        T w[6], e[6];  // characteristic values and gradients of cells j-2..j+3
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const int o = (k - 2);
-            const T tu = al * in.u[1][o * su], tp = be * in.u[3][o * su];
-            w0[k] = tp - tu;
-            w3[k] = tp + tu;
-            const T gu = al * in.g[1][o * sg], gp = be * in.g[3][o * sg];
-            e0[k] = gp - gu;
-            e3[k] = gp + gu;
+            if (fld == 0 || fld == 3) {
+                const T tu = al * in.u[1][o * su], tp = be * in.u[3][o * su];
+                const T gu = al * in.g[1][o * sg], gp = be * in.g[3][o * sg];
+                w[k] = fld == 0 ? tp - tu : tp + tu;
+                e[k] = fld == 0 ? gp - gu : gp + gu;
+            } else if (fld == 1) {
+                w[k] = in.u[0][o * su] - ic2 * in.u[3][o * su];
+                e[k] = in.g[0][o * sg] - ic2 * in.g[3][o * sg];
+            } else {
+                w[k] = in.u[2][o * su];
+                e[k] = in.g[2][o * sg];
+            }
         }
-        wL[0] = meg7(w0[0], w0[1], w0[2], w0[3], w0[4], e0[0], e0[1], e0[2], e0[3], e0[4]);
-        wR[0] = meg7(w0[5], w0[4], w0[3], w0[2], w0[1], -e0[5], -e0[4], -e0[3], -e0[2], -e0[1]);
-        wL[3] = meg7(w3[0], w3[1], w3[2], w3[3], w3[4], e3[0], e3[1], e3[2], e3[3], e3[4]);
-        wR[3] = meg7(w3[5], w3[4], w3[3], w3[2], w3[1], -e3[5], -e3[4], -e3[3], -e3[2], -e3[1]);
-    }
-    {  // field 2 (entropy): rho - p / c^2
-        T w[6], e[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const int o = (k - 2);
-            w[k] = in.u[0][o * su] - ic2 * in.u[3][o * su];
-            e[k] = in.g[0][o * sg] - ic2 * in.g[3][o * sg];
-        }
-        wL[1] = meg7(w[0], w[1], w[2], w[3], w[4], e[0], e[1], e[2], e[3], e[4]);
-        wR[1] = meg7(w[5], w[4], w[3], w[2], w[1], -e[5], -e[4], -e[3], -e[2], -e[1]);
-    }
-    {  // field 3 (shear): ut
-        T w[6], e[6];
+        for (int side = 0; side < 2; ++side) {
+            const int v = 2 * fld + side;
+            T pp[5], dd[5];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const int o = (k - 2);
-            w[k] = in.u[2][o * su];
-            e[k] = in.g[2][o * sg];
+            for (int k = 0; k < 5; ++k) {
+                pp[k] = side == 0 ? w[k] : w[5 - k];
+                dd[k] = side == 0 ? e[k] : -e[5 - k];
+            }
+            bool pending;
+            wv[v] = grb_check(pp, dd, pending);
+            qpos[v] = -1;
+            // Add the failing lanes in rank order while the queue has room;
+            // when it is full, evaluate it and hand out the results. Every
+            // condition below is uniform over the warp.
+            for (;;) {
+                const unsigned m = __ballot_sync(0xffffffffu, pending);
+                if (m == 0u) break;
+                const int room = QCAP - q.count;
+                if (room == 0) {
+                    q.flush();
+#pragma unroll
+                    for (int u = 0; u <= v; ++u)
+                        if (qpos[u] >= 0) {
+                            wv[u] = q.buf[qpos[u] * 11 + 10];
+                            qpos[u] = -1;
+                        }
+                    q.count = 0;
+                    continue;
+                }
+                const int rank = __popc(m & lt);
+                if (pending && rank < room) {
+                    const int pos = q.count + rank;
+                    T* it = q.buf + pos * 11;
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+                        it[k] = pp[k];
+                        it[5 + k] = dd[k];
+                    }
+                    it[10] = wv[v];
+                    qpos[v] = pos;
+                    pending = false;
+                }
+                const int cnt = __popc(m);
+                q.count += cnt < room ? cnt : room;
+            }
         }
-        wL[2] = meg7(w[0], w[1], w[2], w[3], w[4], e[0], e[1], e[2], e[3], e[4]);
-        wR[2] = meg7(w[5], w[4], w[3], w[2], w[1], -e[5], -e[4], -e[3], -e[2], -e[1]);
     }
+    if (q.count > 0) {
+        q.flush();
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (qpos[u] >= 0) wv[u] = q.buf[qpos[u] * 11 + 10];
+        q.count = 0;
+    }
+    const T wL[4] = {wv[0], wv[2], wv[4], wv[6]};
+    const T wR[4] = {wv[1], wv[3], wv[5], wv[7]};
     // Back to primitive variables with the right eigenvectors.
     const T crb = cb * irb;
     const T rL = wL[0] + wL[1] + wL[3], unL = crb * (wL[3] - wL[0]), utL = wL[2], pL = c2 * (wL[0] + wL[3]);
@@ -327,7 +410,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
     T* const sFY = sm + L::oFY;
     T* const sHX = sm + L::oHX;
     T* const sHY = sm + L::oHY;
-    unsigned char* const sPX = reinterpret_cast<unsigned char*>(sm + L::nT);
+    unsigned char* const sPX = reinterpret_cast<unsigned char*>(sm + L::template nT<T, NT>());
     unsigned char* const sPY = sPX + L::NPX;
     constexpr int RW = L::RW, NU = L::NU, V = L::V;
 
@@ -363,7 +446,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         sU[3 * NU + idx] = p;
     }
     if constexpr (LEARNED)
-        load_sensor(reinterpret_cast<SensorDev*>(smem_raw + L::template sensor_offset<T>()), P.sensor);
+        load_sensor(reinterpret_cast<SensorDev*>(smem_raw + L::template sensor_offset<T, NT>()), P.sensor);
     __syncthreads();
 
     // Phase 1: per-cell quantities, each computed once per tile.
@@ -392,7 +475,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         // Learned sensor on the tensor cores, 16 cells per warp: 1 = trouble,
         // 0 = smooth, 2 = unsure (the plain detector decides below).
         unsigned char* const sT = sPY + L::NPY;
-        const SensorDev& W = *reinterpret_cast<const SensorDev*>(smem_raw + L::template sensor_offset<T>());
+        const SensorDev& W = *reinterpret_cast<const SensorDev*>(smem_raw + L::template sensor_offset<T, NT>());
         const int nchunks = (L::NBOX + 15) / 16;
         for (int chunk = tid >> 5; chunk < nchunks; chunk += NT / 32) {
             auto cells = [&](int i, const float*& r, const float*& p) {
@@ -466,82 +549,107 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         __syncthreads();
     }
 
-    // Phase 2: every x face and y face of the tile, once.
-    for (int w = tid; w < L::NHX + L::NHY; w += NT) {
-        T out[4];
-        bool smooth;
-        if (w < L::NHX) {
-            const int r = w / L::HXW, f = w - r * L::HXW;
-            const int ry = r + 6, rx = f + 5;  // left cell of the face
+    // Phase 2: every x face and y face of the tile, once. All lanes of a warp
+    // run the same number of rounds (lanes past the last face redo a valid
+    // face and discard it), so the warp-synchronous limiter queue can be used.
+    {
+        constexpr int QCAP = L::template qcap<T>();
+        MpQueue<T, QCAP> q;
+        q.buf = sm + L::oQ + (tid >> 5) * QCAP * 11;
+        q.count = 0;
+        q.lane = tid & 31;
+        constexpr int ROUNDS = (L::NF + NT - 1) / NT;
+        for (int round = 0; round < ROUNDS; ++round) {
+            const int wv = round * NT + tid;
+            const bool valid = wv < L::NF;
+            const int w = valid ? wv : L::NF - 1;
+            const bool xf = w < L::NHX;
             FaceIn<T> in;
-            const T* u = sU + ry * RW + rx;
-            in.u[0] = u;
-            in.u[1] = u + NU;
-            in.u[2] = u + 2 * NU;
-            in.u[3] = u + 3 * NU;
-            in.su = 1;
-            const T* gx = sGX + (r + V) * L::GXW + (rx - 3);
-            in.g[0] = gx;
-            in.g[1] = gx + L::NGX;
-            in.g[2] = gx + 2 * L::NGX;
-            in.g[3] = gx + 3 * L::NGX;
-            in.sg = 1;
-            in.tr = sPX + r * L::PXW + (rx - 3);
-            in.st = 1;
-            const T* fx = sFX + r * L::FXW + (rx - 1);
-            in.f[0] = fx;
-            in.f[1] = fx + L::NFX;
-            in.f[2] = fx + 2 * L::NFX;
-            in.f[3] = fx + 3 * L::NFX;
-            in.sf = 1;
-            const T* ty = sGY + (ry - 3) * L::GYW + (rx - 6 + V);
-            in.tun = ty + L::NGY;      // d u / d y
-            in.tut = ty + 2 * L::NGY;  // d v / d y
-            in.stq = 1;
-            face_flux<T, VISC>(in, ph, inv_dx, inv_dy, out, smooth);
-#pragma unroll
-            for (int m = 0; m < 4; ++m) sHX[m * L::NHX + w] = out[m];
-            if (P.sigx) {
-                const int i = ty0 + r, jf = tx0 + f;
-                if (i < ny && jf <= nx) P.sigx[(long long)i * (nx + 1) + jf] = smooth ? 1 : 0;
+            T inv_n, inv_t;
+            int r = 0, f = 0, c = 0, w2 = 0;
+            if (xf) {
+                r = w / L::HXW;
+                f = w - r * L::HXW;
+                const int ry = r + 6, rx = f + 5;  // left cell of the face
+                const T* u = sU + ry * RW + rx;
+                in.u[0] = u;
+                in.u[1] = u + NU;
+                in.u[2] = u + 2 * NU;
+                in.u[3] = u + 3 * NU;
+                in.su = 1;
+                const T* gx = sGX + (r + V) * L::GXW + (rx - 3);
+                in.g[0] = gx;
+                in.g[1] = gx + L::NGX;
+                in.g[2] = gx + 2 * L::NGX;
+                in.g[3] = gx + 3 * L::NGX;
+                in.sg = 1;
+                in.tr = sPX + r * L::PXW + (rx - 3);
+                in.st = 1;
+                const T* fx = sFX + r * L::FXW + (rx - 1);
+                in.f[0] = fx;
+                in.f[1] = fx + L::NFX;
+                in.f[2] = fx + 2 * L::NFX;
+                in.f[3] = fx + 3 * L::NFX;
+                in.sf = 1;
+                const T* ty = sGY + (ry - 3) * L::GYW + (rx - 6 + V);
+                in.tun = ty + L::NGY;      // d u / d y
+                in.tut = ty + 2 * L::NGY;  // d v / d y
+                in.stq = 1;
+                inv_n = inv_dx;
+                inv_t = inv_dy;
+            } else {
+                w2 = w - L::NHX;
+                f = w2 / BX;
+                c = w2 - f * BX;
+                const int ry = f + 5, rx = c + 6;  // lower cell of the face
+                const T* u = sU + ry * RW + rx;
+                in.u[0] = u;
+                in.u[1] = u + 2 * NU;  // normal velocity v
+                in.u[2] = u + NU;      // tangential velocity u
+                in.u[3] = u + 3 * NU;
+                in.su = RW;
+                const T* gy = sGY + (ry - 3) * L::GYW + (rx - 6 + V);
+                in.g[0] = gy;
+                in.g[1] = gy + 2 * L::NGY;
+                in.g[2] = gy + L::NGY;
+                in.g[3] = gy + 3 * L::NGY;
+                in.sg = L::GYW;
+                in.tr = sPY + (ry - 3) * BX + c;
+                in.st = BX;
+                const T* fy = sFY + (ry - 1) * BX + c;
+                in.f[0] = fy;
+                in.f[1] = fy + 2 * L::NFY;  // rho v^2 + p
+                in.f[2] = fy + L::NFY;      // rho u v
+                in.f[3] = fy + 3 * L::NFY;
+                in.sf = BX;
+                const T* tx = sGX + (ry - 6 + V) * L::GXW + (rx - 3);
+                in.tun = tx + 2 * L::NGX;  // d v / d x
+                in.tut = tx + L::NGX;      // d u / d x
+                in.stq = L::GXW;
+                inv_n = inv_dy;
+                inv_t = inv_dx;
             }
-        } else {
-            const int w2 = w - L::NHX;
-            const int f = w2 / BX, c = w2 - f * BX;
-            const int ry = f + 5, rx = c + 6;  // lower cell of the face
-            FaceIn<T> in;
-            const T* u = sU + ry * RW + rx;
-            in.u[0] = u;
-            in.u[1] = u + 2 * NU;  // normal velocity v
-            in.u[2] = u + NU;      // tangential velocity u
-            in.u[3] = u + 3 * NU;
-            in.su = RW;
-            const T* gy = sGY + (ry - 3) * L::GYW + (rx - 6 + V);
-            in.g[0] = gy;
-            in.g[1] = gy + 2 * L::NGY;
-            in.g[2] = gy + L::NGY;
-            in.g[3] = gy + 3 * L::NGY;
-            in.sg = L::GYW;
-            in.tr = sPY + (ry - 3) * BX + c;
-            in.st = BX;
-            const T* fy = sFY + (ry - 1) * BX + c;
-            in.f[0] = fy;
-            in.f[1] = fy + 2 * L::NFY;  // rho v^2 + p
-            in.f[2] = fy + L::NFY;      // rho u v
-            in.f[3] = fy + 3 * L::NFY;
-            in.sf = BX;
-            const T* tx = sGX + (ry - 6 + V) * L::GXW + (rx - 3);
-            in.tun = tx + 2 * L::NGX;  // d v / d x
-            in.tut = tx + L::NGX;      // d u / d x
-            in.stq = L::GXW;
-            face_flux<T, VISC>(in, ph, inv_dy, inv_dx, out, smooth);
-            sHY[w2] = out[0];
-            sHY[L::NHY + w2] = out[2];
-            sHY[2 * L::NHY + w2] = out[1];
-            sHY[3 * L::NHY + w2] = out[3];
-            if (P.sigy) {
-                const int j = tx0 + c, iface = ty0 + f;
-                if (j < nx && iface <= ny) P.sigy[(long long)iface * nx + j] = smooth ? 1 : 0;
+            T out[4];
+            bool smooth;
+            face_flux<T, VISC, QCAP>(in, ph, inv_n, inv_t, out, smooth, q);
+            if (valid) {
+                if (xf) {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) sHX[m * L::NHX + w] = out[m];
+                    if (P.sigx) {
+                        const int i = ty0 + r, jf = tx0 + f;
+                        if (i < ny && jf <= nx) P.sigx[(long long)i * (nx + 1) + jf] = smooth ? 1 : 0;
+                    }
+                } else {
+                    sHY[w2] = out[0];
+                    sHY[L::NHY + w2] = out[2];
+                    sHY[2 * L::NHY + w2] = out[1];
+                    sHY[3 * L::NHY + w2] = out[3];
+                    if (P.sigy) {
+                        const int j = tx0 + c, iface = ty0 + f;
+                        if (j < nx && iface <= ny) P.sigy[(long long)iface * nx + j] = smooth ? 1 : 0;
+                    }
+                }
             }
         }
     }
@@ -624,7 +732,7 @@ template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED = false>
 cudaError_t launch_stage_t(const StageParams& p, cudaStream_t s)
 {
     using L = TileLayout<BX, BY, VISC>;
-    constexpr size_t smem = L::template total_bytes<T, LEARNED>();
+    constexpr size_t smem = L::template total_bytes<T, NT, LEARNED>();
     static bool configured = false;
     auto kern = stage_kernel<T, BX, BY, NT, VISC, LEARNED>;
     if (!configured) {
