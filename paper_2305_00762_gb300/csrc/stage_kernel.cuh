@@ -550,8 +550,9 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
     }
 
     // Phase 2: every x face and y face of the tile, once. All lanes of a warp
-    // run the same number of rounds (lanes past the last face redo a valid
-    // face and discard it), so the warp-synchronous limiter queue can be used.
+    // run the same rounds (in a warp's last round, lanes past the last face
+    // redo a valid face and discard it), so the warp-synchronous limiter
+    // queue can be used.
     {
         constexpr int QCAP = L::template qcap<T>();
         MpQueue<T, QCAP> q;
@@ -562,6 +563,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         for (int round = 0; round < ROUNDS; ++round) {
             const int wv = round * NT + tid;
             const bool valid = wv < L::NF;
+            if (__all_sync(0xffffffffu, !valid)) break;  // the warp has no face left
             const int w = valid ? wv : L::NF - 1;
             const bool xf = w < L::NHX;
             FaceIn<T> in;
