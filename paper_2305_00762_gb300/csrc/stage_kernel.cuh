@@ -49,17 +49,14 @@ struct TileLayout {
     static constexpr int oFY = oFX + 4 * NFX;
     static constexpr int oHX = oFY + 4 * NFY;
     static constexpr int oHY = oHX + 4 * NHX;
-    static constexpr int oQ = oHY + 4 * NHY;  // MP-limiter work queues, one per warp
+    static constexpr int oEnd = oHY + 4 * NHY;
 
     // learned sensor: per-cell decisions on the bounding box of both
     // detector regions, rows and columns [3, B+9), and the weights
     static constexpr int BOXW = BX + 6, BOXH = BY + 6, NBOX = BOXW * BOXH;
 
-    // Work-queue capacity per warp (items of 10 stencil values + the GRB value).
-    template <typename T>
-    static constexpr int qcap() { return sizeof(T) == 8 ? 16 : 32; }
     template <typename T, int NT>
-    static constexpr int nT() { return oQ + (NT / 32) * qcap<T>() * 11; }  // elements of T
+    static constexpr int nT() { return oEnd; }  // elements of T
     template <typename T, int NT>
     static constexpr size_t bytes() { return sizeof(T) * (size_t)nT<T, NT>() + (size_t)(NPX + NPY) + 16; }
     template <typename T, int NT>
@@ -141,27 +138,17 @@ __device__ __forceinline__ T mp_limit(const T* p, const T* d, T pl)
     return pl + minmod(pmin - pl, pmax - pl);
 }
 
-// Per-warp queue of MP-limiter work (Eq. mp-procedure). Lanes add only the
-// (field, side) values that fail the MP test; a flush evaluates up to QCAP of
-// them at once, one per lane, so the warp pays for the limiter once per batch
-// of failing values instead of once per field and side in which any lane
-// fails. All 32 lanes must call add() and flush() together.
-template <typename T, int QCAP>
-struct MpQueue {
-    T* buf;     // [QCAP][11]: p0..p4, d0..d4, then pl (replaced by the result)
-    int count;  // uniform over the warp
-    int lane;
-
-    __device__ __forceinline__ void flush()
-    {
-        __syncwarp();
-        if (lane < count) {
-            T* it = buf + lane * 11;
-            it[10] = mp_limit(it, it + 5, it[10]);
-        }
-        __syncwarp();
-    }
-};
+// MEG7 left value at j+1/2 from Phi_{j-2..j+2} (p0..p4) and Phi'_{j-2..j+2}
+// (d0..d4): the GRB value, MP-limited where the MP test fails.
+template <typename T>
+__device__ __forceinline__ T meg7(T p0, T p1, T p2, T p3, T p4, T d0, T d1, T d2, T d3, T d4)
+{
+    const T p[5] = {p0, p1, p2, p3, p4}, d[5] = {d0, d1, d2, d3, d4};
+    bool need;
+    const T pl = grb_check(p, d, need);
+    if (!need) return pl;
+    return mp_limit(p, d, pl);
+}
 
 // 1/2 (F(f_L) + F(f_R)) at the face after cell f[0]: the sum of Eq.
 // flux-full and its mirror Eq. flux-right is the symmetric 10-point stencil
@@ -196,9 +183,9 @@ struct PhysT {
 
 // The whole interface procedure of Secs. 2.1-2.4 at face j+1/2. Returns the
 // total flux in face-normal order and the detector flag sigma.
-template <typename T, bool VISC, int QCAP>
+template <typename T, bool VISC>
 __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P, T inv_dn, T inv_dt, T out[4],
-                                          bool& smooth, MpQueue<T, QCAP>& q)
+                                          bool& smooth)
 {
     // Eq. buffer: sigma = 0 if psi_k < psi_c for any k in j-2..j+3.
     bool tr = false;
@@ -218,90 +205,46 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
     const T ic2 = icb * icb;         // 1 / c^2
     const T be = T(0.5) * ic2;       // 1 / (2 c^2)
 
-    // GRB + MP test for the 8 (field, side) values, one characteristic field
-    // at a time (fields: u - c, entropy rho - p/c^2, shear ut, u + c); failing
-    // values go to the warp's limiter queue. The right side is the left
-    // formula on the stencil mirrored about the face (cell j+1-k, gradient
-    // sign flipped).
-    T wv[8];
-    int qpos[8];
-    const unsigned lt = (1u << q.lane) - 1u;
-#pragma unroll
-    for (int fld = 0; fld < 4; ++fld) {
-        T w[6], e[6];  // characteristic values and gradients of cells j-2..j+3
+    T wL[4], wR[4];
+    {  // fields 1 and 4 (u - c and u + c) share un and p
+        T w0[6], w3[6], e0[6], e3[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const int o = (k - 2);
-            if (fld == 0 || fld == 3) {
-                const T tu = al * in.u[1][o * su], tp = be * in.u[3][o * su];
-                const T gu = al * in.g[1][o * sg], gp = be * in.g[3][o * sg];
-                w[k] = fld == 0 ? tp - tu : tp + tu;
-                e[k] = fld == 0 ? gp - gu : gp + gu;
-            } else if (fld == 1) {
-                w[k] = in.u[0][o * su] - ic2 * in.u[3][o * su];
-                e[k] = in.g[0][o * sg] - ic2 * in.g[3][o * sg];
-            } else {
-                w[k] = in.u[2][o * su];
-                e[k] = in.g[2][o * sg];
-            }
+            const T tu = al * in.u[1][o * su], tp = be * in.u[3][o * su];
+            w0[k] = tp - tu;
+            w3[k] = tp + tu;
+            const T gu = al * in.g[1][o * sg], gp = be * in.g[3][o * sg];
+            e0[k] = gp - gu;
+            e3[k] = gp + gu;
         }
+        wL[0] = meg7(w0[0], w0[1], w0[2], w0[3], w0[4], e0[0], e0[1], e0[2], e0[3], e0[4]);
+        wR[0] = meg7(w0[5], w0[4], w0[3], w0[2], w0[1], -e0[5], -e0[4], -e0[3], -e0[2], -e0[1]);
+        wL[3] = meg7(w3[0], w3[1], w3[2], w3[3], w3[4], e3[0], e3[1], e3[2], e3[3], e3[4]);
+        wR[3] = meg7(w3[5], w3[4], w3[3], w3[2], w3[1], -e3[5], -e3[4], -e3[3], -e3[2], -e3[1]);
+    }
+    {  // field 2 (entropy): rho - p / c^2
+        T w[6], e[6];
 #pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const int v = 2 * fld + side;
-            T pp[5], dd[5];
-#pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                pp[k] = side == 0 ? w[k] : w[5 - k];
-                dd[k] = side == 0 ? e[k] : -e[5 - k];
-            }
-            bool pending;
-            wv[v] = grb_check(pp, dd, pending);
-            qpos[v] = -1;
-            // Add the failing lanes in rank order while the queue has room;
-            // when it is full, evaluate it and hand out the results. Every
-            // condition below is uniform over the warp.
-            for (;;) {
-                const unsigned m = __ballot_sync(0xffffffffu, pending);
-                if (m == 0u) break;
-                const int room = QCAP - q.count;
-                if (room == 0) {
-                    q.flush();
-#pragma unroll
-                    for (int u = 0; u <= v; ++u)
-                        if (qpos[u] >= 0) {
-                            wv[u] = q.buf[qpos[u] * 11 + 10];
-                            qpos[u] = -1;
-                        }
-                    q.count = 0;
-                    continue;
-                }
-                const int rank = __popc(m & lt);
-                if (pending && rank < room) {
-                    const int pos = q.count + rank;
-                    T* it = q.buf + pos * 11;
-#pragma unroll
-                    for (int k = 0; k < 5; ++k) {
-                        it[k] = pp[k];
-                        it[5 + k] = dd[k];
-                    }
-                    it[10] = wv[v];
-                    qpos[v] = pos;
-                    pending = false;
-                }
-                const int cnt = __popc(m);
-                q.count += cnt < room ? cnt : room;
-            }
+        for (int k = 0; k < 6; ++k) {
+            const int o = (k - 2);
+            w[k] = in.u[0][o * su] - ic2 * in.u[3][o * su];
+            e[k] = in.g[0][o * sg] - ic2 * in.g[3][o * sg];
         }
+        wL[1] = meg7(w[0], w[1], w[2], w[3], w[4], e[0], e[1], e[2], e[3], e[4]);
+        wR[1] = meg7(w[5], w[4], w[3], w[2], w[1], -e[5], -e[4], -e[3], -e[2], -e[1]);
     }
-    if (q.count > 0) {
-        q.flush();
+    {  // field 3 (shear): ut
+        T w[6], e[6];
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (qpos[u] >= 0) wv[u] = q.buf[qpos[u] * 11 + 10];
-        q.count = 0;
+        for (int k = 0; k < 6; ++k) {
+            const int o = (k - 2);
+            w[k] = in.u[2][o * su];
+            e[k] = in.g[2][o * sg];
+        }
+        wL[2] = meg7(w[0], w[1], w[2], w[3], w[4], e[0], e[1], e[2], e[3], e[4]);
+        wR[2] = meg7(w[5], w[4], w[3], w[2], w[1], -e[5], -e[4], -e[3], -e[2], -e[1]);
     }
-    const T wL[4] = {wv[0], wv[2], wv[4], wv[6]};
-    const T wR[4] = {wv[1], wv[3], wv[5], wv[7]};
     // Back to primitive variables with the right eigenvectors.
     const T crb = cb * irb;
     const T rL = wL[0] + wL[1] + wL[3], unL = crb * (wL[3] - wL[0]), utL = wL[2], pL = c2 * (wL[0] + wL[3]);
@@ -549,22 +492,12 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         __syncthreads();
     }
 
-    // Phase 2: every x face and y face of the tile, once. All lanes of a warp
-    // run the same rounds (in a warp's last round, lanes past the last face
-    // redo a valid face and discard it), so the warp-synchronous limiter
-    // queue can be used.
+    // Phase 2: every x face and y face of the tile, once (one thread per
+    // face; x and y faces share the call, with pointers and strides chosen
+    // per face).
     {
-        constexpr int QCAP = L::template qcap<T>();
-        MpQueue<T, QCAP> q;
-        q.buf = sm + L::oQ + (tid >> 5) * QCAP * 11;
-        q.count = 0;
-        q.lane = tid & 31;
-        constexpr int ROUNDS = (L::NF + NT - 1) / NT;
-        for (int round = 0; round < ROUNDS; ++round) {
-            const int wv = round * NT + tid;
-            const bool valid = wv < L::NF;
-            if (__all_sync(0xffffffffu, !valid)) break;  // the warp has no face left
-            const int w = valid ? wv : L::NF - 1;
+        for (int w = tid; w < L::NF; w += NT) {
+            const bool valid = true;
             const bool xf = w < L::NHX;
             FaceIn<T> in;
             T inv_n, inv_t;
@@ -633,7 +566,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
             }
             T out[4];
             bool smooth;
-            face_flux<T, VISC, QCAP>(in, ph, inv_n, inv_t, out, smooth, q);
+            face_flux<T, VISC>(in, ph, inv_n, inv_t, out, smooth);
             if (valid) {
                 if (xf) {
 #pragma unroll
