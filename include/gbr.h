@@ -89,7 +89,13 @@ typedef enum {
     GBR_OPT_SENSOR = 2,
     /* 1: bracket every kernel launch with CUDA events on the context's
      * stream (read back with gbr_get_timing); 0: off (default). */
-    GBR_OPT_TIMING = 3
+    GBR_OPT_TIMING = 3,
+    /* Order of the gradient-based reconstruction: 7 (default; MEG7, alpha =
+     * 38/7, beta = 3/190 in Eqs. good_6tth-order_scheme_flux and alpha-beta,
+     * Eqs. grb, flux-full, flux-right) or 4 (the alpha = 4, beta = 0 member of
+     * the same family, Sec. 3 Eq. fourth for the flux reconstruction). The MP
+     * limiter, detector, Riemann solver and viscous flux are unchanged. */
+    GBR_OPT_ORDER = 4
 } gbr_option;
 
 /* Kernel classes reported by gbr_get_timing. */

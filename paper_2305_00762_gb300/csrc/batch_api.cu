@@ -169,6 +169,7 @@ int gbr_batch_create(int n, const int* nx, const int* ny, const double* dx, cons
         c.ph.Pr = 1.0;
         c.ph.dx = dx[k];
         c.ph.dy = dy[k];
+        c.ph.order = 7;
         for (int s = 0; s < 4; ++s) c.bc[s] = bc[4 * k + s];
         c.t_end = 1e300;
         c.ghost_begin = ghosts;

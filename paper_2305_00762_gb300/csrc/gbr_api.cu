@@ -234,6 +234,7 @@ int gbr_create(int nx, int ny, double gamma, double mu, double Pr, const gbr_bc*
     c->ph.Pr = Pr;
     c->ph.dx = bc->dx;
     c->ph.dy = bc->dy;
+    c->ph.order = 7;
     c->bc[0] = bc->west;
     c->bc[1] = bc->east;
     c->bc[2] = bc->south;
@@ -401,6 +402,10 @@ int gbr_set_option(gbr_ctx* c, int key, double val)
         if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;
         if (val == 1.0 && !c->d_sensor) return GBR_ERR_STATE;
         c->sensor = (int)val;
+        return GBR_OK;
+    case GBR_OPT_ORDER:
+        if (val != 7.0 && val != 4.0) return GBR_ERR_ARG;
+        c->ph.order = (int)val;
         return GBR_OK;
     case GBR_OPT_TIMING:
         if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;

@@ -28,6 +28,7 @@ struct Grid {
 
 struct Physics {
     double gamma, mu, Pr, dx, dy;
+    int order;  // 7: MEG7 (alpha = 38/7, beta = 3/190); 4: the alpha = 4, beta = 0 member
 };
 
 struct SensorDev;

@@ -106,17 +106,59 @@ __device__ __forceinline__ bool trouble_cell(const T* r, int st)
     return T(2) * (T(2) * a * b + eps) < a * a + b * b + eps;
 }
 
-// Eq. grb and the MP test of Eqs. mp5Condition and alpha for the left value
+// The GRB left value and the MP test of Eqs. mp5Condition and alpha for the left value
 // at j+1/2 from Phi_{j-2..j+2} (p[0..4]) and Phi'_{j-2..j+2} (d[0..4]),
 // xi = 7. Returns the GRB value; `need` is set when the MP limiter must be
 // applied. The GRB weights of Phi sum to one (478 + 2*178 + 2*3 = 840), so
 // Eq. grb is evaluated as Phi_j plus weighted differences: on flat data Phi^L
 // equals Phi_j exactly and the test passes (the limiter would return Phi_j).
+// Weights of the left value Phi_j + (w0 Phi'_j + w1 (Phi'_{j-1} - Phi'_{j+1})
+// + w2 (D_{-1} + D_{+1}) + w3 (D_{-2} + D_{+2})) / 840 with D_k = Phi_{j+k} -
+// Phi_j, and of 1/2 (F(f_L) + F(f_R)) = sum_k c_k (f_{j+1-k} + f_{j+k}) / den.
+// Order 7: Eq. grb and Eqs. flux-full/flux-right. Order 4 (alpha = 4,
+// beta = 0 in Eqs. good_6tth-order_scheme_flux and alpha-beta):
+// Phi^L = Phi_j + Phi'_j/2 + (Phi'_{j-1} - Phi'_{j+1})/24 + (D_{-1} + D_{+1})/6,
+// and Eq. fourth with its mirror.
 template <typename T>
-__device__ __forceinline__ T grb_check(const T* p, const T* d, bool& need)
+struct GrbCoef {
+    T w1, w2, w3;          // w0 = 420 for both orders
+    T c1, c2, c3, c4, c5;  // pairs (j, j+1), (j-1, j+2), ..., (j-4, j+5)
+    T inv_den;
+};
+
+template <typename T>
+__device__ __forceinline__ GrbCoef<T> grb_coef(int order)
 {
-    const T pl = p[2] + (T(420) * d[2] + T(60) * (d[1] - d[3]) + T(178) * ((p[1] - p[2]) + (p[3] - p[2])) +
-                         T(3) * ((p[0] - p[2]) + (p[4] - p[2]))) *
+    GrbCoef<T> c;
+    if (order == 4) {
+        c.w1 = T(35);
+        c.w2 = T(140);
+        c.w3 = T(0);
+        c.c1 = T(1821);
+        c.c2 = T(-461);
+        c.c3 = T(85);
+        c.c4 = T(-4);
+        c.c5 = T(-1);
+        c.inv_den = T(1.0 / 2880.0);
+    } else {
+        c.w1 = T(60);
+        c.w2 = T(178);
+        c.w3 = T(3);
+        c.c1 = T(1052);
+        c.c2 = T(-250);
+        c.c3 = T(38);
+        c.c4 = T(1);
+        c.c5 = T(-1);
+        c.inv_den = T(1.0 / 1680.0);
+    }
+    return c;
+}
+
+template <typename T>
+__device__ __forceinline__ T grb_check(const T* p, const T* d, bool& need, const GrbCoef<T>& C)
+{
+    const T pl = p[2] + (T(420) * d[2] + C.w1 * (d[1] - d[3]) + C.w2 * ((p[1] - p[2]) + (p[3] - p[2])) +
+                         C.w3 * ((p[0] - p[2]) + (p[4] - p[2]))) *
                             T(1.0 / 840.0);
     const T pmp = p[2] + minmod(p[3] - p[2], T(7) * (p[2] - p[1]));
     need = !((pl - p[2]) * (pl - pmp) <= T(1e-40));
@@ -141,11 +183,11 @@ __device__ __forceinline__ T mp_limit(const T* p, const T* d, T pl)
 // MEG7 left value at j+1/2 from Phi_{j-2..j+2} (p0..p4) and Phi'_{j-2..j+2}
 // (d0..d4): the GRB value, MP-limited where the MP test fails.
 template <typename T>
-__device__ __forceinline__ T meg7(T p0, T p1, T p2, T p3, T p4, T d0, T d1, T d2, T d3, T d4)
+__device__ __forceinline__ T meg7(const GrbCoef<T>& C, T p0, T p1, T p2, T p3, T p4, T d0, T d1, T d2, T d3, T d4)
 {
     const T p[5] = {p0, p1, p2, p3, p4}, d[5] = {d0, d1, d2, d3, d4};
     bool need;
-    const T pl = grb_check(p, d, need);
+    const T pl = grb_check(p, d, need, C);
     if (!need) return pl;
     return mp_limit(p, d, pl);
 }
@@ -154,11 +196,11 @@ __device__ __forceinline__ T meg7(T p0, T p1, T p2, T p3, T p4, T d0, T d1, T d2
 // flux-full and its mirror Eq. flux-right is the symmetric 10-point stencil
 // (-1, 1, 38, -250, 1052 | 1052, -250, 38, 1, -1) / 840 over f_{j-4..j+5}.
 template <typename T>
-__device__ __forceinline__ T recon_mean(const T* f, int s)
+__device__ __forceinline__ T recon_mean(const T* f, int s, const GrbCoef<T>& C)
 {
-    return (T(1052) * (f[0] + f[s]) - T(250) * (f[-s] + f[2 * s]) + T(38) * (f[-2 * s] + f[3 * s]) +
-            (f[-3 * s] + f[4 * s]) - (f[-4 * s] + f[5 * s])) *
-           T(1.0 / 1680.0);
+    return (C.c1 * (f[0] + f[s]) + C.c2 * (f[-s] + f[2 * s]) + C.c3 * (f[-2 * s] + f[3 * s]) +
+            C.c4 * (f[-3 * s] + f[4 * s]) + C.c5 * (f[-4 * s] + f[5 * s])) *
+           C.inv_den;
 }
 
 template <typename T>
@@ -183,10 +225,11 @@ struct PhysT {
 
 // The whole interface procedure of Secs. 2.1-2.4 at face j+1/2. Returns the
 // total flux in face-normal order and the detector flag sigma.
-template <typename T, bool VISC>
+template <typename T, bool VISC, int ORDER>
 __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P, T inv_dn, T inv_dt, T out[4],
                                           bool& smooth)
 {
+    const GrbCoef<T> coef = grb_coef<T>(ORDER);  // compile-time constants
     // Eq. buffer: sigma = 0 if psi_k < psi_c for any k in j-2..j+3.
     bool tr = false;
 #pragma unroll
@@ -218,10 +261,10 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
             e0[k] = gp - gu;
             e3[k] = gp + gu;
         }
-        wL[0] = meg7(w0[0], w0[1], w0[2], w0[3], w0[4], e0[0], e0[1], e0[2], e0[3], e0[4]);
-        wR[0] = meg7(w0[5], w0[4], w0[3], w0[2], w0[1], -e0[5], -e0[4], -e0[3], -e0[2], -e0[1]);
-        wL[3] = meg7(w3[0], w3[1], w3[2], w3[3], w3[4], e3[0], e3[1], e3[2], e3[3], e3[4]);
-        wR[3] = meg7(w3[5], w3[4], w3[3], w3[2], w3[1], -e3[5], -e3[4], -e3[3], -e3[2], -e3[1]);
+        wL[0] = meg7(coef, w0[0], w0[1], w0[2], w0[3], w0[4], e0[0], e0[1], e0[2], e0[3], e0[4]);
+        wR[0] = meg7(coef, w0[5], w0[4], w0[3], w0[2], w0[1], -e0[5], -e0[4], -e0[3], -e0[2], -e0[1]);
+        wL[3] = meg7(coef, w3[0], w3[1], w3[2], w3[3], w3[4], e3[0], e3[1], e3[2], e3[3], e3[4]);
+        wR[3] = meg7(coef, w3[5], w3[4], w3[3], w3[2], w3[1], -e3[5], -e3[4], -e3[3], -e3[2], -e3[1]);
     }
     {  // field 2 (entropy): rho - p / c^2
         T w[6], e[6];
@@ -231,8 +274,8 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
             w[k] = in.u[0][o * su] - ic2 * in.u[3][o * su];
             e[k] = in.g[0][o * sg] - ic2 * in.g[3][o * sg];
         }
-        wL[1] = meg7(w[0], w[1], w[2], w[3], w[4], e[0], e[1], e[2], e[3], e[4]);
-        wR[1] = meg7(w[5], w[4], w[3], w[2], w[1], -e[5], -e[4], -e[3], -e[2], -e[1]);
+        wL[1] = meg7(coef, w[0], w[1], w[2], w[3], w[4], e[0], e[1], e[2], e[3], e[4]);
+        wR[1] = meg7(coef, w[5], w[4], w[3], w[2], w[1], -e[5], -e[4], -e[3], -e[2], -e[1]);
     }
     {  // field 3 (shear): ut
         T w[6], e[6];
@@ -242,8 +285,8 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
             w[k] = in.u[2][o * su];
             e[k] = in.g[2][o * sg];
         }
-        wL[2] = meg7(w[0], w[1], w[2], w[3], w[4], e[0], e[1], e[2], e[3], e[4]);
-        wR[2] = meg7(w[5], w[4], w[3], w[2], w[1], -e[5], -e[4], -e[3], -e[2], -e[1]);
+        wL[2] = meg7(coef, w[0], w[1], w[2], w[3], w[4], e[0], e[1], e[2], e[3], e[4]);
+        wR[2] = meg7(coef, w[5], w[4], w[3], w[2], w[1], -e[5], -e[4], -e[3], -e[2], -e[1]);
     }
     // Back to primitive variables with the right eigenvectors.
     const T crb = cb * irb;
@@ -259,7 +302,7 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
     T Fc[4];
     if (smooth) {
 #pragma unroll
-        for (int m = 0; m < 4; ++m) Fc[m] = recon_mean(in.f[m], in.sf);
+        for (int m = 0; m < 4; ++m) Fc[m] = recon_mean(in.f[m], in.sf, coef);
     } else {
         Fc[0] = T(0.5) * (QL[1] + QR[1]);
         Fc[1] = T(0.5) * ((QL[1] * unL + pL) + (QR[1] * unR + pR));
@@ -340,7 +383,7 @@ __device__ __forceinline__ double warp_max(double v)
 // the single-grid kernel (one CTA per tile) and the persistent batch kernel
 // (a CTA walks many tiles of many grids). Starts and ends with all threads
 // synchronised, so consecutive calls may reuse the shared memory.
-template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED = false>
+template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED = false, int ORDER = 7>
 __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, const int ty0,
                                            unsigned char* smem_raw)
 {
@@ -566,7 +609,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
             }
             T out[4];
             bool smooth;
-            face_flux<T, VISC>(in, ph, inv_n, inv_t, out, smooth);
+            face_flux<T, VISC, ORDER>(in, ph, inv_n, inv_t, out, smooth);
             if (valid) {
                 if (xf) {
 #pragma unroll
@@ -656,20 +699,20 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
     __syncthreads();
 }
 
-template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED>
+template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED, int ORDER>
 __global__ void __launch_bounds__(NT) stage_kernel(const StageParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    stage_tile<T, BX, BY, NT, VISC, LEARNED>(P, blockIdx.x * BX, blockIdx.y * BY, smem_raw);
+    stage_tile<T, BX, BY, NT, VISC, LEARNED, ORDER>(P, blockIdx.x * BX, blockIdx.y * BY, smem_raw);
 }
 
-template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED = false>
+template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED = false, int ORDER = 7>
 cudaError_t launch_stage_t(const StageParams& p, cudaStream_t s)
 {
     using L = TileLayout<BX, BY, VISC>;
     constexpr size_t smem = L::template total_bytes<T, NT, LEARNED>();
     static bool configured = false;
-    auto kern = stage_kernel<T, BX, BY, NT, VISC, LEARNED>;
+    auto kern = stage_kernel<T, BX, BY, NT, VISC, LEARNED, ORDER>;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -222,3 +222,24 @@ def test_full_size_sampled(env, which):
     assert max(np.abs(Ro[m][sel]).max() for m in range(4)) > 0   # samples hit the discontinuities
     assert max(errs) <= TOL64, errs
     s.close()
+
+
+@pytest.mark.parametrize("name,make", [("vortex64", lambda: C.isentropic_vortex(64)),
+                                       ("riemann70x45", lambda: C.riemann_2d(70, 45)),
+                                       ("vst45x29", lambda: C.viscous_shock_tube(45, 29))],
+                         ids=["vortex64", "riemann70x45", "vst45x29"])
+def test_fourth_order_member(env, name, make):
+    """GBR_OPT_ORDER = 4 (alpha = 4, beta = 0, Eq. fourth) against the oracle
+    with order = 4: residual and one RK3 step."""
+    torch, O, gbr = env
+    c = make()
+    cfg = O.Config(c.nx, c.ny, c.dx, c.dy, c.gamma, c.mu, c.Pr, c.bc, 4)
+    s = gbr.Solver.for_case(c, order=4)
+    s.set_state(c.Q)
+    assert_residual_close(s.residual(), O.residual(cfg, c.Q), c.Q, c, what=f"{name} order-4 residual")
+    dt = c.cfl / O.max_wavespeed(cfg, c.Q)
+    s.step(dt)
+    Qo, rc = O.rk3_step(cfg, c.Q, dt)
+    assert rc == 0
+    assert_state_close(s.get_state(), Qo, what=f"{name} order-4 step")
+    s.close()

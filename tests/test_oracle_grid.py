@@ -187,3 +187,20 @@ def test_max_wavespeed_closed_form(oracle_mod):
     c.mu = 5.0
     lam = O.max_wavespeed(cfg_of(O, c), c.Q)
     assert abs(lam - 4 * (5.0 / 1.3) / min(c.dx, c.dy) ** 2) < 1e-13 * lam
+
+
+def test_fourth_order_member_truncation(oracle_mod):
+    """Remark after Eq. grb: alpha = 4, beta = 0 (with Eq. fourth) is the
+    fourth-order scheme: residual truncation order ~4 on the vortex."""
+    O = oracle_mod
+    errs = []
+    for n in (64, 128, 256):
+        c = C.isentropic_vortex(n)
+        cfg = O.Config(n, n, c.dx, c.dy, 1.4, 0.0, 0.72, c.bc, 4)
+        R = O.residual(cfg, c.Q)
+        xc, _ = C.centres(n, 0.0, 10.0)
+        X, Y = np.meshgrid(xc, xc)
+        mask = np.hypot(X - 5, Y - 5) < 3
+        errs.append(np.abs(R - _vortex_dqdt(X, Y))[:, mask].max())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert (orders > 3.6).all() and (orders < 4.6).all(), orders
