@@ -60,7 +60,7 @@ class _Cfg(ctypes.Structure):
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("mu", ctypes.c_double),
                 ("Pr", ctypes.c_double), ("bc", ctypes.c_int * 4),
-                ("order", ctypes.c_int)]
+                ("order", ctypes.c_int), ("cons", ctypes.c_int)]
 
 
 def lib():
@@ -96,6 +96,8 @@ def lib():
             L.or_max_wavespeed.argtypes = [cp, dp]
             L.or_fill_ghosts_padded.restype = ctypes.c_int
             L.or_fill_ghosts_padded.argtypes = [cp, dp]
+            L.or_cons_eigenvectors.restype = None
+            L.or_cons_eigenvectors.argtypes = [ctypes.c_double, dp, dp, dp]
             L.or_trouble_labels.restype = ctypes.c_int
             L.or_trouble_labels.argtypes = [cp, dp, u8]
             L.or_num_threads.restype = ctypes.c_int
@@ -133,10 +135,11 @@ class Config:
     Pr: float = 0.72
     bc: tuple = (BC_PERIODIC,) * 4   # west, east, south, north
     order: int = 7
+    cons: int = 0                    # 1: MEG7-cons (conservative reconstruction)
 
     def c(self) -> _Cfg:
         return _Cfg(self.nx, self.ny, self.dx, self.dy, self.gamma, self.mu,
-                    self.Pr, (ctypes.c_int * 4)(*self.bc), self.order)
+                    self.Pr, (ctypes.c_int * 4)(*self.bc), self.order, self.cons)
 
 
 # ---- scalar building blocks (pins) ----------------------------------------
@@ -237,6 +240,15 @@ def fill_ghosts_padded(cfg: Config, Qp) -> np.ndarray:
     if rc != 0:
         raise RuntimeError(f"oracle ghost fill failed: {rc}")
     return Qp
+
+
+def cons_eigenvectors(gamma, w):
+    """(L, R) eigenvector matrices of the conservative x-flux Jacobian at
+    primitive state w = (rho, u, v, p)."""
+    L = np.zeros(16)
+    R = np.zeros(16)
+    lib().or_cons_eigenvectors(float(gamma), _dp(_vec(w, 4)), _dp(L), _dp(R))
+    return L.reshape(4, 4), R.reshape(4, 4)
 
 
 def trouble_labels(cfg: Config, Q) -> np.ndarray:

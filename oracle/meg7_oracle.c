@@ -45,6 +45,12 @@
  *      rho', p'; heat conductivity mu/(Pr (gamma-1)) (Eq. visc-interface).
  *  R9  G = 6 ghost layers: the LC bound at j+1/2 uses d_{j-1}, which uses
  *      Phi'_{j-2}, which uses Phi_{j-5}.
+ *  R10 MEG7-cons (Sec. 2.2, conservative reconstruction): Q and its
+ *      sixth-order gradients are projected with the left eigenvectors of the
+ *      conservative flux Jacobian frozen at the same mean state as in R2
+ *      (H = c^2/(gamma-1) + (u^2+v^2)/2); the viscous terms take u', v' from
+ *      the chain rule printed in Sec. 2.2 and T' = gamma (p'/rho - p rho'/rho^2)
+ *      with p' = (gamma-1)(E' - u (rho u)' - v (rho v)' + (u^2+v^2) rho'/2).
  */
 #include <math.h>
 #include <stddef.h>
@@ -62,6 +68,7 @@ typedef struct {
     double gamma, mu, Pr;     /* ratio of specific heats, viscosity, Prandtl */
     int bc[4];                /* west, east, south, north (OR_BC_*) */
     int order;                /* 7 = MEG7 (Eq. grb / flux-full); 4 = alpha=4, beta=0 subset */
+    int cons;                 /* 0 = MEG7-prim (reconstruct U), 1 = MEG7-cons (reconstruct Q) */
 } or_cfg;
 
 /* ---------------------------------------------------------------------- */
@@ -370,25 +377,45 @@ void or_fill_ghosts(const or_cfg *c, double *Qp)
  * `st` the step along the tangential direction; dn and dtn are the cell sizes
  * along and across the sweep. Writes the total flux (convective + viscous) in
  * face-normal order and the detector flag sigma. */
-static void face_flux(const or_cfg *c, const double *const P[4], ptrdiff_t at, ptrdiff_t s, ptrdiff_t st,
-                      double dn, double dtn, double *Fh, int *sigma_out)
+/* Primitive (rho, un, ut, p) dx-scaled gradient of a cell from its
+ * conservative state q and conservative gradient dq (reading R10). */
+static void prim_gradient_from_cons(double gamma, const double *q, const double *dq, double *dw)
+{
+    double rho = q[0], u = q[1] / rho, v = q[2] / rho;
+    dw[0] = dq[0];
+    dw[1] = (rho * dq[1] - q[1] * dq[0]) / (rho * rho); /* Sec. 2.2 chain rule */
+    dw[2] = (rho * dq[2] - q[2] * dq[0]) / (rho * rho);
+    dw[3] = (gamma - 1.0) * (dq[3] - u * dq[1] - v * dq[2] + 0.5 * (u * u + v * v) * dq[0]);
+}
+
+static void face_flux(const or_cfg *c, const double *const P[4], const double *const Cq[4], ptrdiff_t at,
+                      ptrdiff_t s, ptrdiff_t st, double dn, double dtn, double *Fh, int *sigma_out)
 {
     const double g = c->gamma;
     const int order = c->order;
     double U[12][4]; /* U[k+5] = primitive state of cell j+k, k = -5..6 */
+    double V[12][4]; /* the reconstructed variables: U (prim) or Q (cons) */
     for (int k = -5; k <= 6; ++k)
-        for (int m = 0; m < 4; ++m)
+        for (int m = 0; m < 4; ++m) {
             U[k + 5][m] = P[m][at + k * s];
+            V[k + 5][m] = c->cons ? Cq[m][at + k * s] : U[k + 5][m];
+        }
 
-    /* Eq. six: dx-scaled gradients of cells j-2..j+3 (D[k+2]). */
-    double D[6][4];
+    /* Eq. six: dx-scaled gradients of cells j-2..j+3 (D[k+2]) of the
+     * reconstructed variables; DU: the primitive ones (viscous terms). */
+    double D[6][4], DU[6][4];
     for (int k = -2; k <= 3; ++k) {
         for (int m = 0; m < 4; ++m) {
             double st7[7];
             for (int l = 0; l < 7; ++l)
-                st7[l] = U[k + 5 - 3 + l][m];
+                st7[l] = V[k + 5 - 3 + l][m];
             D[k + 2][m] = or_grad6(st7);
         }
+        if (c->cons)
+            prim_gradient_from_cons(g, V[k + 5], D[k + 2], DU[k + 2]);
+        else
+            for (int m = 0; m < 4; ++m)
+                DU[k + 2][m] = D[k + 2][m];
     }
 
     /* Eqs. detector and buffer: sigma = 0 if min(psi_{j-2..j+3}) < psi_c. */
@@ -402,28 +429,52 @@ static void face_flux(const or_cfg *c, const double *const P[4], ptrdiff_t at, p
     int sigma = (psimin < 0.5) ? 0 : 1;
     *sigma_out = sigma;
 
-    /* Reading R2: eigenvectors of the primitive Jacobian at the mean state. */
+    /* Reading R2: eigenvectors of the primitive Jacobian at the mean state
+     * (R10: of the conservative Jacobian for MEG7-cons). */
     double rb = 0.5 * (U[5][0] + U[6][0]);
     double pb = 0.5 * (U[5][3] + U[6][3]);
     double cb = sqrt(g * pb / rb);
-    const double Lm[4][4] = {
-        {0.0, -rb / (2.0 * cb), 0.0, 1.0 / (2.0 * cb * cb)},
-        {1.0, 0.0, 0.0, -1.0 / (cb * cb)},
-        {0.0, 0.0, 1.0, 0.0},
-        {0.0, rb / (2.0 * cb), 0.0, 1.0 / (2.0 * cb * cb)},
-    };
-    const double Rm[4][4] = {/* columns are the right eigenvectors */
-                             {1.0, 1.0, 0.0, 1.0},
-                             {-cb / rb, 0.0, 0.0, cb / rb},
-                             {0.0, 0.0, 1.0, 0.0},
-                             {cb * cb, 0.0, 0.0, cb * cb}};
+    double Lm[4][4], Rm[4][4];
+    if (!c->cons) {
+        const double L0[4][4] = {
+            {0.0, -rb / (2.0 * cb), 0.0, 1.0 / (2.0 * cb * cb)},
+            {1.0, 0.0, 0.0, -1.0 / (cb * cb)},
+            {0.0, 0.0, 1.0, 0.0},
+            {0.0, rb / (2.0 * cb), 0.0, 1.0 / (2.0 * cb * cb)},
+        };
+        const double R0[4][4] = {/* columns are the right eigenvectors */
+                                 {1.0, 1.0, 0.0, 1.0},
+                                 {-cb / rb, 0.0, 0.0, cb / rb},
+                                 {0.0, 0.0, 1.0, 0.0},
+                                 {cb * cb, 0.0, 0.0, cb * cb}};
+        memcpy(Lm, L0, sizeof(Lm));
+        memcpy(Rm, R0, sizeof(Rm));
+    } else {
+        double ub = 0.5 * (U[5][1] + U[6][1]), vb = 0.5 * (U[5][2] + U[6][2]);
+        double q2 = ub * ub + vb * vb;
+        double Hb = cb * cb / (g - 1.0) + 0.5 * q2;
+        double b1 = (g - 1.0) / (cb * cb), b2 = 0.5 * q2 * b1;
+        const double L1[4][4] = {
+            {0.5 * (b2 + ub / cb), -0.5 * (b1 * ub + 1.0 / cb), -0.5 * b1 * vb, 0.5 * b1},
+            {1.0 - b2, b1 * ub, b1 * vb, -b1},
+            {-vb, 0.0, 1.0, 0.0},
+            {0.5 * (b2 - ub / cb), -0.5 * (b1 * ub - 1.0 / cb), -0.5 * b1 * vb, 0.5 * b1},
+        };
+        const double R1[4][4] = {/* columns r1..r4 */
+                                 {1.0, 1.0, 0.0, 1.0},
+                                 {ub - cb, ub, 0.0, ub + cb},
+                                 {vb, vb, 1.0, vb},
+                                 {Hb - ub * cb, 0.5 * q2, vb, Hb + ub * cb}};
+        memcpy(Lm, L1, sizeof(Lm));
+        memcpy(Rm, R1, sizeof(Rm));
+    }
     /* characteristic values and gradients of cells j-2..j+3 */
     double Wc[6][4], Wd[6][4];
     for (int k = 0; k < 6; ++k) {
         for (int a = 0; a < 4; ++a) {
             double sv = 0.0, sd = 0.0;
             for (int b = 0; b < 4; ++b) {
-                sv += Lm[a][b] * U[k + 3][b];
+                sv += Lm[a][b] * V[k + 3][b];
                 sd += Lm[a][b] * D[k][b];
             }
             Wc[k][a] = sv;
@@ -455,6 +506,13 @@ static void face_flux(const or_cfg *c, const double *const P[4], ptrdiff_t at, p
         UL[b] = sl;
         UR[b] = sr;
     }
+    if (c->cons) { /* the reconstructed face states are conservative */
+        double qL[4], qR[4];
+        memcpy(qL, UL, sizeof(qL));
+        memcpy(qR, UR, sizeof(qR));
+        cons_to_prim(g, qL, UL);
+        cons_to_prim(g, qR, UR);
+    }
 
     /* Hybrid face fluxes (Sec. 2.4): F(f) of Eqs. flux-full/flux-right where
      * sigma = 1, F(Q_L), F(Q_R) of the MEG7 states where sigma = 0. */
@@ -483,20 +541,34 @@ static void face_flux(const or_cfg *c, const double *const P[4], ptrdiff_t at, p
          * gradient by the chain rule from rho' and p'. */
         const double av = 4.0, mu = c->mu;
         double T0 = g * U[5][3] / U[5][0], T1 = g * U[6][3] / U[6][0];
-        double dT0 = g * (D[2][3] / U[5][0] - U[5][3] * D[2][0] / (U[5][0] * U[5][0]));
-        double dT1 = g * (D[3][3] / U[6][0] - U[6][3] * D[3][0] / (U[6][0] * U[6][0]));
+        double dT0 = g * (DU[2][3] / U[5][0] - U[5][3] * DU[2][0] / (U[5][0] * U[5][0]));
+        double dT1 = g * (DU[3][3] / U[6][0] - U[6][3] * DU[3][0] / (U[6][0] * U[6][0]));
         /* Eq. alphad with Phi' = dx dPhi/dx: normal derivatives at the face */
-        double un_n = 0.5 * (D[2][1] + D[3][1]) / dn + av / (2.0 * dn) * (U[6][1] - 0.5 * D[3][1] - U[5][1] - 0.5 * D[2][1]);
-        double ut_n = 0.5 * (D[2][2] + D[3][2]) / dn + av / (2.0 * dn) * (U[6][2] - 0.5 * D[3][2] - U[5][2] - 0.5 * D[2][2]);
+        double un_n = 0.5 * (DU[2][1] + DU[3][1]) / dn + av / (2.0 * dn) * (U[6][1] - 0.5 * DU[3][1] - U[5][1] - 0.5 * DU[2][1]);
+        double ut_n = 0.5 * (DU[2][2] + DU[3][2]) / dn + av / (2.0 * dn) * (U[6][2] - 0.5 * DU[3][2] - U[5][2] - 0.5 * DU[2][2]);
         double T_n = 0.5 * (dT0 + dT1) / dn + av / (2.0 * dn) * (T1 - 0.5 * dT1 - T0 - 0.5 * dT0);
         /* tangential derivatives: mean of the cell-centre sixth-order values */
         double tg[2][2];
         for (int q = 0; q < 2; ++q) {
-            for (int m = 1; m <= 2; ++m) {
-                double st7[7];
-                for (int l = 0; l < 7; ++l)
-                    st7[l] = P[m][at + q * s + (l - 3) * st];
-                tg[q][m - 1] = or_grad6(st7) / dtn;
+            if (!c->cons) {
+                for (int m = 1; m <= 2; ++m) {
+                    double st7[7];
+                    for (int l = 0; l < 7; ++l)
+                        st7[l] = P[m][at + q * s + (l - 3) * st];
+                    tg[q][m - 1] = or_grad6(st7) / dtn;
+                }
+            } else { /* chain rule from the conservative tangential gradients */
+                double qc[4], dq[4], dw[4];
+                for (int m = 0; m < 4; ++m) {
+                    double st7[7];
+                    for (int l = 0; l < 7; ++l)
+                        st7[l] = Cq[m][at + q * s + (l - 3) * st];
+                    dq[m] = or_grad6(st7);
+                    qc[m] = Cq[m][at + q * s];
+                }
+                prim_gradient_from_cons(g, qc, dq, dw);
+                tg[q][0] = dw[1] / dtn;
+                tg[q][1] = dw[2] / dtn;
             }
         }
         double un_t = 0.5 * (tg[0][0] + tg[1][0]);
@@ -519,6 +591,8 @@ static int cfg_ok(const or_cfg *c)
         || !(c->Pr > 0.0))
         return 0;
     if (c->order != 7 && c->order != 4)
+        return 0;
+    if (c->cons != 0 && c->cons != 1)
         return 0;
     for (int k = 0; k < 4; ++k)
         if (c->bc[k] < 0 || c->bc[k] > 3)
@@ -565,6 +639,8 @@ int or_residual(const or_cfg *c, const double *Q, double *Res, unsigned char *si
     }
     const double *Px[4] = {Up, Up + N, Up + 2 * N, Up + 3 * N};     /* (rho, u, v, p) */
     const double *Py[4] = {Up, Up + 2 * N, Up + N, Up + 3 * N};     /* (rho, v, u, p) */
+    const double *Cx[4] = {Qp, Qp + N, Qp + 2 * N, Qp + 3 * N};     /* (rho, rho u, rho v, E) */
+    const double *Cy[4] = {Qp, Qp + 2 * N, Qp + N, Qp + 3 * N};     /* (rho, rho v, rho u, E) */
 
     /* x faces j+1/2, j = -1..nx-1, of every interior row */
 #pragma omp parallel for schedule(dynamic, 1)
@@ -577,7 +653,7 @@ int or_residual(const or_cfg *c, const double *Q, double *Res, unsigned char *si
             }
             double fh[4];
             int sg;
-            face_flux(c, Px, pidx(c, j, i), 1, W, c->dx, c->dy, fh, &sg);
+            face_flux(c, Px, Cx, pidx(c, j, i), 1, W, c->dx, c->dy, fh, &sg);
             for (int m = 0; m < 4; ++m)
                 FX[((size_t)m * ny + i) * (nx + 1) + (j + 1)] = fh[m];
             if (sigx)
@@ -595,7 +671,7 @@ int or_residual(const or_cfg *c, const double *Q, double *Res, unsigned char *si
             }
             double fh[4];
             int sg;
-            face_flux(c, Py, pidx(c, j, i), W, 1, c->dy, c->dx, fh, &sg);
+            face_flux(c, Py, Cy, pidx(c, j, i), W, 1, c->dy, c->dx, fh, &sg);
             /* back from (rho, rho v, rho u, E) to (rho, rho u, rho v, E) */
             double gq[4] = {fh[0], fh[2], fh[1], fh[3]};
             for (int m = 0; m < 4; ++m)
@@ -736,6 +812,25 @@ int or_trouble_labels(const or_cfg *c, const double *Q, unsigned char *label)
     }
     free(Qp);
     return OR_OK;
+}
+
+/* Pin helper: the left (rows) and right (columns) eigenvector matrices of
+ * the x-direction conservative flux Jacobian at primitive state w (R10). */
+void or_cons_eigenvectors(double g, const double *w, double *L, double *R)
+{
+    double ub = w[1], vb = w[2], cb = sqrt(g * w[3] / w[0]);
+    double q2 = ub * ub + vb * vb, Hb = cb * cb / (g - 1.0) + 0.5 * q2;
+    double b1 = (g - 1.0) / (cb * cb), b2 = 0.5 * q2 * b1;
+    const double L1[16] = {0.5 * (b2 + ub / cb), -0.5 * (b1 * ub + 1.0 / cb), -0.5 * b1 * vb, 0.5 * b1,
+                           1.0 - b2, b1 * ub, b1 * vb, -b1,
+                           -vb, 0.0, 1.0, 0.0,
+                           0.5 * (b2 - ub / cb), -0.5 * (b1 * ub - 1.0 / cb), -0.5 * b1 * vb, 0.5 * b1};
+    const double R1[16] = {1.0, 1.0, 0.0, 1.0,
+                           ub - cb, ub, 0.0, ub + cb,
+                           vb, vb, 1.0, vb,
+                           Hb - ub * cb, 0.5 * q2, vb, Hb + ub * cb};
+    memcpy(L, L1, sizeof(L1));
+    memcpy(R, R1, sizeof(R1));
 }
 
 /* Pin helper: fill ghosts of a padded state given as 4 planes of
