@@ -95,7 +95,14 @@ typedef enum {
      * Eqs. grb, flux-full, flux-right) or 4 (the alpha = 4, beta = 0 member of
      * the same family, Sec. 3 Eq. fourth for the flux reconstruction). The MP
      * limiter, detector, Riemann solver and viscous flux are unchanged. */
-    GBR_OPT_ORDER = 4
+    GBR_OPT_ORDER = 4,
+    /* Reconstructed variables: 0 = primitive (MEG7-prim, default), 1 =
+     * conservative (MEG7-cons: Q and its gradients projected with the
+     * eigenvectors of the conservative flux Jacobian; the viscous terms take
+     * their velocity and temperature gradients from the conservative ones by
+     * the chain rule of Sec. 2.2). Order 7 only; the learned sensor is not
+     * used with it (the density detector decides). */
+    GBR_OPT_VARIABLES = 5
 } gbr_option;
 
 /* Kernel classes reported by gbr_get_timing. */

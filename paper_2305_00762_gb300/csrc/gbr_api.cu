@@ -405,7 +405,13 @@ int gbr_set_option(gbr_ctx* c, int key, double val)
         return GBR_OK;
     case GBR_OPT_ORDER:
         if (val != 7.0 && val != 4.0) return GBR_ERR_ARG;
+        if (val == 4.0 && c->ph.cons) return GBR_ERR_UNSUPPORTED;
         c->ph.order = (int)val;
+        return GBR_OK;
+    case GBR_OPT_VARIABLES:
+        if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;
+        if (val == 1.0 && c->ph.order != 7) return GBR_ERR_UNSUPPORTED;
+        c->ph.cons = (int)val;
         return GBR_OK;
     case GBR_OPT_TIMING:
         if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;

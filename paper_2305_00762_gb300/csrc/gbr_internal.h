@@ -29,6 +29,7 @@ struct Grid {
 struct Physics {
     double gamma, mu, Pr, dx, dy;
     int order;  // 7: MEG7 (alpha = 38/7, beta = 3/190); 4: the alpha = 4, beta = 0 member
+    int cons;   // 0: MEG7-prim (reconstruct U); 1: MEG7-cons (reconstruct Q)
 };
 
 struct SensorDev;
@@ -109,5 +110,7 @@ cudaError_t launch_wavespeed(const Grid& g, const Physics& ph, const double* q,
                              unsigned long long* lam, cudaStream_t s);
 cudaError_t launch_stage_f64(const StageParams& p, cudaStream_t s);
 cudaError_t launch_stage_f32(const StageParams& p, cudaStream_t s);
+cudaError_t launch_stage_cons_f64(const StageParams& p, cudaStream_t s);
+cudaError_t launch_stage_cons_f32(const StageParams& p, cudaStream_t s);
 
 }  // namespace gbr

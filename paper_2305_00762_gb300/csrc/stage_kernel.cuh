@@ -21,7 +21,7 @@
 
 namespace gbr {
 
-template <int BX, int BY, bool VISC>
+template <int BX, int BY, bool VISC, bool CONS = false>
 struct TileLayout {
     static constexpr int V = VISC ? 1 : 0;
     static constexpr int RW = BX + 12, RH = BY + 12;  // staged region (tile + halo)
@@ -49,7 +49,8 @@ struct TileLayout {
     static constexpr int oFY = oFX + 4 * NFX;
     static constexpr int oHX = oFY + 4 * NFY;
     static constexpr int oHY = oHX + 4 * NHX;
-    static constexpr int oEnd = oHY + 4 * NHY;
+    static constexpr int oQc = oHY + 4 * NHY;         // conservative values (MEG7-cons)
+    static constexpr int oEnd = oQc + (CONS ? 4 * NU : 0);
 
     // learned sensor: per-cell decisions on the bounding box of both
     // detector regions, rows and columns [3, B+9), and the weights
@@ -216,6 +217,11 @@ struct FaceIn {
     const T* tun;  // tangential derivative (dx-scaled) of un at cell j
     const T* tut;  // ... of ut
     int stq;       // step from cell j to cell j+1 in the tangential arrays
+    // MEG7-cons: conservative values (rho, rho un, rho ut, E) at cell j with
+    // stride su (the g planes then hold their gradients), and the tangential
+    // gradients of rho (tr0); tun / tut then point at those of rho un / rho ut.
+    const T* q[4];
+    const T* tr0;
 };
 
 template <typename T>
@@ -225,7 +231,24 @@ struct PhysT {
 
 // The whole interface procedure of Secs. 2.1-2.4 at face j+1/2. Returns the
 // total flux in face-normal order and the detector flag sigma.
-template <typename T, bool VISC, int ORDER>
+// Projection of a conservative vector q = (rho, rho un, rho ut, E) onto the
+// left eigenvectors of the conservative flux Jacobian at the mean state
+// (MEG7-cons): with A = b2 q0 - b1 (u q1 + v q2 - q3), b1 = (gamma-1)/c^2,
+// b2 = b1 (u^2+v^2)/2 and t = (u q0 - q1)/c, the four rows give
+// (A + t)/2, q0 - A, q2 - v q0, (A - t)/2.
+template <typename T>
+__device__ __forceinline__ void cons_project(T q0, T q1, T q2, T q3, T ub, T vb, T icb, T b1, T b2, T& w0, T& w1,
+                                             T& w2, T& w3)
+{
+    const T A = b2 * q0 - b1 * (ub * q1 + vb * q2 - q3);
+    const T t = (ub * q0 - q1) * icb;
+    w0 = T(0.5) * (A + t);
+    w1 = q0 - A;
+    w2 = q2 - vb * q0;
+    w3 = T(0.5) * (A - t);
+}
+
+template <typename T, bool VISC, int ORDER, bool CONS = false>
 __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P, T inv_dn, T inv_dt, T out[4],
                                           bool& smooth)
 {
@@ -249,53 +272,121 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
     const T be = T(0.5) * ic2;       // 1 / (2 c^2)
 
     T wL[4], wR[4];
-    {  // fields 1 and 4 (u - c and u + c) share un and p
-        T w0[6], w3[6], e0[6], e3[6];
+    if constexpr (!CONS) {
+        {  // fields 1 and 4 (u - c and u + c) share un and p
+            T w0[6], w3[6], e0[6], e3[6];
+    #pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const int o = (k - 2);
+                const T tu = al * in.u[1][o * su], tp = be * in.u[3][o * su];
+                w0[k] = tp - tu;
+                w3[k] = tp + tu;
+                const T gu = al * in.g[1][o * sg], gp = be * in.g[3][o * sg];
+                e0[k] = gp - gu;
+                e3[k] = gp + gu;
+            }
+            wL[0] = meg7(coef, w0[0], w0[1], w0[2], w0[3], w0[4], e0[0], e0[1], e0[2], e0[3], e0[4]);
+            wR[0] = meg7(coef, w0[5], w0[4], w0[3], w0[2], w0[1], -e0[5], -e0[4], -e0[3], -e0[2], -e0[1]);
+            wL[3] = meg7(coef, w3[0], w3[1], w3[2], w3[3], w3[4], e3[0], e3[1], e3[2], e3[3], e3[4]);
+            wR[3] = meg7(coef, w3[5], w3[4], w3[3], w3[2], w3[1], -e3[5], -e3[4], -e3[3], -e3[2], -e3[1]);
+        }
+        {  // field 2 (entropy): rho - p / c^2
+            T w[6], e[6];
+    #pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const int o = (k - 2);
+                w[k] = in.u[0][o * su] - ic2 * in.u[3][o * su];
+                e[k] = in.g[0][o * sg] - ic2 * in.g[3][o * sg];
+            }
+            wL[1] = meg7(coef, w[0], w[1], w[2], w[3], w[4], e[0], e[1], e[2], e[3], e[4]);
+            wR[1] = meg7(coef, w[5], w[4], w[3], w[2], w[1], -e[5], -e[4], -e[3], -e[2], -e[1]);
+        }
+        {  // field 3 (shear): ut
+            T w[6], e[6];
+    #pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const int o = (k - 2);
+                w[k] = in.u[2][o * su];
+                e[k] = in.g[2][o * sg];
+            }
+            wL[2] = meg7(coef, w[0], w[1], w[2], w[3], w[4], e[0], e[1], e[2], e[3], e[4]);
+            wR[2] = meg7(coef, w[5], w[4], w[3], w[2], w[1], -e[5], -e[4], -e[3], -e[2], -e[1]);
+        }
+    } else {
+        const T ub = T(0.5) * (in.u[1][0] + in.u[1][su]), vb = T(0.5) * (in.u[2][0] + in.u[2][su]);
+        const T b1 = P.gm1 * ic2, b2 = T(0.5) * (ub * ub + vb * vb) * b1;
+        T w[4][6], e[4][6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const int o = (k - 2);
-            const T tu = al * in.u[1][o * su], tp = be * in.u[3][o * su];
-            w0[k] = tp - tu;
-            w3[k] = tp + tu;
-            const T gu = al * in.g[1][o * sg], gp = be * in.g[3][o * sg];
-            e0[k] = gp - gu;
-            e3[k] = gp + gu;
+            cons_project(in.q[0][o * su], in.q[1][o * su], in.q[2][o * su], in.q[3][o * su], ub, vb, icb, b1, b2,
+                         w[0][k], w[1][k], w[2][k], w[3][k]);
+            cons_project(in.g[0][o * sg], in.g[1][o * sg], in.g[2][o * sg], in.g[3][o * sg], ub, vb, icb, b1, b2,
+                         e[0][k], e[1][k], e[2][k], e[3][k]);
         }
-        wL[0] = meg7(coef, w0[0], w0[1], w0[2], w0[3], w0[4], e0[0], e0[1], e0[2], e0[3], e0[4]);
-        wR[0] = meg7(coef, w0[5], w0[4], w0[3], w0[2], w0[1], -e0[5], -e0[4], -e0[3], -e0[2], -e0[1]);
-        wL[3] = meg7(coef, w3[0], w3[1], w3[2], w3[3], w3[4], e3[0], e3[1], e3[2], e3[3], e3[4]);
-        wR[3] = meg7(coef, w3[5], w3[4], w3[3], w3[2], w3[1], -e3[5], -e3[4], -e3[3], -e3[2], -e3[1]);
-    }
-    {  // field 2 (entropy): rho - p / c^2
-        T w[6], e[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const int o = (k - 2);
-            w[k] = in.u[0][o * su] - ic2 * in.u[3][o * su];
-            e[k] = in.g[0][o * sg] - ic2 * in.g[3][o * sg];
+        for (int f = 0; f < 4; ++f) {
+            wL[f] = meg7(coef, w[f][0], w[f][1], w[f][2], w[f][3], w[f][4], e[f][0], e[f][1], e[f][2], e[f][3],
+                         e[f][4]);
+            wR[f] = meg7(coef, w[f][5], w[f][4], w[f][3], w[f][2], w[f][1], -e[f][5], -e[f][4], -e[f][3], -e[f][2],
+                         -e[f][1]);
         }
-        wL[1] = meg7(coef, w[0], w[1], w[2], w[3], w[4], e[0], e[1], e[2], e[3], e[4]);
-        wR[1] = meg7(coef, w[5], w[4], w[3], w[2], w[1], -e[5], -e[4], -e[3], -e[2], -e[1]);
     }
-    {  // field 3 (shear): ut
-        T w[6], e[6];
+    // Back with the right eigenvectors: to primitive face states (MEG7-prim)
+    // or to conservative ones (MEG7-cons).
+    T rL, unL, utL, pL, EL, rR, unR, utR, pR, ER;
+    T QL[4], QR[4];
+    if constexpr (!CONS) {
+        const T crb = cb * irb;
+        rL = wL[0] + wL[1] + wL[3];
+        unL = crb * (wL[3] - wL[0]);
+        utL = wL[2];
+        pL = c2 * (wL[0] + wL[3]);
+        rR = wR[0] + wR[1] + wR[3];
+        unR = crb * (wR[3] - wR[0]);
+        utR = wR[2];
+        pR = c2 * (wR[0] + wR[3]);
+        EL = pL * P.igm1 + T(0.5) * rL * (unL * unL + utL * utL);
+        ER = pR * P.igm1 + T(0.5) * rR * (unR * unR + utR * utR);
+        QL[0] = rL;
+        QL[1] = rL * unL;
+        QL[2] = rL * utL;
+        QL[3] = EL;
+        QR[0] = rR;
+        QR[1] = rR * unR;
+        QR[2] = rR * utR;
+        QR[3] = ER;
+    } else {
+        const T ub = T(0.5) * (in.u[1][0] + in.u[1][su]), vb = T(0.5) * (in.u[2][0] + in.u[2][su]);
+        const T h2 = T(0.5) * (ub * ub + vb * vb);
+        const T Hb = c2 * P.igm1 + h2, uc = ub * cb;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const int o = (k - 2);
-            w[k] = in.u[2][o * su];
-            e[k] = in.g[2][o * sg];
+        for (int side = 0; side < 2; ++side) {
+            const T* wv = side == 0 ? wL : wR;
+            T* Qs = side == 0 ? QL : QR;
+            const T S = wv[0] + wv[1] + wv[3];
+            Qs[0] = S;
+            Qs[1] = ub * S + cb * (wv[3] - wv[0]);
+            Qs[2] = vb * S + wv[2];
+            Qs[3] = Hb * (wv[0] + wv[3]) + uc * (wv[3] - wv[0]) + h2 * wv[1] + vb * wv[2];
         }
-        wL[2] = meg7(coef, w[0], w[1], w[2], w[3], w[4], e[0], e[1], e[2], e[3], e[4]);
-        wR[2] = meg7(coef, w[5], w[4], w[3], w[2], w[1], -e[5], -e[4], -e[3], -e[2], -e[1]);
+        rL = QL[0];
+        EL = QL[3];
+        {
+            const T ir = T(1) / rL;
+            unL = QL[1] * ir;
+            utL = QL[2] * ir;
+            pL = P.gm1 * (EL - T(0.5) * rL * (unL * unL + utL * utL));
+        }
+        rR = QR[0];
+        ER = QR[3];
+        {
+            const T ir = T(1) / rR;
+            unR = QR[1] * ir;
+            utR = QR[2] * ir;
+            pR = P.gm1 * (ER - T(0.5) * rR * (unR * unR + utR * utR));
+        }
     }
-    // Back to primitive variables with the right eigenvectors.
-    const T crb = cb * irb;
-    const T rL = wL[0] + wL[1] + wL[3], unL = crb * (wL[3] - wL[0]), utL = wL[2], pL = c2 * (wL[0] + wL[3]);
-    const T rR = wR[0] + wR[1] + wR[3], unR = crb * (wR[3] - wR[0]), utR = wR[2], pR = c2 * (wR[0] + wR[3]);
-    const T EL = pL * P.igm1 + T(0.5) * rL * (unL * unL + utL * utL);
-    const T ER = pR * P.igm1 + T(0.5) * rR * (unR * unR + utR * utR);
-    const T QL[4] = {rL, rL * unL, rL * utL, EL};
-    const T QR[4] = {rR, rR * unR, rR * utR, ER};
 
     // Central part 1/2 (F_L + F_R) of the hybrid face fluxes (Sec. 2.4):
     // flux reconstruction where sigma = 1, F(Q_L), F(Q_R) where sigma = 0.
@@ -348,19 +439,37 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
         const T n0 = in.u[1][0], n1 = in.u[1][su];
         const T t0 = in.u[2][0], t1 = in.u[2][su];
         const T p0 = in.u[3][0], p1 = in.u[3][su];
-        const T dr0 = in.g[0][0], dr1 = in.g[0][sg];
-        const T dn0 = in.g[1][0], dn1 = in.g[1][sg];
-        const T dt0 = in.g[2][0], dt1 = in.g[2][sg];
-        const T dp0 = in.g[3][0], dp1 = in.g[3][sg];
+        T dr0 = in.g[0][0], dr1 = in.g[0][sg];
+        T dn0 = in.g[1][0], dn1 = in.g[1][sg];
+        T dt0 = in.g[2][0], dt1 = in.g[2][sg];
+        T dp0 = in.g[3][0], dp1 = in.g[3][sg];
         const T ir0 = T(1) / r0, ir1 = T(1) / r1;
+        if constexpr (CONS) {  // primitive gradients from the conservative ones (chain rule)
+            const T k0 = T(0.5) * (n0 * n0 + t0 * t0), k1 = T(0.5) * (n1 * n1 + t1 * t1);
+            const T e0 = dp0, e1 = dp1;  // dE
+            dp0 = P.gm1 * (e0 - n0 * dn0 - t0 * dt0 + k0 * dr0);
+            dp1 = P.gm1 * (e1 - n1 * dn1 - t1 * dt1 + k1 * dr1);
+            dn0 = (dn0 - n0 * dr0) * ir0;
+            dn1 = (dn1 - n1 * dr1) * ir1;
+            dt0 = (dt0 - t0 * dr0) * ir0;
+            dt1 = (dt1 - t1 * dr1) * ir1;
+        }
         const T T0 = P.gamma * p0 * ir0, T1 = P.gamma * p1 * ir1;
         const T dT0 = P.gamma * (dp0 * ir0 - p0 * dr0 * ir0 * ir0);
         const T dT1 = P.gamma * (dp1 * ir1 - p1 * dr1 * ir1 * ir1);
         const T un_n = (T(0.5) * (dn0 + dn1) + T(2) * (n1 - T(0.5) * dn1 - n0 - T(0.5) * dn0)) * inv_dn;
         const T ut_n = (T(0.5) * (dt0 + dt1) + T(2) * (t1 - T(0.5) * dt1 - t0 - T(0.5) * dt0)) * inv_dn;
         const T T_n = (T(0.5) * (dT0 + dT1) + T(2) * (T1 - T(0.5) * dT1 - T0 - T(0.5) * dT0)) * inv_dn;
-        const T un_t = T(0.5) * (in.tun[0] + in.tun[in.stq]) * inv_dt;
-        const T ut_t = T(0.5) * (in.tut[0] + in.tut[in.stq]) * inv_dt;
+        T gn0 = in.tun[0], gn1 = in.tun[in.stq], gt0 = in.tut[0], gt1 = in.tut[in.stq];
+        if constexpr (CONS) {  // tangential derivatives of un, ut from those of rho un, rho ut, rho
+            const T ra0 = in.tr0[0], ra1 = in.tr0[in.stq];
+            gn0 = (gn0 - n0 * ra0) * ir0;
+            gn1 = (gn1 - n1 * ra1) * ir1;
+            gt0 = (gt0 - t0 * ra0) * ir0;
+            gt1 = (gt1 - t1 * ra1) * ir1;
+        }
+        const T un_t = T(0.5) * (gn0 + gn1) * inv_dt;
+        const T ut_t = T(0.5) * (gt0 + gt1) * inv_dt;
         const T unf = T(0.5) * (n0 + n1), utf = T(0.5) * (t0 + t1);
         const T tau_nn = T(2.0 / 3.0) * P.mu * (T(2) * un_n - ut_t);
         const T tau_nt = P.mu * (un_t + ut_n);
@@ -383,11 +492,11 @@ __device__ __forceinline__ double warp_max(double v)
 // the single-grid kernel (one CTA per tile) and the persistent batch kernel
 // (a CTA walks many tiles of many grids). Starts and ends with all threads
 // synchronised, so consecutive calls may reuse the shared memory.
-template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED = false, int ORDER = 7>
+template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED = false, int ORDER = 7, bool CONS = false>
 __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, const int ty0,
                                            unsigned char* smem_raw)
 {
-    using L = TileLayout<BX, BY, VISC>;
+    using L = TileLayout<BX, BY, VISC, CONS>;
     T* const sm = reinterpret_cast<T*>(smem_raw);
     T* const sU = sm + L::oU;
     T* const sGX = sm + L::oGX;
@@ -396,6 +505,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
     T* const sFY = sm + L::oFY;
     T* const sHX = sm + L::oHX;
     T* const sHY = sm + L::oHY;
+    T* const sQc = sm + L::oQc;  // MEG7-cons only
     unsigned char* const sPX = reinterpret_cast<unsigned char*>(sm + L::template nT<T, NT>());
     unsigned char* const sPY = sPX + L::NPX;
     constexpr int RW = L::RW, NU = L::NU, V = L::V;
@@ -430,21 +540,28 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         sU[NU + idx] = u;
         sU[2 * NU + idx] = v;
         sU[3 * NU + idx] = p;
+        if constexpr (CONS) {
+            sQc[idx] = r;
+            sQc[NU + idx] = T(P.q[o + plane]);
+            sQc[2 * NU + idx] = T(P.q[o + 2 * plane]);
+            sQc[3 * NU + idx] = T(P.q[o + 3 * plane]);
+        }
     }
     if constexpr (LEARNED)
         load_sensor(reinterpret_cast<SensorDev*>(smem_raw + L::template sensor_offset<T, NT>()), P.sensor);
     __syncthreads();
 
     // Phase 1: per-cell quantities, each computed once per tile.
+    const T* const sV = CONS ? sQc : sU;  // the reconstructed variables
     for (int idx = tid; idx < L::NGX; idx += NT) {  // x-gradients (Eq. six)
         const int a = idx / L::GXW, b = idx - a * L::GXW;
-        const T* s = sU + (a + 6 - V) * RW + (b + 3);
+        const T* s = sV + (a + 6 - V) * RW + (b + 3);
 #pragma unroll
         for (int m = 0; m < 4; ++m) sGX[m * L::NGX + idx] = grad6(s + m * NU, 1);
     }
     for (int idx = tid; idx < L::NGY; idx += NT) {  // y-gradients
         const int a = idx / L::GYW, b = idx - a * L::GYW;
-        const T* s = sU + (a + 3) * RW + (b + 6 - V);
+        const T* s = sV + (a + 3) * RW + (b + 6 - V);
 #pragma unroll
         for (int m = 0; m < 4; ++m) sGY[m * L::NGY + idx] = grad6(s + m * NU, RW);
     }
@@ -570,9 +687,17 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
                 in.f[3] = fx + 3 * L::NFX;
                 in.sf = 1;
                 const T* ty = sGY + (ry - 3) * L::GYW + (rx - 6 + V);
-                in.tun = ty + L::NGY;      // d u / d y
-                in.tut = ty + 2 * L::NGY;  // d v / d y
+                in.tun = ty + L::NGY;      // d u / d y (cons: d rho u / d y)
+                in.tut = ty + 2 * L::NGY;  // d v / d y (cons: d rho v / d y)
                 in.stq = 1;
+                if constexpr (CONS) {
+                    const T* qc = sQc + ry * RW + rx;
+                    in.q[0] = qc;
+                    in.q[1] = qc + NU;
+                    in.q[2] = qc + 2 * NU;
+                    in.q[3] = qc + 3 * NU;
+                    in.tr0 = ty;
+                }
                 inv_n = inv_dx;
                 inv_t = inv_dy;
             } else {
@@ -601,15 +726,23 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
                 in.f[3] = fy + 3 * L::NFY;
                 in.sf = BX;
                 const T* tx = sGX + (ry - 6 + V) * L::GXW + (rx - 3);
-                in.tun = tx + 2 * L::NGX;  // d v / d x
-                in.tut = tx + L::NGX;      // d u / d x
+                in.tun = tx + 2 * L::NGX;  // d v / d x (cons: d rho v / d x)
+                in.tut = tx + L::NGX;      // d u / d x (cons: d rho u / d x)
                 in.stq = L::GXW;
+                if constexpr (CONS) {
+                    const T* qc = sQc + ry * RW + rx;
+                    in.q[0] = qc;
+                    in.q[1] = qc + 2 * NU;  // rho v
+                    in.q[2] = qc + NU;      // rho u
+                    in.q[3] = qc + 3 * NU;
+                    in.tr0 = tx;
+                }
                 inv_n = inv_dy;
                 inv_t = inv_dx;
             }
             T out[4];
             bool smooth;
-            face_flux<T, VISC, ORDER>(in, ph, inv_n, inv_t, out, smooth);
+            face_flux<T, VISC, ORDER, CONS>(in, ph, inv_n, inv_t, out, smooth);
             if (valid) {
                 if (xf) {
 #pragma unroll
@@ -699,20 +832,20 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
     __syncthreads();
 }
 
-template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED, int ORDER>
+template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED, int ORDER, bool CONS>
 __global__ void __launch_bounds__(NT) stage_kernel(const StageParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    stage_tile<T, BX, BY, NT, VISC, LEARNED, ORDER>(P, blockIdx.x * BX, blockIdx.y * BY, smem_raw);
+    stage_tile<T, BX, BY, NT, VISC, LEARNED, ORDER, CONS>(P, blockIdx.x * BX, blockIdx.y * BY, smem_raw);
 }
 
-template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED = false, int ORDER = 7>
+template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED = false, int ORDER = 7, bool CONS = false>
 cudaError_t launch_stage_t(const StageParams& p, cudaStream_t s)
 {
-    using L = TileLayout<BX, BY, VISC>;
+    using L = TileLayout<BX, BY, VISC, CONS>;
     constexpr size_t smem = L::template total_bytes<T, NT, LEARNED>();
     static bool configured = false;
-    auto kern = stage_kernel<T, BX, BY, NT, VISC, LEARNED, ORDER>;
+    auto kern = stage_kernel<T, BX, BY, NT, VISC, LEARNED, ORDER, CONS>;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -20,6 +20,7 @@ GBR_OK, GBR_ERR_ARG, GBR_ERR_CUDA, GBR_ERR_NONPHYSICAL = 0, -1, -2, -3
 GBR_ERR_TIMEOUT, GBR_ERR_STATE, GBR_ERR_NOMEM, GBR_ERR_UNSUPPORTED = -4, -5, -6, -7
 GBR_BC_PERIODIC, GBR_BC_TRANSMISSIVE, GBR_BC_NOSLIP_WALL, GBR_BC_SYMMETRY = 0, 1, 2, 3
 GBR_OPT_PRECISION, GBR_OPT_RECORD_FLAGS, GBR_OPT_SENSOR, GBR_OPT_TIMING, GBR_OPT_ORDER = 0, 1, 2, 3, 4
+GBR_OPT_VARIABLES = 5
 GBR_KERNEL_STAGE, GBR_KERNEL_GHOST, GBR_KERNEL_WAVESPEED, GBR_KERNEL_CLASSES = 0, 1, 2, 3
 GBR_GHOST = 6
 GBR_STATIC_SCRATCH_DOUBLES = 1 << 20
@@ -289,7 +290,7 @@ class Solver:
     """Convenience owner of one gbr context (marshalling only)."""
 
     def __init__(self, nx, ny, dx, dy, gamma=1.4, mu=0.0, Pr=0.72, bc=(GBR_BC_PERIODIC,) * 4,
-                 precision=64, stream=None, order=7):
+                 precision=64, stream=None, order=7, cons=False):
         self.nx, self.ny = int(nx), int(ny)
         self.ctx = gbr_create(nx, ny, gamma, mu, Pr, bc, dx, dy)
         if stream is not None:
@@ -298,6 +299,8 @@ class Solver:
             gbr_set_option(self.ctx, GBR_OPT_PRECISION, precision)
         if order != 7:
             gbr_set_option(self.ctx, GBR_OPT_ORDER, order)
+        if cons:
+            gbr_set_option(self.ctx, GBR_OPT_VARIABLES, 1)
 
     @classmethod
     def for_case(cls, case, **kw):

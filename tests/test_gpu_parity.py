@@ -243,3 +243,34 @@ def test_fourth_order_member(env, name, make):
     assert rc == 0
     assert_state_close(s.get_state(), Qo, what=f"{name} order-4 step")
     s.close()
+
+
+CONS_CASES = [("vortex64", lambda: C.isentropic_vortex(64)),
+              ("riemann70x45", lambda: C.riemann_2d(70, 45)),
+              ("kh48", lambda: C.kelvin_helmholtz(48, np.random.default_rng(5))),
+              ("vst45x29", lambda: C.viscous_shock_tube(45, 29))]
+
+
+@pytest.mark.parametrize("name,make", CONS_CASES, ids=[x[0] for x in CONS_CASES])
+def test_meg7_cons(env, name, make):
+    """GBR_OPT_VARIABLES = 1 (MEG7-cons) against the oracle with cons = 1:
+    residual and flags, then two RK3 steps."""
+    torch, O, gbr = env
+    c = make()
+    cfg = O.Config(c.nx, c.ny, c.dx, c.dy, c.gamma, c.mu, c.Pr, c.bc, 7, 1)
+    s = gbr.Solver.for_case(c, cons=True)
+    s.record_flags(True)
+    s.set_state(c.Q)
+    R = s.residual()
+    sx, sy = s.flags()
+    Ro, sxo, syo = O.residual(cfg, c.Q, want_flags=True)
+    excl = tie_faces_ok(O, cfg, c.Q, sx, sxo, sy, syo)
+    assert_residual_close(R, Ro, c.Q, c, exclude=excl, what=f"{name} cons residual")
+    Q = c.Q.copy()
+    for _ in range(2):
+        dt = c.cfl / O.max_wavespeed(cfg, Q)
+        s.step(dt)
+        Q, rc = O.rk3_step(cfg, Q, dt)
+        assert rc == 0
+    assert_state_close(s.get_state(), Q, what=f"{name} cons steps")
+    s.close()
