@@ -45,7 +45,7 @@
  *      rho', p'; heat conductivity mu/(Pr (gamma-1)) (Eq. visc-interface).
  *  R9  G = 6 ghost layers: the LC bound at j+1/2 uses d_{j-1}, which uses
  *      Phi'_{j-2}, which uses Phi_{j-5}.
- *  R10 MEG7-cons (Sec. 2.2, conservative reconstruction): Q and its
+ *  R20 MEG7-cons (Sec. 2.2, conservative reconstruction): Q and its
  *      sixth-order gradients are projected with the left eigenvectors of the
  *      conservative flux Jacobian frozen at the same mean state as in R2
  *      (H = c^2/(gamma-1) + (u^2+v^2)/2); the viscous terms take u', v' from
@@ -378,7 +378,7 @@ void or_fill_ghosts(const or_cfg *c, double *Qp)
  * along and across the sweep. Writes the total flux (convective + viscous) in
  * face-normal order and the detector flag sigma. */
 /* Primitive (rho, un, ut, p) dx-scaled gradient of a cell from its
- * conservative state q and conservative gradient dq (reading R10). */
+ * conservative state q and conservative gradient dq (reading R20). */
 static void prim_gradient_from_cons(double gamma, const double *q, const double *dq, double *dw)
 {
     double rho = q[0], u = q[1] / rho, v = q[2] / rho;
@@ -430,7 +430,7 @@ static void face_flux(const or_cfg *c, const double *const P[4], const double *c
     *sigma_out = sigma;
 
     /* Reading R2: eigenvectors of the primitive Jacobian at the mean state
-     * (R10: of the conservative Jacobian for MEG7-cons). */
+     * (R20: of the conservative Jacobian for MEG7-cons). */
     double rb = 0.5 * (U[5][0] + U[6][0]);
     double pb = 0.5 * (U[5][3] + U[6][3]);
     double cb = sqrt(g * pb / rb);
@@ -815,7 +815,7 @@ int or_trouble_labels(const or_cfg *c, const double *Q, unsigned char *label)
 }
 
 /* Pin helper: the left (rows) and right (columns) eigenvector matrices of
- * the x-direction conservative flux Jacobian at primitive state w (R10). */
+ * the x-direction conservative flux Jacobian at primitive state w (R20). */
 void or_cons_eigenvectors(double g, const double *w, double *L, double *R)
 {
     double ub = w[1], vb = w[2], cb = sqrt(g * w[3] / w[0]);

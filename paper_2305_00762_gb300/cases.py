@@ -209,6 +209,22 @@ def shear_wave(n, amp=1e-6, L=1.0, mu=1e-2, gamma=1.4, Pr=0.72, rho0=1.0, p0=1.0
                 (BC_PERIODIC,) * 4, meta={"amp": amp, "k": 2 * np.pi / L})
 
 
+def shock_tube(n, left, right, t_end, ny=8, x_split=0.5, gamma=1.4, cfl=0.5):
+    """Example 2 (Sod, Lax) as an n x ny strip on [0,1] x [0, ny/n]:
+    transmissive in x, periodic in y; left/right = (rho, u, p)."""
+    xc, dx = centres(n, 0.0, 1.0)
+    X = np.tile(xc, (ny, 1))
+    prim = [np.where(X < x_split, left[k], right[k]) for k in range(3)]
+    Q = prim_to_cons(prim[0], prim[1], np.zeros_like(X), prim[2], gamma)
+    return Case("shock_tube", np.ascontiguousarray(Q), dx, dx, gamma, 0.0, 0.72,
+                (BC_TRANSMISSIVE, BC_TRANSMISSIVE, BC_PERIODIC, BC_PERIODIC), t_end, cfl,
+                {"left": left, "right": right, "x_split": x_split})
+
+
+SOD = ((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 0.2)           # Example 2, Sod
+LAX = ((0.445, 0.698, 3.528), (0.5, 0.0, 0.571), 0.14)   # Example 2, Lax (t = 0.14)
+
+
 def ensemble(n_cases=64, seed=762, sizes=(256, 512, 1024, 2048)):
     """Seeded table of independent cases of uneven size: half isentropic
     vortices with strength U[1,5] on [0,10]^2, half shear layers."""

@@ -80,19 +80,80 @@ __device__ __forceinline__ float trsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double tabs(double x) { return fabs(x); }
 __device__ __forceinline__ float tabs(float x) { return fabsf(x); }
 
+// FP64 comparisons on the integer pipe. GB300 runs every FP64 instruction,
+// compares and min/max included, on a unit that retires 2 thread-operations
+// per SM per clock, against 64 for the 32-bit integer pipe; the MP limiter is
+// mostly comparisons. For doubles that are not NaN, the signed 64-bit order of
+// ordkey(x) is the order of x (with -0 just below +0), ordkey is its own
+// inverse, and |x| orders as the bit pattern of x with the sign cleared.
+// Values chosen this way equal those of the floating-point comparisons; only
+// the sign of a zero result may differ, which no later sum or product turns
+// into a different non-zero value.
+__device__ __forceinline__ long long ordkey(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ double tmin(double a, double b) { return ordkey(a) < ordkey(b) ? a : b; }
+__device__ __forceinline__ double tmax(double a, double b) { return ordkey(a) > ordkey(b) ? a : b; }
+
 // Eq. alpha: minmod(a, b) = 1/2 (sign a + sign b) min(|a|, |b|).
 template <typename T>
 __device__ __forceinline__ T minmod(T a, T b)
 {
     return (a > T(0) && b > T(0)) ? tmin(a, b) : ((a < T(0) && b < T(0)) ? tmax(a, b) : T(0));
 }
+__device__ __forceinline__ double minmod(double a, double b)
+{
+    const long long ba = __double_as_longlong(a), bb = __double_as_longlong(b);
+    const unsigned long long ma = (unsigned long long)ba & 0x7FFFFFFFFFFFFFFFULL;
+    const unsigned long long mb = (unsigned long long)bb & 0x7FFFFFFFFFFFFFFFULL;
+    const double r = ma <= mb ? a : b;  // the smaller magnitude
+    return (ba ^ bb) < 0 ? 0.0 : r;     // opposite signs
+}
+
+// The MP test's comparison x <= 1e-40 (Eq. mp5Condition).
+template <typename T>
+__device__ __forceinline__ bool mp_accept(T x) { return x <= T(1e-40); }
+__device__ __forceinline__ bool mp_accept(double x) { return ordkey(x) <= ordkey(1e-40); }
+
+// Phi^min and Phi^max of Eq. mp-procedure from Phi_j, Phi_{j+1}, Phi^MD,
+// Phi^UL and Phi^LC.
+template <typename T>
+__device__ __forceinline__ void mp_bounds(T p2, T p3, T md, T ul, T lc, T& pmin, T& pmax)
+{
+    pmin = tmax(tmin(p2, tmin(p3, md)), tmin(p2, tmin(ul, lc)));
+    pmax = tmin(tmax(p2, tmax(p3, md)), tmax(p2, tmax(ul, lc)));
+}
+__device__ __forceinline__ void mp_bounds(double p2, double p3, double md, double ul, double lc, double& pmin,
+                                          double& pmax)
+{
+    const long long k2 = ordkey(p2), k3 = ordkey(p3), km = ordkey(md), ku = ordkey(ul), kl = ordkey(lc);
+    const long long kmin = max(min(k2, min(k3, km)), min(k2, min(ku, kl)));
+    const long long kmax = min(max(k2, max(k3, km)), max(k2, max(ku, kl)));
+    pmin = __longlong_as_double(kmin ^ ((kmin >> 63) & 0x7FFFFFFFFFFFFFFFLL));
+    pmax = __longlong_as_double(kmax ^ ((kmax >> 63) & 0x7FFFFFFFFFFFFFFFLL));
+}
+
+// Explicitly rounded products and fused multiply-adds. Per-cell work that is
+// done once along x and once along y sits at two call sites, where the
+// compiler could contract a*b + c into an FMA at one and not at the other.
+// Written with these, both sites round alike, so the x and y results of
+// mirrored data are bitwise mirrors (the face work shares one call site).
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+// a^2 + b^2, symmetric in a and b to the last bit.
+template <typename T>
+__device__ __forceinline__ T sumsq(T a, T b) { return rmul(a, a) + rmul(b, b); }
 
 // Eq. six: dx-scaled sixth-order gradient at s[0] along stride st.
 template <typename T>
 __device__ __forceinline__ T grad6(const T* s, int st)
 {
-    return (T(45) * (s[st] - s[-st]) - T(9) * (s[2 * st] - s[-2 * st]) + (s[3 * st] - s[-3 * st])) *
-           T(1.0 / 60.0);
+    return rmul(rfma(T(45), s[st] - s[-st], rfma(T(-9), s[2 * st] - s[-2 * st], s[3 * st] - s[-3 * st])),
+                T(1.0 / 60.0));
 }
 
 // Eq. detector with eps = 0.9 psi_c xi^2 / (1 - 0.9 psi_c), xi = 1e-3: returns
@@ -102,9 +163,9 @@ template <typename T>
 __device__ __forceinline__ bool trouble_cell(const T* r, int st)
 {
     const T eps = T(0.9 * 0.5 / (1.0 - 0.9 * 0.5) * 1e-6);
-    T a = tabs(r[0] - r[-st]) + tabs(r[0] - T(2) * r[-st] + r[-2 * st]);
-    T b = tabs(r[0] - r[st]) + tabs(r[0] - T(2) * r[st] + r[2 * st]);
-    return T(2) * (T(2) * a * b + eps) < a * a + b * b + eps;
+    const T a = tabs(r[0] - r[-st]) + tabs(rfma(T(-2), r[-st], r[0]) + r[-2 * st]);
+    const T b = tabs(r[0] - r[st]) + tabs(rfma(T(-2), r[st], r[0]) + r[2 * st]);
+    return T(2) * rfma(T(2) * a, b, eps) < rfma(a, a, rfma(b, b, eps));
 }
 
 // The GRB left value and the MP test of Eqs. mp5Condition and alpha for the left value
@@ -162,7 +223,7 @@ __device__ __forceinline__ T grb_check(const T* p, const T* d, bool& need, const
                          C.w3 * ((p[0] - p[2]) + (p[4] - p[2]))) *
                             T(1.0 / 840.0);
     const T pmp = p[2] + minmod(p[3] - p[2], T(7) * (p[2] - p[1]));
-    need = !((pl - p[2]) * (pl - pmp) <= T(1e-40));
+    need = !mp_accept((pl - p[2]) * (pl - pmp));
     return pl;
 }
 
@@ -176,8 +237,8 @@ __device__ __forceinline__ T mp_limit(const T* p, const T* d, T pl)
     const T md = T(0.5) * (p[2] + p[3]) - T(0.5) * minmod(dj, dp1);
     const T ul = p[2] + T(7) * (p[2] - p[1]);
     const T lc = T(0.5) * (T(3) * p[2] - p[1]) + T(4.0 / 3.0) * minmod(dj, dm1);
-    const T pmin = tmax(tmin(p[2], tmin(p[3], md)), tmin(p[2], tmin(ul, lc)));
-    const T pmax = tmin(tmax(p[2], tmax(p[3], md)), tmax(p[2], tmax(ul, lc)));
+    T pmin, pmax;
+    mp_bounds(p[2], p[3], md, ul, lc, pmin, pmax);
     return pl + minmod(pmin - pl, pmax - pl);
 }
 
@@ -535,7 +596,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         const T ir = T(1) / r;
         const T u = T(P.q[o + plane]) * ir;
         const T v = T(P.q[o + 2 * plane]) * ir;
-        const T p = ph.gm1 * (T(P.q[o + 3 * plane]) - T(0.5) * r * (u * u + v * v));
+        const T p = ph.gm1 * (T(P.q[o + 3 * plane]) - T(0.5) * r * sumsq(u, v));
         sU[idx] = r;
         sU[NU + idx] = u;
         sU[2 * NU + idx] = v;
@@ -601,10 +662,10 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         const int a = idx / L::FXW, b = idx - a * L::FXW;
         const int c = (a + 6) * RW + (b + 1);
         const T r = sU[c], u = sU[NU + c], v = sU[2 * NU + c], p = sU[3 * NU + c];
-        const T E = p * ph.igm1 + T(0.5) * r * (u * u + v * v);
+        const T E = rfma(p, ph.igm1, rmul(T(0.5) * r, sumsq(u, v)));
         const T ru = r * u;
         sFX[idx] = ru;
-        sFX[L::NFX + idx] = ru * u + p;
+        sFX[L::NFX + idx] = rfma(ru, u, p);
         sFX[2 * L::NFX + idx] = ru * v;
         sFX[3 * L::NFX + idx] = u * (E + p);
     }
@@ -612,11 +673,11 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         const int a = idx / BX, b = idx - a * BX;
         const int c = (a + 1) * RW + (b + 6);
         const T r = sU[c], u = sU[NU + c], v = sU[2 * NU + c], p = sU[3 * NU + c];
-        const T E = p * ph.igm1 + T(0.5) * r * (u * u + v * v);
+        const T E = rfma(p, ph.igm1, rmul(T(0.5) * r, sumsq(u, v)));
         const T rv = r * v;
         sFY[idx] = rv;
         sFY[L::NFY + idx] = rv * u;
-        sFY[2 * L::NFY + idx] = rv * v + p;
+        sFY[2 * L::NFY + idx] = rfma(rv, v, p);
         sFY[3 * L::NFY + idx] = v * (E + p);
     }
     __syncthreads();
@@ -780,7 +841,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         for (int m = 0; m < 4; ++m) {
             const T dF = sHX[m * L::NHX + r * L::HXW + c + 1] - sHX[m * L::NHX + r * L::HXW + c];
             const T dG = sHY[m * L::NHY + (r + 1) * BX + c] - sHY[m * L::NHY + r * BX + c];
-            res[m] = double(-dF * inv_dx - dG * inv_dy);
+            res[m] = double(-(rmul(dF, inv_dx) + rmul(dG, inv_dy)));
         }
         if (P.res) {
 #pragma unroll
@@ -804,7 +865,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
             if (P.lam_out) {  // Sec. 2.5 wavespeed of the new state
                 const T r = T(qv[0]), ir = T(1) / r;
                 const T u = T(qv[1]) * ir, v = T(qv[2]) * ir;
-                const T p = ph.gm1 * (T(qv[3]) - T(0.5) * r * (u * u + v * v));
+                const T p = ph.gm1 * (T(qv[3]) - T(0.5) * r * sumsq(u, v));
                 const T cs = tsqrt(ph.gamma * p * ir);
                 T l = tmax((tabs(u) + cs) * inv_dx, (tabs(v) + cs) * inv_dy);
                 if (P.ph.mu > 0.0) {
