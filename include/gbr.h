@@ -211,20 +211,26 @@ int gbr_set_sensor_weights(gbr_ctx *ctx, const float *w, int n);
 int gbr_sensor_eval(gbr_ctx *ctx, float *prob, int on_device);
 
 /* Training data from the current state (device buffers): features[ny*nx][64]
- * BF16 (row-major cells, zero-padded past 50) and labels[ny*nx] = 1 where the
- * plain detector marks the cell (psi_x < 0.5 or psi_y < 0.5, FP64). Either
- * may be NULL. Asynchronous. */
-int gbr_sensor_dataset(gbr_ctx *ctx, void *features, unsigned char *labels);
+ * BF16 (row-major cells, zero-padded past 50); labels[ny*nx] = 1 where the
+ * plain detector marks the cell (psi_x < 0.5 or psi_y < 0.5, FP64), else 0;
+ * targets[ny*nx] = round(255 / (1 + exp((psi_min - 0.5) / 0.02))) with
+ * psi_min = min(psi_x, psi_y) in FP64, the soft training target in units of
+ * 1/255 (a cell within 0.016 of the threshold gets a target inside the
+ * fallback band [0.3, 0.7]). Any of the three may be NULL, not all.
+ * Asynchronous. */
+int gbr_sensor_dataset(gbr_ctx *ctx, void *features, unsigned char *labels, unsigned char *targets);
 
 /* Train the sensor on n samples (device buffers as written by
- * gbr_sensor_dataset): `steps` Adam steps (learning rate lr) on mini-batches
- * of `batch` samples drawn with replacement by a counter-based hash of
- * (seed, step, slot); binary cross-entropy with label-1 samples weighted by
- * pos_weight; BF16 operands, FP32 accumulation. w (host, GBR_SENSOR_PARAMS
- * floats) holds the initial weights on entry and the trained ones on return;
- * loss (host, `steps` floats, may be NULL) receives each step's summed loss.
- * Allocates temporary device memory; synchronises `stream`. */
-int gbr_sensor_train(const void *features, const unsigned char *labels, long long n, int steps, int batch,
+ * gbr_sensor_dataset; targets in units of 1/255, hard labels as 0 / 255):
+ * `steps` Adam steps (learning rate lr) on mini-batches of `batch` samples
+ * drawn with replacement by a counter-based hash of (seed, step, slot);
+ * binary cross-entropy against target t with sample weight
+ * 1 + (pos_weight - 1) t; BF16 operands, FP32 accumulation. w (host,
+ * GBR_SENSOR_PARAMS floats) holds the initial weights on entry and the
+ * trained ones on return; loss (host, `steps` floats, may be NULL) receives
+ * each step's summed loss. Allocates temporary device memory; synchronises
+ * `stream`. */
+int gbr_sensor_train(const void *features, const unsigned char *targets, long long n, int steps, int batch,
                      double lr, double pos_weight, unsigned long long seed, float *w, float *loss, void *stream);
 
 /* Wait for the context's stream and report pending device errors. */

@@ -100,6 +100,8 @@ def lib():
             L.or_cons_eigenvectors.argtypes = [ctypes.c_double, dp, dp, dp]
             L.or_trouble_labels.restype = ctypes.c_int
             L.or_trouble_labels.argtypes = [cp, dp, u8]
+            L.or_psi_min.restype = ctypes.c_int
+            L.or_psi_min.argtypes = [cp, dp, dp]
             L.or_num_threads.restype = ctypes.c_int
             L.or_set_num_threads.argtypes = [ctypes.c_int]
             _lib = L
@@ -258,6 +260,16 @@ def trouble_labels(cfg: Config, Q) -> np.ndarray:
     rc = lib().or_trouble_labels(ctypes.byref(cfg.c()), _dp(Q), _u8(out))
     if rc != 0:
         raise RuntimeError(f"oracle labels failed: {rc}")
+    return out
+
+
+def psi_min(cfg: Config, Q) -> np.ndarray:
+    """min(psi_x, psi_y) of Eq. detector per interior cell, FP64."""
+    Q = _state(cfg, Q)
+    out = np.zeros((cfg.ny, cfg.nx))
+    rc = lib().or_psi_min(ctypes.byref(cfg.c()), _dp(Q), _dp(out))
+    if rc != 0:
+        raise RuntimeError(f"oracle psi failed: {rc}")
     return out
 
 

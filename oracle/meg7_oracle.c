@@ -814,6 +814,39 @@ int or_trouble_labels(const or_cfg *c, const double *Q, unsigned char *label)
     return OR_OK;
 }
 
+/* min(psi_x, psi_y) per interior cell ([ny][nx]): Eq. detector along x and
+ * along y on the density, ghost cells by the boundary conditions. The cell is
+ * a plain-detector cell (label 1) exactly when this is below psi_c = 0.5; the
+ * learned sensor's soft training target is a function of it. */
+int or_psi_min(const or_cfg *c, const double *Q, double *psi)
+{
+    if (!cfg_ok(c) || !Q || !psi)
+        return OR_ERR_ARG;
+    const int nx = c->nx, ny = c->ny, W = nx + 2 * OR_G;
+    const ptrdiff_t N = (ptrdiff_t)W * (ny + 2 * OR_G);
+    double *Qp = (double *)malloc(sizeof(double) * 4 * N);
+    if (!Qp)
+        return OR_ERR_NOMEM;
+    for (int m = 0; m < 4; ++m)
+        for (int i = 0; i < ny; ++i)
+            for (int j = 0; j < nx; ++j)
+                Qp[m * N + pidx(c, j, i)] = Q[((size_t)m * ny + i) * nx + j];
+    or_fill_ghosts(c, Qp);
+    for (int i = 0; i < ny; ++i) {
+        for (int j = 0; j < nx; ++j) {
+            double rx[5], ry[5];
+            for (int l = 0; l < 5; ++l) {
+                rx[l] = Qp[pidx(c, j + l - 2, i)];
+                ry[l] = Qp[pidx(c, j, i + l - 2)];
+            }
+            const double px = or_psi(rx), py = or_psi(ry);
+            psi[(size_t)i * nx + j] = px < py ? px : py;
+        }
+    }
+    free(Qp);
+    return OR_OK;
+}
+
 /* Pin helper: the left (rows) and right (columns) eigenvector matrices of
  * the x-direction conservative flux Jacobian at primitive state w (R20). */
 void or_cons_eigenvectors(double g, const double *w, double *L, double *R)

@@ -24,6 +24,7 @@ import numpy as np
 from . import G, Config, fill_ghosts_padded
 
 N_IN, N_H = 50, 32
+TAU = 0.02  # width of the soft training target around psi_c = 0.5
 N_PARAMS = N_IN * N_H + N_H + N_H * N_H + N_H + N_H + 1
 FLOOR = np.float32(1e-3)
 LO, HI = 0.3, 0.7
@@ -94,3 +95,11 @@ def forward(x, w) -> np.ndarray:
 def decision(p) -> np.ndarray:
     p = np.asarray(p)
     return np.where(p > HI, 1, np.where(p < LO, 0, 2)).astype(np.uint8)
+
+
+def soft_target(psi_min, tau=TAU) -> np.ndarray:
+    """Training target of a cell in units of 1/255 (uint8): 255 / (1 +
+    exp((psi_min - 1/2) / tau)) rounded half up, in FP64; psi_min =
+    min(psi_x, psi_y) of Eq. detector (oracle.psi_min)."""
+    t = 1.0 / (1.0 + np.exp((np.asarray(psi_min, dtype=np.float64) - 0.5) / tau))
+    return np.floor(255.0 * t + 0.5).astype(np.uint8)

@@ -483,7 +483,7 @@ int gbr_sensor_eval(gbr_ctx* c, float* prob, int on_device)
         if (!c->prob) GBR_TRY(cudaMalloc(&c->prob, sizeof(float) * n));
         out = c->prob;
     }
-    GBR_TRY(launch_sensor_tile(c->g, c->ph.gamma, c->Qn, c->d_sensor, out, nullptr, nullptr, c->stream));
+    GBR_TRY(launch_sensor_tile(c->g, c->ph.gamma, c->Qn, c->d_sensor, out, nullptr, nullptr, nullptr, c->stream));
     if (!on_device) {
         GBR_TRY(cudaMemcpyAsync(prob, c->prob, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
         GBR_TRY(cudaStreamSynchronize(c->stream));
@@ -491,20 +491,21 @@ int gbr_sensor_eval(gbr_ctx* c, float* prob, int on_device)
     return GBR_OK;
 }
 
-int gbr_sensor_dataset(gbr_ctx* c, void* features, unsigned char* labels)
+int gbr_sensor_dataset(gbr_ctx* c, void* features, unsigned char* labels, unsigned char* targets)
 {
-    if (!c || (!features && !labels)) return GBR_ERR_ARG;
+    if (!c || (!features && !labels && !targets)) return GBR_ERR_ARG;
     if (!c->have_state) return GBR_ERR_STATE;
     DeviceGuard dg(c->device);
     int rc = ghosts(c, c->Qn, 0, 0, 0, 0);
     if (rc != GBR_OK) return rc;
-    return cuda_status(launch_sensor_tile(c->g, c->ph.gamma, c->Qn, nullptr, nullptr, features, labels, c->stream));
+    return cuda_status(
+        launch_sensor_tile(c->g, c->ph.gamma, c->Qn, nullptr, nullptr, features, labels, targets, c->stream));
 }
 
-int gbr_sensor_train(const void* features, const unsigned char* labels, long long n, int steps, int batch,
+int gbr_sensor_train(const void* features, const unsigned char* targets, long long n, int steps, int batch,
                      double lr, double pos_weight, unsigned long long seed, float* w, float* loss, void* stream)
 {
-    if (!features || !labels || !w || n < 1 || steps < 1 || batch < 1 || !(lr > 0.0) || !(pos_weight > 0.0))
+    if (!features || !targets || !w || n < 1 || steps < 1 || batch < 1 || !(lr > 0.0) || !(pos_weight > 0.0))
         return GBR_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     float *dw = nullptr, *dg = nullptr, *dm = nullptr, *dv = nullptr, *dl = nullptr;
@@ -520,7 +521,7 @@ int gbr_sensor_train(const void* features, const unsigned char* labels, long lon
     if (rc == GBR_OK) rc = cuda_status(cudaMemsetAsync(dv, 0, pb, s));
     if (rc == GBR_OK) rc = cuda_status(cudaMemsetAsync(dl, 0, sizeof(float) * steps, s));
     if (rc == GBR_OK)
-        rc = cuda_status(launch_sensor_train(features, labels, n, steps, batch, (float)lr, (float)pos_weight, seed,
+        rc = cuda_status(launch_sensor_train(features, targets, n, steps, batch, (float)lr, (float)pos_weight, seed,
                                              dw, dg, dm, dv, dl, s));
     if (rc == GBR_OK) rc = cuda_status(cudaMemcpyAsync(w, dw, pb, cudaMemcpyDeviceToHost, s));
     if (rc == GBR_OK && loss) rc = cuda_status(cudaMemcpyAsync(loss, dl, sizeof(float) * steps, cudaMemcpyDeviceToHost, s));

@@ -102,7 +102,7 @@ cudaError_t launch_batch_stage_f32(int shape, const BatchCase* cases, int ncases
 // evaluation / dataset extraction on a padded state, training.
 void pack_sensor(const float* w, SensorDev* out);
 cudaError_t launch_sensor_tile(const Grid& g, double gamma, const double* q, const SensorDev* w, float* prob,
-                               void* feat_bf16, unsigned char* label, cudaStream_t s);
+                               void* feat_bf16, unsigned char* label, unsigned char* target, cudaStream_t s);
 cudaError_t launch_sensor_train(const void* X_bf16, const unsigned char* y, long long n, int steps, int batch,
                                 float lr, float pos_weight, unsigned long long seed, float* w, float* grad, float* m,
                                 float* v, float* loss, cudaStream_t s);

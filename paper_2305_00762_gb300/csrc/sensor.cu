@@ -48,6 +48,7 @@ struct SensorTileParams {
     float* prob;            // [ny][nx] network output, or nullptr
     __nv_bfloat16* feat;    // [ny*nx][64] features, or nullptr
     unsigned char* label;   // [ny*nx] plain-detector label, or nullptr
+    unsigned char* target;  // [ny*nx] soft target in units of 1/255, or nullptr
 };
 
 __global__ void __launch_bounds__(256) sensor_tile_kernel(const SensorTileParams P)
@@ -106,19 +107,26 @@ __global__ void __launch_bounds__(256) sensor_tile_kernel(const SensorTileParams
             }
         }
     }
-    if (P.label) {  // plain detector in FP64 on the density (Eq. detector)
+    if (P.label || P.target) {  // plain detector in FP64 on the density (Eq. detector)
         for (int c = threadIdx.x; c < kTX * kTY; c += blockDim.x) {
             const int cy = c / kTX, cx = c - cy * kTX, i = ty0 + cy, j = tx0 + cx;
             if (i >= ny || j >= nx) continue;
             const double* r = P.q + (long long)(i + kGhost) * P.g.pitch + (j + kGhost);
-            const bool tr = trouble_cell<double>(r, 1) || trouble_cell<double>(r, P.g.pitch);
-            P.label[(long long)i * nx + j] = tr ? 1 : 0;
+            if (P.label) {
+                const bool tr = trouble_cell<double>(r, 1) || trouble_cell<double>(r, P.g.pitch);
+                P.label[(long long)i * nx + j] = tr ? 1 : 0;
+            }
+            if (P.target) {
+                const double psi = fmin(detector_psi(r, 1), detector_psi(r, P.g.pitch));
+                const double t = 1.0 / (1.0 + exp((psi - 0.5) / kSensorTau));
+                P.target[(long long)i * nx + j] = (unsigned char)floor(255.0 * t + 0.5);
+            }
         }
     }
 }
 
 cudaError_t launch_sensor_tile(const Grid& g, double gamma, const double* q, const SensorDev* w, float* prob,
-                               void* feat_bf16, unsigned char* label, cudaStream_t s)
+                               void* feat_bf16, unsigned char* label, unsigned char* target, cudaStream_t s)
 {
     __nv_bfloat16* feat = static_cast<__nv_bfloat16*>(feat_bf16);
     SensorTileParams P;
@@ -129,6 +137,7 @@ cudaError_t launch_sensor_tile(const Grid& g, double gamma, const double* q, con
     P.prob = prob;
     P.feat = feat;
     P.label = label;
+    P.target = target;
     dim3 grid((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY);
     sensor_tile_kernel<<<grid, 256, 0, s>>>(P);
     return cudaGetLastError();
@@ -166,7 +175,7 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z)
 
 struct TrainParams {
     const __nv_bfloat16* X;  // [n][64]
-    const unsigned char* y;  // [n]
+    const unsigned char* y;  // [n] targets in units of 1/255
     long long n;
     int batch;               // samples per step
     unsigned long long seed;
@@ -228,7 +237,7 @@ __global__ void __launch_bounds__(kTrainWarps * 32) sensor_grad_kernel(const Tra
         const long long idx = (long long)(hsh % (unsigned long long)P.n);
         const __nv_bfloat16* xin = P.X + idx * kSensorK;
         for (int k = 0; k < kSensorIn; ++k) xr[k] = valid ? __bfloat162float(xin[k]) : 0.f;
-        const float yv = valid ? (float)P.y[idx] : 0.f;
+        const float yv = valid ? (float)P.y[idx] * (1.f / 255.f) : 0.f;
         // forward
         for (int n = 0; n < kSensorH; ++n) {
             float a = b1[n];
@@ -244,7 +253,7 @@ __global__ void __launch_bounds__(kTrainWarps * 32) sensor_grad_kernel(const Tra
             z = fmaf(a, w3[n], z);
         }
         const float p = 1.f / (1.f + expf(-z));
-        const float wt = valid ? (yv > 0.5f ? P.pos_weight : 1.f) : 0.f;
+        const float wt = valid ? 1.f + (P.pos_weight - 1.f) * yv : 0.f;
         // binary cross-entropy from the logit: softplus(z) - y z
         const float l = fmaxf(z, 0.f) - yv * z + log1pf(expf(-fabsf(z)));
         lsum += wt * l;

@@ -27,6 +27,11 @@ constexpr int kW2Pitch = kSensorH + 8;
 constexpr float kSensorFloor = 1e-3f;
 constexpr float kSensorLo = 0.3f;  // p < lo: smooth
 constexpr float kSensorHi = 0.7f;  // p > hi: discontinuity; otherwise the plain detector decides
+// Soft training target of a cell: 1 / (1 + exp((psi_min - 1/2) / tau)), with
+// psi_min = min(psi_x, psi_y) of Eq. detector, stored in units of 1/255. A
+// cell whose psi lies within 0.8 tau of the threshold gets a target inside
+// the fallback band, so the network learns to leave it to the plain detector.
+constexpr double kSensorTau = 0.02;
 // Host weight vector: W1[50][32], b1[32], W2[32][32], b2[32], w3[32], b3.
 constexpr int kSensorParams = kSensorIn * kSensorH + kSensorH + kSensorH * kSensorH + kSensorH + kSensorH + 1;
 

@@ -168,6 +168,15 @@ __device__ __forceinline__ bool trouble_cell(const T* r, int st)
     return T(2) * rfma(T(2) * a, b, eps) < rfma(a, a, rfma(b, b, eps));
 }
 
+// The value of psi itself (Eq. detector), same a, b and eps as trouble_cell.
+__device__ __forceinline__ double detector_psi(const double* r, int st)
+{
+    const double eps = 0.9 * 0.5 / (1.0 - 0.9 * 0.5) * 1e-6;
+    const double a = fabs(r[0] - r[-st]) + fabs(rfma(-2.0, r[-st], r[0]) + r[-2 * st]);
+    const double b = fabs(r[0] - r[st]) + fabs(rfma(-2.0, r[st], r[0]) + r[2 * st]);
+    return rfma(2.0 * a, b, eps) / rfma(a, a, rfma(b, b, eps));
+}
+
 // The GRB left value and the MP test of Eqs. mp5Condition and alpha for the left value
 // at j+1/2 from Phi_{j-2..j+2} (p[0..4]) and Phi'_{j-2..j+2} (d[0..4]),
 // xi = 7. Returns the GRB value; `need` is set when the MP limiter must be
@@ -228,30 +237,91 @@ __device__ __forceinline__ T grb_check(const T* p, const T* d, bool& need, const
 }
 
 // Eq. mp-procedure: the MP-limited value given the GRB value pl.
+// Its products are explicitly rounded: it is inlined at two sites (packed
+// and per lane, see meg7_pair) that must round alike.
 template <typename T>
 __device__ __forceinline__ T mp_limit(const T* p, const T* d, T pl)
 {
-    const T dm1 = T(2) * (p[2] - T(2) * p[1] + p[0]) - T(0.5) * (d[2] - d[0]);
-    const T dj = T(2) * (p[3] - T(2) * p[2] + p[1]) - T(0.5) * (d[3] - d[1]);
-    const T dp1 = T(2) * (p[4] - T(2) * p[3] + p[2]) - T(0.5) * (d[4] - d[2]);
-    const T md = T(0.5) * (p[2] + p[3]) - T(0.5) * minmod(dj, dp1);
-    const T ul = p[2] + T(7) * (p[2] - p[1]);
-    const T lc = T(0.5) * (T(3) * p[2] - p[1]) + T(4.0 / 3.0) * minmod(dj, dm1);
+    const T dm1 = rfma(T(2), rfma(T(-2), p[1], p[2]) + p[0], rmul(T(-0.5), d[2] - d[0]));
+    const T dj = rfma(T(2), rfma(T(-2), p[2], p[3]) + p[1], rmul(T(-0.5), d[3] - d[1]));
+    const T dp1 = rfma(T(2), rfma(T(-2), p[3], p[4]) + p[2], rmul(T(-0.5), d[4] - d[2]));
+    const T md = rmul(T(0.5), p[2] + p[3]) - rmul(T(0.5), minmod(dj, dp1));
+    const T ul = rfma(T(7), p[2] - p[1], p[2]);
+    const T lc = rfma(T(4.0 / 3.0), minmod(dj, dm1), rmul(T(0.5), rfma(T(3), p[2], -p[1])));
     T pmin, pmax;
     mp_bounds(p[2], p[3], md, ul, lc, pmin, pmax);
     return pl + minmod(pmin - pl, pmax - pl);
 }
 
-// MEG7 left value at j+1/2 from Phi_{j-2..j+2} (p0..p4) and Phi'_{j-2..j+2}
-// (d0..d4): the GRB value, MP-limited where the MP test fails.
-template <typename T>
-__device__ __forceinline__ T meg7(const GrbCoef<T>& C, T p0, T p1, T p2, T p3, T p4, T d0, T d1, T d2, T d3, T d4)
+// Position of the n-th (0-based) set bit of m; m has more than n set bits.
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n)
 {
-    const T p[5] = {p0, p1, p2, p3, p4}, d[5] = {d0, d1, d2, d3, d4};
-    bool need;
-    const T pl = grb_check(p, d, need, C);
-    if (!need) return pl;
-    return mp_limit(p, d, pl);
+    int pos = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const int c = __popc(m & ((1u << s) - 1u));
+        if (n >= c) {
+            n -= c;
+            m >>= s;
+            pos += s;
+        }
+    }
+    return pos;
+}
+
+// MEG7 left and right values at face j+1/2 of one characteristic field, from
+// its values w[0..5] and gradients e[0..5] at cells j-2..j+3: the left value
+// from cells j-2..j+2, the right one from the stencil mirrored about the face
+// (cell j+1-k in the place of cell j+k, gradients with their sign changed).
+//
+// Where the MP test fails (a third of the values or more in developed flow),
+// the limiter runs; with one face per lane nearly every warp has such a lane,
+// so per lane the limiter would cost the whole warp every time. In FP64, on a
+// warp whose left and right failures together number at most 32, the failing
+// values are packed onto the warp's lanes instead (each lane fetches one
+// stencil by shuffle), limited in one pass and returned by shuffle. Every
+// lane of the warp must call this together. The arithmetic of each value is
+// unchanged, so the result is the same.
+template <typename T>
+__device__ __forceinline__ void meg7_pair(const GrbCoef<T>& C, const T (&w)[6], const T (&e)[6], T& vl, T& vr)
+{
+    const T pL[5] = {w[0], w[1], w[2], w[3], w[4]}, dL[5] = {e[0], e[1], e[2], e[3], e[4]};
+    const T pR[5] = {w[5], w[4], w[3], w[2], w[1]}, dR[5] = {-e[5], -e[4], -e[3], -e[2], -e[1]};
+    bool needL, needR;
+    vl = grb_check(pL, dL, needL, C);
+    vr = grb_check(pR, dR, needR, C);
+    if constexpr (sizeof(T) == 8) {
+        const unsigned mL = __ballot_sync(0xffffffffu, needL), mR = __ballot_sync(0xffffffffu, needR);
+        const int nL = __popc(mL), nR = __popc(mR);
+        if (nL + nR <= 32) {  // warp-uniform
+            const int lane = threadIdx.x & 31;
+            const bool isR = lane >= nL;
+            const bool act = lane < nL + nR;
+            const int src = !act ? lane : (isR ? nth_set_bit(mR, lane - nL) : nth_set_bit(mL, lane));
+            T W[6], E[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                W[k] = __shfl_sync(0xffffffffu, w[k], src);
+                E[k] = __shfl_sync(0xffffffffu, e[k], src);
+            }
+            const T gl = __shfl_sync(0xffffffffu, vl, src), gr = __shfl_sync(0xffffffffu, vr, src);
+            T p[5], d[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                p[k] = isR ? W[5 - k] : W[k];
+                d[k] = isR ? -E[5 - k] : E[k];
+            }
+            const T lim = mp_limit(p, d, isR ? gr : gl);
+            const unsigned below = (1u << lane) - 1u;
+            const T rl = __shfl_sync(0xffffffffu, lim, __popc(mL & below));
+            const T rr = __shfl_sync(0xffffffffu, lim, (nL + __popc(mR & below)) & 31);
+            if (needL) vl = rl;
+            if (needR) vr = rr;
+            return;
+        }
+    }
+    if (needL) vl = mp_limit(pL, dL, vl);
+    if (needR) vr = mp_limit(pR, dR, vr);
 }
 
 // 1/2 (F(f_L) + F(f_R)) at the face after cell f[0]: the sum of Eq.
@@ -346,10 +416,8 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
                 e0[k] = gp - gu;
                 e3[k] = gp + gu;
             }
-            wL[0] = meg7(coef, w0[0], w0[1], w0[2], w0[3], w0[4], e0[0], e0[1], e0[2], e0[3], e0[4]);
-            wR[0] = meg7(coef, w0[5], w0[4], w0[3], w0[2], w0[1], -e0[5], -e0[4], -e0[3], -e0[2], -e0[1]);
-            wL[3] = meg7(coef, w3[0], w3[1], w3[2], w3[3], w3[4], e3[0], e3[1], e3[2], e3[3], e3[4]);
-            wR[3] = meg7(coef, w3[5], w3[4], w3[3], w3[2], w3[1], -e3[5], -e3[4], -e3[3], -e3[2], -e3[1]);
+            meg7_pair(coef, w0, e0, wL[0], wR[0]);
+            meg7_pair(coef, w3, e3, wL[3], wR[3]);
         }
         {  // field 2 (entropy): rho - p / c^2
             T w[6], e[6];
@@ -359,8 +427,7 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
                 w[k] = in.u[0][o * su] - ic2 * in.u[3][o * su];
                 e[k] = in.g[0][o * sg] - ic2 * in.g[3][o * sg];
             }
-            wL[1] = meg7(coef, w[0], w[1], w[2], w[3], w[4], e[0], e[1], e[2], e[3], e[4]);
-            wR[1] = meg7(coef, w[5], w[4], w[3], w[2], w[1], -e[5], -e[4], -e[3], -e[2], -e[1]);
+            meg7_pair(coef, w, e, wL[1], wR[1]);
         }
         {  // field 3 (shear): ut
             T w[6], e[6];
@@ -370,8 +437,7 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
                 w[k] = in.u[2][o * su];
                 e[k] = in.g[2][o * sg];
             }
-            wL[2] = meg7(coef, w[0], w[1], w[2], w[3], w[4], e[0], e[1], e[2], e[3], e[4]);
-            wR[2] = meg7(coef, w[5], w[4], w[3], w[2], w[1], -e[5], -e[4], -e[3], -e[2], -e[1]);
+            meg7_pair(coef, w, e, wL[2], wR[2]);
         }
     } else {
         const T ub = T(0.5) * (in.u[1][0] + in.u[1][su]), vb = T(0.5) * (in.u[2][0] + in.u[2][su]);
@@ -387,10 +453,7 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
         }
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-            wL[f] = meg7(coef, w[f][0], w[f][1], w[f][2], w[f][3], w[f][4], e[f][0], e[f][1], e[f][2], e[f][3],
-                         e[f][4]);
-            wR[f] = meg7(coef, w[f][5], w[f][4], w[f][3], w[f][2], w[f][1], -e[f][5], -e[f][4], -e[f][3], -e[f][2],
-                         -e[f][1]);
+            meg7_pair(coef, w[f], e[f], wL[f], wR[f]);
         }
     }
     // Back with the right eigenvectors: to primitive face states (MEG7-prim)
@@ -717,8 +780,12 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
     // face; x and y faces share the call, with pointers and strides chosen
     // per face).
     {
-        for (int w = tid; w < L::NF; w += NT) {
-            const bool valid = true;
+        // Whole warps iterate together (the limiter packing in meg7_pair
+        // needs all 32 lanes); a lane past the last face repeats it and
+        // stores nothing.
+        for (int w0 = tid & ~31; w0 < L::NF; w0 += NT) {
+            const bool valid = w0 + (tid & 31) < L::NF;
+            const int w = valid ? w0 + (tid & 31) : L::NF - 1;
             const bool xf = w < L::NHX;
             FaceIn<T> in;
             T inv_n, inv_t;

@@ -85,7 +85,7 @@ def load():
         "gbr_batch_set_sensor_weights": (ip, [vp, ctypes.POINTER(ctypes.c_float), ip]),
         "gbr_set_sensor_weights": (ip, [vp, ctypes.POINTER(ctypes.c_float), ip]),
         "gbr_sensor_eval": (ip, [vp, vp, ip]),
-        "gbr_sensor_dataset": (ip, [vp, vp, vp]),
+        "gbr_sensor_dataset": (ip, [vp, vp, vp, vp]),
         "gbr_sensor_train": (ip, [vp, vp, ctypes.c_longlong, ip, ip, dp, dp, ctypes.c_ulonglong,
                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), vp]),
         "gbr_error_string": (ctypes.c_char_p, [ip]),
@@ -259,27 +259,27 @@ def gbr_sensor_eval(ctx, prob, nx, ny):
     return _check(load().gbr_sensor_eval(ctx, p, dev), "gbr_sensor_eval")
 
 
-def gbr_sensor_dataset(ctx, features, labels):
-    """features: device bfloat16 tensor [ncells, 64] (or None); labels:
-    device uint8 tensor [ncells] (or None)."""
-    pf = _ptr(features)[0] if features is not None else None
-    pl = _ptr(labels)[0] if labels is not None else None
-    for a in (features, labels):
+def gbr_sensor_dataset(ctx, features, labels, targets=None):
+    """features: device bfloat16 tensor [ncells, 64]; labels, targets: device
+    uint8 tensors [ncells]; any of them may be None."""
+    bufs = (features, labels, targets)
+    for a in bufs:
         if a is not None and not _ptr(a)[1]:
             raise ValueError("gbr_sensor_dataset writes device buffers")
-    return _check(load().gbr_sensor_dataset(ctx, pf, pl), "gbr_sensor_dataset")
+    pf, pl, pt = (_ptr(a)[0] if a is not None else None for a in bufs)
+    return _check(load().gbr_sensor_dataset(ctx, pf, pl, pt), "gbr_sensor_dataset")
 
 
-def gbr_sensor_train(features, labels, steps, batch, lr, pos_weight, seed, w0, stream=0):
-    """Train from device features [n, 64] bf16 and labels [n] uint8; returns
-    (trained weights, per-step loss)."""
-    n = int(labels.shape[0])
+def gbr_sensor_train(features, targets, steps, batch, lr, pos_weight, seed, w0, stream=0):
+    """Train from device features [n, 64] bf16 and targets [n] uint8 (units
+    of 1/255); returns (trained weights, per-step loss)."""
+    n = int(targets.shape[0])
     if tuple(features.shape) != (n, 64):
         raise ValueError("features must be [n, 64]")
     w = _fvec(w0, GBR_SENSOR_PARAMS).copy()
     loss = np.zeros(int(steps), np.float32)
     fp = ctypes.POINTER(ctypes.c_float)
-    _check(load().gbr_sensor_train(_ptr(features)[0], _ptr(labels)[0], n, int(steps), int(batch), float(lr),
+    _check(load().gbr_sensor_train(_ptr(features)[0], _ptr(targets)[0], n, int(steps), int(batch), float(lr),
                                    float(pos_weight), int(seed) & (2**64 - 1), w.ctypes.data_as(fp),
                                    loss.ctypes.data_as(fp), ctypes.c_void_p(int(stream or 0))),
            "gbr_sensor_train")

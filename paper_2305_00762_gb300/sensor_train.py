@@ -5,10 +5,14 @@ Data: snapshots of seeded 2D four-quadrant Riemann problems with random
 states (rho in [0.1, 2], p in [0.02, 2], |u|, |v| <= 1.5, split point in
 [0.35, 0.65]^2) and of isentropic vortices of strength in [1, 5], run with the
 FP32 form. Every interior cell of a snapshot is one sample: its 5 x 5 stencil
-features (BF16) and the plain detector's label (psi_x < 0.5 or psi_y < 0.5,
-FP64), both written on the device by gbr_sensor_dataset. Training runs in the
-library's hand-written kernels (gbr_sensor_train). Agreement with the plain
-detector is scored on held-out snapshots through gbr_sensor_eval.
+features (BF16) and a soft target derived from the plain detector,
+1 / (1 + exp((psi_min - 0.5) / 0.02)) with psi_min = min(psi_x, psi_y) in FP64
+(the hard label is psi_min < 0.5), all written on the device by
+gbr_sensor_dataset. A cell near the detector threshold thus has a target
+inside the fallback band [0.3, 0.7], where the plain detector decides; the
+network is confident only where the detector's decision is clear. Training
+runs in the library's hand-written kernels (gbr_sensor_train). Agreement with
+the plain detector is scored on held-out snapshots through gbr_sensor_eval.
 
     python -m paper_2305_00762_gb300.sensor_train [--samples 20000000] [--out FILE]
 """
@@ -83,18 +87,19 @@ def snapshots(torch, rng, n, count, cfl=0.5):
 
 
 def dataset(torch, rng, samples, n=512):
-    feats, labels = [], []
-    total = 0
+    """Features, soft targets (units of 1/255) and plain-detector labels."""
+    feats, targets, labels = [], [], []
     per = n * n
     for s in snapshots(torch, rng, n, (samples + per - 1) // per):
         f = torch.empty((per, 64), dtype=torch.bfloat16, device="cuda")
+        t = torch.empty(per, dtype=torch.uint8, device="cuda")
         y = torch.empty(per, dtype=torch.uint8, device="cuda")
-        gbr.gbr_sensor_dataset(s.ctx, f, y)
+        gbr.gbr_sensor_dataset(s.ctx, f, y, t)
         feats.append(f)
+        targets.append(t)
         labels.append(y)
-        total += per
     torch.cuda.synchronize()
-    return torch.cat(feats)[:samples], torch.cat(labels)[:samples]
+    return torch.cat(feats)[:samples], torch.cat(targets)[:samples], torch.cat(labels)[:samples]
 
 
 def agreement(torch, rng, w, count=8, n=512):
@@ -120,15 +125,27 @@ def agreement(torch, rng, w, count=8, n=512):
     return stats
 
 
+# Fractions of the steps and learning-rate multipliers of the training phases
+# (Adam restarts at each phase).
+LR_SCHEDULE = ((0.6, 1.0), (0.25, 0.25), (0.15, 1.0 / 16.0))
+
+
 def train(samples=20_000_000, epochs=4.0, batch=8192, lr=2e-3, pos_weight=6.0, seed=SEED, out=DEFAULT_WEIGHTS,
           verbose=True):
     import torch
     rng = np.random.default_rng(seed)
     t0 = time.time()
-    X, y = dataset(torch, rng, samples)
+    X, tgt, y = dataset(torch, rng, samples)
     t1 = time.time()
     steps = max(1, int(epochs * X.shape[0] / batch))
-    w, loss = gbr.gbr_sensor_train(X, y, steps, batch, lr, pos_weight, seed, init_weights(rng))
+    w = init_weights(rng)
+    losses = []
+    for k, (frac, scale) in enumerate(LR_SCHEDULE):  # step-wise learning-rate decay
+        n = max(1, int(round(frac * steps)))
+        w, loss = gbr.gbr_sensor_train(X, tgt, n, batch, lr * scale, pos_weight, seed + k, w)
+        losses.append(loss)
+    loss = np.concatenate(losses)
+    steps = int(loss.size)
     t2 = time.time()
     held = agreement(torch, np.random.default_rng(seed + 1), w)
     info = {"seed": seed, "samples": int(X.shape[0]), "label_fraction": float(y.float().mean()),

@@ -43,17 +43,34 @@ def test_dataset_labels_and_features(env):
     n = c.nx * c.ny
     f = torch.empty((n, 64), dtype=torch.bfloat16, device="cuda")
     y = torch.empty(n, dtype=torch.uint8, device="cuda")
-    gbr.gbr_sensor_dataset(s.ctx, f, y)
+    t = torch.empty(n, dtype=torch.uint8, device="cuda")
+    gbr.gbr_sensor_dataset(s.ctx, f, y, t)
     torch.cuda.synchronize()
     lab = O.trouble_labels(cfg_of(O, c), c.Q).reshape(-1)
     assert np.array_equal(y.cpu().numpy(), lab)          # no psi ties in this data
     assert lab.sum() > 100
+    # soft targets: the same psi in FP64; exp and the rounding may differ by one unit
+    to = OS.soft_target(O.psi_min(cfg_of(O, c), c.Q)).reshape(-1).astype(int)
+    tg = t.cpu().numpy().astype(int)
+    assert np.abs(tg - to).max() <= 1 and np.mean(tg == to) > 0.999
     fg = f.float().cpu().numpy()
     assert np.all(fg[:, 50:] == 0)
     fo = OS.bf16_round(OS.features(cfg_of(O, c), c.Q))
     # the FP32 primitives may round differently by an ulp: one BF16 step
     assert np.all(np.abs(fg[:, :50] - fo) <= np.abs(fo) * 2.0 ** -7 + 1e-6)
     assert np.mean(fg[:, :50] == fo) > 0.999
+    s.close()
+    # smeared jumps (the oracle's own run to t = 0.05): psi between 0 and 1
+    c = C.riemann_2d(48)
+    Q, _, _ = O.run(cfg_of(O, c), c.Q, 0.05, 0.5)
+    s = gbr.Solver.for_case(c)
+    s.set_state(Q)
+    t = torch.empty(c.nx * c.ny, dtype=torch.uint8, device="cuda")
+    gbr.gbr_sensor_dataset(s.ctx, None, None, t)
+    to = OS.soft_target(O.psi_min(cfg_of(O, c), Q)).reshape(-1).astype(int)
+    tg = t.cpu().numpy().astype(int)
+    assert np.abs(tg - to).max() <= 1 and np.mean(tg == to) > 0.99
+    assert len(np.unique(to)) > 5
     s.close()
 
 
@@ -85,9 +102,9 @@ def test_training_learns_the_detector(env):
     torch, O, OS, gbr = env
     from paper_2305_00762_gb300 import sensor_train as T
     rng = np.random.default_rng(5)
-    X, y = T.dataset(torch, rng, 600_000, n=256)
+    X, tgt, y = T.dataset(torch, rng, 600_000, n=256)
     w0 = T.init_weights(np.random.default_rng(6))
-    w, loss = gbr.gbr_sensor_train(X, y, 400, 4096, 2e-3, 3.0, 7, w0)
+    w, loss = gbr.gbr_sensor_train(X, tgt, 400, 4096, 2e-3, 3.0, 7, w0)
     first, last = loss[:20].mean(), loss[-20:].mean()
     assert np.all(np.isfinite(loss)) and last < 0.5 * first, (first, last)
     held = T.agreement(torch, np.random.default_rng(8), w, count=4, n=256)

@@ -70,3 +70,28 @@ def test_labels_at_a_step(oracle_mod):
     cols = np.nonzero(lab[0])[0]
     assert list(cols) == [s - 2, s - 1, s, s + 1]
     assert np.all(lab == lab[0])
+
+
+def test_psi_min_at_a_step_and_flat(oracle_mod, OS):
+    """Eq. detector by hand: on flat data a = b = 0 and psi = eps/eps = 1;
+    beside a density step 1 -> 0.4 (stencil 1, 1, 1, 0.4, 0.4 centred on the
+    last 1) a = 0, b = 0.6 + 0.6, psi = eps / (1.44 + eps). Labels are exactly
+    psi_min < 1/2, and the soft target is 1/2 there, monotone in psi."""
+    O = oracle_mod
+    n, s = 24, 11
+    rho = np.where(np.arange(n)[None, :] >= s, 0.4, 1.0) * np.ones((n, 1))
+    z = np.zeros_like(rho)
+    Q = C.prim_to_cons(rho, z, z, 1 + z, 1.4)
+    cfg = O.Config(n, n, 0.1, 0.1, 1.4, 0.0, 0.72, (1, 1, 0, 0))
+    psi = O.psi_min(cfg, Q)
+    eps = 0.9 * 0.5 / (1 - 0.9 * 0.5) * 1e-6
+    assert np.all(psi[:, :s - 3] == 1.0) and np.all(psi[:, s + 3:] == 1.0)
+    assert psi[5, s - 1] == pytest.approx(eps / (1.44 + eps), rel=1e-12)
+    assert np.array_equal(O.trouble_labels(cfg, Q), (psi < 0.5).astype(np.uint8))
+    Qr = C.kelvin_helmholtz(32, np.random.default_rng(9)).Q
+    cr = O.Config(32, 32, 1 / 32, 1 / 32, 1.4, 0.0, 0.72, (0, 0, 0, 0))
+    pr = O.psi_min(cr, Qr)
+    assert np.array_equal(O.trouble_labels(cr, Qr), (pr < 0.5).astype(np.uint8))
+    t = OS.soft_target(np.array([0.0, 0.5 - 0.8 * OS.TAU, 0.5, 0.5 + 0.8 * OS.TAU, 1.0]))
+    assert t[0] == 255 and t[-1] == 0 and t[2] == 128
+    assert 0.3 * 255 < t[3] < t[2] < t[1] < 0.7 * 255 + 1
