@@ -66,6 +66,12 @@ def peaks():
 # of the plain smooth-region path comes from paper_2305_00762_gb300.costs,
 # which derives it term by term.
 FP64_PEAK_GFLOPS = 1250.0     # GB300 FP64 (non-tensor) nominal, 152 SMs
+# DRAM bytes (read + write) per launch of the FP64 stage kernel on the default
+# 1024^2 workload, mean over the three stages of a step, from an ncu capture of
+# `bench.py --steps 3 --warmup 1 --no-cpu-baseline --no-ensemble --profile`
+# (dram__bytes_read.sum + dram__bytes_write.sum). Re-measure when the kernel
+# changes; reported only for that workload.
+F64_STAGE_DRAM_BYTES_1024 = 59.79e6
 
 
 class ClockSampler:
@@ -399,7 +405,8 @@ def main():
                    "window_t_start": round(t_start, 6), "prelude_fp64_steps": pre_steps,
                    "replicas": ws},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                     "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                     "frac": achieved / FP64_PEAK_GFLOPS,
+                     "traffic": F64_STAGE_DRAM_BYTES_1024 if args.n == 1024 else None, "traffic_unit": "bytes/launch",
                      "kernel": "stage_kernel<double> (fused residual + RK stage)",
                      "flop_per_cell_update": flop_cell, "stage_ms_avg": stage_avg_s * 1e3,
                      "hbm_achieved_gbs": hbm, "hbm_peak_gbs": hbm_peak, "hbm_frac": hbm / hbm_peak},

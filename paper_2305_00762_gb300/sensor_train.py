@@ -130,7 +130,7 @@ def agreement(torch, rng, w, count=8, n=512):
 LR_SCHEDULE = ((0.6, 1.0), (0.25, 0.25), (0.15, 1.0 / 16.0))
 
 
-def train(samples=20_000_000, epochs=4.0, batch=8192, lr=2e-3, pos_weight=6.0, seed=SEED, out=DEFAULT_WEIGHTS,
+def train(samples=20_000_000, epochs=256.0, batch=8192, lr=2e-3, pos_weight=1.0, seed=SEED, out=DEFAULT_WEIGHTS,
           verbose=True):
     import torch
     rng = np.random.default_rng(seed)
@@ -170,8 +170,8 @@ def load_weights(path=DEFAULT_WEIGHTS):
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--samples", type=int, default=20_000_000)
-    ap.add_argument("--epochs", type=float, default=4.0)
-    ap.add_argument("--pos-weight", type=float, default=6.0)
+    ap.add_argument("--epochs", type=float, default=256.0)
+    ap.add_argument("--pos-weight", type=float, default=1.0)
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     a = ap.parse_args()
     from . import build
