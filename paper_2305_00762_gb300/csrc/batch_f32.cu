@@ -4,7 +4,7 @@
 
 namespace gbr {
 
-static const TileShape kShapesF32[] = {{32, 16}, {32, 8}, {64, 8}};
+static const TileShape kShapesF32[] = {{28, 16}, {32, 16}, {32, 8}};
 
 int batch_tile_shapes_f32(const TileShape** shapes)
 {
@@ -17,15 +17,15 @@ cudaError_t launch_batch_stage_f32(int shape, const BatchCase* cases, int ncases
 {
     if (sensor) {
         switch (shape) {
-        case 0: return launch_batch_t<float, 32, 16, 256, true>(cases, ncases, total_tiles, stage, s, sensor);
-        case 1: return launch_batch_t<float, 32, 8, 256, true>(cases, ncases, total_tiles, stage, s, sensor);
-        default: return launch_batch_t<float, 64, 8, 256, true>(cases, ncases, total_tiles, stage, s, sensor);
+        case 0: return launch_batch_t<float, 28, 16, 256, true>(cases, ncases, total_tiles, stage, s, sensor);
+        case 1: return launch_batch_t<float, 32, 16, 256, true>(cases, ncases, total_tiles, stage, s, sensor);
+        default: return launch_batch_t<float, 32, 8, 256, true>(cases, ncases, total_tiles, stage, s, sensor);
         }
     }
     switch (shape) {
-    case 0: return launch_batch_t<float, 32, 16, 256>(cases, ncases, total_tiles, stage, s);
-    case 1: return launch_batch_t<float, 32, 8, 256>(cases, ncases, total_tiles, stage, s);
-    default: return launch_batch_t<float, 64, 8, 256>(cases, ncases, total_tiles, stage, s);
+    case 0: return launch_batch_t<float, 28, 16, 256>(cases, ncases, total_tiles, stage, s);
+    case 1: return launch_batch_t<float, 32, 16, 256>(cases, ncases, total_tiles, stage, s);
+    default: return launch_batch_t<float, 32, 8, 256>(cases, ncases, total_tiles, stage, s);
     }
 }
 

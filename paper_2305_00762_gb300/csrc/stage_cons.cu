@@ -6,14 +6,14 @@ namespace gbr {
 
 cudaError_t launch_stage_cons_f64(const StageParams& p, cudaStream_t s)
 {
-    if (p.ph.mu > 0.0) return launch_stage_t<double, 32, 8, 256, true, false, 7, true>(p, s);
-    return launch_stage_t<double, 32, 8, 256, false, false, 7, true>(p, s);
+    if (p.ph.mu > 0.0) return launch_stage_t<double, 16, 16, 256, true, false, 7, true>(p, s);
+    return launch_stage_t<double, 16, 16, 256, false, false, 7, true>(p, s);
 }
 
 cudaError_t launch_stage_cons_f32(const StageParams& p, cudaStream_t s)
 {
-    if (p.ph.mu > 0.0) return launch_stage_t<float, 32, 16, 256, true, false, 7, true>(p, s);
-    return launch_stage_t<float, 32, 16, 256, false, false, 7, true>(p, s);
+    if (p.ph.mu > 0.0) return launch_stage_t<float, 28, 16, 256, true, false, 7, true>(p, s);
+    return launch_stage_t<float, 28, 16, 256, false, false, 7, true>(p, s);
 }
 
 }  // namespace gbr

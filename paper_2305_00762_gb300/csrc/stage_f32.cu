@@ -8,15 +8,15 @@ cudaError_t launch_stage_f32(const StageParams& p, cudaStream_t s)
 {
     if (p.ph.cons) return launch_stage_cons_f32(p, s);
     if (p.ph.order == 4) {  // the learned sensor is trained for the seventh-order scheme only
-        if (p.ph.mu > 0.0) return launch_stage_t<float, 32, 16, 256, true, false, 4>(p, s);
-        return launch_stage_t<float, 32, 16, 256, false, false, 4>(p, s);
+        if (p.ph.mu > 0.0) return launch_stage_t<float, 28, 16, 256, true, false, 4>(p, s);
+        return launch_stage_t<float, 28, 16, 256, false, false, 4>(p, s);
     }
     if (p.sensor) {
-        if (p.ph.mu > 0.0) return launch_stage_t<float, 32, 16, 256, true, true>(p, s);
-        return launch_stage_t<float, 32, 16, 256, false, true>(p, s);
+        if (p.ph.mu > 0.0) return launch_stage_t<float, 28, 16, 256, true, true>(p, s);
+        return launch_stage_t<float, 28, 16, 256, false, true>(p, s);
     }
-    if (p.ph.mu > 0.0) return launch_stage_t<float, 32, 16, 256, true>(p, s);
-    return launch_stage_t<float, 32, 16, 256, false>(p, s);
+    if (p.ph.mu > 0.0) return launch_stage_t<float, 28, 16, 256, true>(p, s);
+    return launch_stage_t<float, 28, 16, 256, false>(p, s);
 }
 
 }  // namespace gbr

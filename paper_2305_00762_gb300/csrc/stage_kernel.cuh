@@ -527,24 +527,29 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
 
     // HLLC in the form 1/2 (F_L + F_R) - 1/2 |A| (Q_R - Q_L), Eq. Riemann_revisit,
     // with Toro's star states; k (E/rho + (S*-u)(S* + p/(rho (S-u)))) is
-    // expanded so that the only divisions are 1/(S_K - S*), S* and the Roe
-    // weight.
+    // expanded so that the only divisions are 1/((S_L - S*)(S_R - S*)), S* and
+    // the Roe weight.
     {
         const T rsL = trsqrt(rL), rsR = trsqrt(rR);  // 1/sqrt(rho)
         const T sL = rL * rsL, sR = rR * rsR;        // sqrt(rho)
         const T irL = rsL * rsL, irR = rsR * rsR;    // 1/rho
-        const T cL = tsqrt(P.gamma * pL * irL), cR = tsqrt(P.gamma * pR * irR);
+        // c = c^2 / sqrt(c^2): a reciprocal square root instead of a square root
+        const T c2L = P.gamma * pL * irL, c2R = P.gamma * pR * irR;
+        const T cL = c2L * trsqrt(c2L), cR = c2R * trsqrt(c2R);
         const T HL = (EL + pL) * irL, HR = (ER + pR) * irR;
         const T isum = T(1) / (sL + sR);
         const T ut = (sL * unL + sR * unR) * isum;
         const T vt = (sL * utL + sR * utR) * isum;
         const T Ht = (sL * HL + sR * HR) * isum;
-        const T ct = tsqrt(P.gm1 * (Ht - T(0.5) * (ut * ut + vt * vt)));
+        const T c2t = P.gm1 * (Ht - T(0.5) * (ut * ut + vt * vt));
+        const T ct = c2t * trsqrt(c2t);
         const T SL = tmin(unL - cL, ut - ct);
         const T SR = tmax(unR + cR, ut + ct);
         const T mL = rL * (SL - unL), mR = rR * (SR - unR);
         const T Ss = (pR - pL + mL * unL - mR * unR) / (mL - mR);
-        const T iL = T(1) / (SL - Ss), iR = T(1) / (SR - Ss);
+        // 1/(S_L - S*) and 1/(S_R - S*) from one division
+        const T dL = SL - Ss, dR = SR - Ss, iLR = T(1) / (dL * dR);
+        const T iL = dR * iLR, iR = dL * iLR;
         const T kL = mL * iL, kR = mR * iR;
         const T QsL[4] = {kL, kL * Ss, kL * utL, kL * (EL * irL + (Ss - unL) * Ss) + (Ss - unL) * pL * iL};
         const T QsR[4] = {kR, kR * Ss, kR * utR, kR * (ER * irR + (Ss - unR) * Ss) + (Ss - unR) * pR * iR};
