@@ -24,7 +24,7 @@ template <typename T, int BX, int BY, int NT, bool LEARNED>
 __global__ void __launch_bounds__(NT) batch_stage_kernel(const BatchCase* __restrict__ cases, int ncases,
                                                          int total_tiles, int stage, const SensorDev* sensor)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const double ca = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
     const double cbc = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
     for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {

@@ -96,6 +96,7 @@ int read_back_errors(gbr_ctx* c, DevScalars* host)
 {
     GBR_TRY(cudaMemcpyAsync(host, c->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
     GBR_TRY(cudaStreamSynchronize(c->stream));
+    if (host->err & 2u) return GBR_ERR_TIMEOUT;
     return (host->err & 1u) ? GBR_ERR_NONPHYSICAL : GBR_OK;
 }
 

@@ -2,6 +2,7 @@
 // translation units. Not part of the public interface (include/gbr.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -101,6 +102,12 @@ cudaError_t launch_batch_stage_f32(int shape, const BatchCase* cases, int ncases
 // Learned sensor (sensor.cu): host packing of the weight vector, per-cell
 // evaluation / dataset extraction on a padded state, training.
 void pack_sensor(const float* w, SensorDev* out);
+// Tensor map of a padded FP64 state for the stage kernels' tile staging:
+// 3-D (x over the nx + 12 padded columns, y over the ny + 12 padded rows,
+// the 4 fields), box box_w x box_h x 4, out-of-range cells read as zero.
+// Host-only; encodings are cached per (state, grid, box).
+cudaError_t encode_state_map(const Grid& g, const double* q, int box_w, int box_h, CUtensorMap* out);
+
 cudaError_t launch_sensor_tile(const Grid& g, double gamma, const double* q, const SensorDev* w, float* prob,
                                void* feat_bf16, unsigned char* label, unsigned char* target, cudaStream_t s);
 cudaError_t launch_sensor_train(const void* X_bf16, const unsigned char* y, long long n, int steps, int batch,

@@ -158,5 +158,6 @@ extern "C" int gbr_step_static(const double* Q_in, double* Q_out, int nx, int ny
     if ((rc = status_of(cudaMemcpyAsync(&err, &ds->err, sizeof(err), cudaMemcpyDeviceToHost, s))) != GBR_OK)
         return rc;
     if ((rc = status_of(cudaStreamSynchronize(s))) != GBR_OK) return rc;
+    if (err & 2u) return GBR_ERR_TIMEOUT;
     return (err & 1u) ? GBR_ERR_NONPHYSICAL : GBR_OK;
 }

@@ -13,6 +13,7 @@
 // the positivity check are always FP64.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -67,6 +68,15 @@ struct TileLayout {
     {
         return LEARNED ? sensor_offset<T, NT>() + sizeof(SensorDev) : bytes<T, NT>();
     }
+
+    // TMA staging: the FP64 conservative tile + halo lands as [4][RH][RW]
+    // doubles on top of the per-cell and face arrays (first written after
+    // phase 0, and below the MEG7-cons copy that phase 0 fills).
+    static constexpr size_t kRawBytes = sizeof(double) * 4 * (size_t)NU;
+    template <typename T>
+    static constexpr size_t raw_offset() { return sizeof(T) * (size_t)oGX; }
+    template <typename T>
+    static constexpr size_t raw_limit() { return sizeof(T) * (size_t)(CONS ? oQc : oEnd); }
 };
 
 template <typename T>
@@ -621,9 +631,66 @@ __device__ __forceinline__ double warp_max(double v)
 // the single-grid kernel (one CTA per tile) and the persistent batch kernel
 // (a CTA walks many tiles of many grids). Starts and ends with all threads
 // synchronised, so consecutive calls may reuse the shared memory.
-template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED = false, int ORDER = 7, bool CONS = false>
+// ---------------------------------------------------------------------------
+// Tile staging by the tensor-memory accelerator: one thread issues a 3-D
+// tiled bulk copy (x, y, field) of the tile + halo into shared memory, and
+// the CTA waits on an mbarrier for its byte count.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Non-blocking test of phase `parity` of the mbarrier.
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity)
+{
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for phase 0 of the mbarrier with an iteration limit (about a second);
+// false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar)
+{
+    for (int it = 0; it < (1 << 24); ++it) {
+        if (mbar_test(bar, 0)) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Error-word bits: 1 = non-physical state, 2 = a bounded wait gave up.
+constexpr unsigned kErrNonPhysical = 1u, kErrTimeout = 2u;
+
+template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED = false, int ORDER = 7, bool CONS = false,
+          bool TMA = false>
 __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, const int ty0,
-                                           unsigned char* smem_raw)
+                                           unsigned char* smem_raw, const CUtensorMap* tmap = nullptr)
 {
     using L = TileLayout<BX, BY, VISC, CONS>;
     T* const sm = reinterpret_cast<T*>(smem_raw);
@@ -652,28 +719,67 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
     const T inv_dx = T(1.0 / P.ph.dx), inv_dy = T(1.0 / P.ph.dy);
 
     // Phase 0: stage the tile + halo as primitive variables (Eq. pressure).
-    // Region cell (rx, ry) is padded cell (tx0 + rx, ty0 + ry); beyond the
-    // padded extent (ragged last tiles) the load is clamped to a valid cell
-    // whose results are never stored.
-    for (int idx = tid; idx < NU; idx += NT) {
-        const int ry = idx / RW, rx = idx - ry * RW;
-        const int gx = min(tx0 + rx, nx + 2 * kGhost - 1);
-        const int gy = min(ty0 + ry, ny + 2 * kGhost - 1);
-        const long long o = (long long)gy * pitch + gx;
-        const T r = T(P.q[o]);
+    // Region cell (rx, ry) is padded cell (tx0 + rx, ty0 + ry).
+    auto stage_cell = [&](int idx, double q0, double q1, double q2, double q3) {
+        const T r = T(q0);
         const T ir = T(1) / r;
-        const T u = T(P.q[o + plane]) * ir;
-        const T v = T(P.q[o + 2 * plane]) * ir;
-        const T p = ph.gm1 * (T(P.q[o + 3 * plane]) - T(0.5) * r * sumsq(u, v));
+        const T u = T(q1) * ir;
+        const T v = T(q2) * ir;
+        const T p = ph.gm1 * (T(q3) - T(0.5) * r * sumsq(u, v));
         sU[idx] = r;
         sU[NU + idx] = u;
         sU[2 * NU + idx] = v;
         sU[3 * NU + idx] = p;
         if constexpr (CONS) {
             sQc[idx] = r;
-            sQc[NU + idx] = T(P.q[o + plane]);
-            sQc[2 * NU + idx] = T(P.q[o + 2 * plane]);
-            sQc[3 * NU + idx] = T(P.q[o + 3 * plane]);
+            sQc[NU + idx] = T(q1);
+            sQc[2 * NU + idx] = T(q2);
+            sQc[3 * NU + idx] = T(q3);
+        }
+    };
+    bool staged = false;
+    if constexpr (TMA) {
+        // The whole region in one tensor copy; cells beyond the padded extent
+        // (ragged last tiles) read as zero and only feed results that are
+        // never stored.
+        static_assert(BX % 2 == 0 && L::RW % 2 == 0, "TMA x offsets and rows must be 16-byte multiples");
+        static_assert(L::RW <= 256 && L::RH <= 256, "TMA box too large");
+        static_assert(L::template raw_offset<T>() + L::kRawBytes <= L::template raw_limit<T>(),
+                      "TMA landing area overlaps live shared memory");
+        double* raw = reinterpret_cast<double*>(smem_raw + L::template raw_offset<T>());
+        __shared__ __align__(8) unsigned long long tma_bar;  // never reused for anything else
+        unsigned long long* bar = &tma_bar;
+        if ((smem_addr(raw) & 127u) == 0) {  // uniform: the copy needs a 128-byte aligned destination
+            if (tid == 0) {
+                mbar_init(bar, 1);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            }
+            __syncthreads();
+            if (tid == 0) {
+                mbar_arrive_expect_tx(bar, (unsigned)L::kRawBytes);
+                tma_load_3d(raw, tmap, tx0, ty0, 0, bar);
+            }
+            const bool ok = mbar_wait_bounded(bar);
+            if (__syncthreads_or(!ok)) {
+                // Give the copy one more bounded wait before the CTA leaves.
+                mbar_wait_bounded(bar);
+                if (tid == 0) atomicOr(P.err, kErrTimeout);
+                return;
+            }
+            for (int idx = tid; idx < NU; idx += NT)
+                stage_cell(idx, raw[idx], raw[NU + idx], raw[2 * NU + idx], raw[3 * NU + idx]);
+            staged = true;
+        }
+    }
+    if (!staged) {
+        // Plain loads, clamped to the padded extent (the clamped cells only
+        // feed results that are never stored).
+        for (int idx = tid; idx < NU; idx += NT) {
+            const int ry = idx / RW, rx = idx - ry * RW;
+            const int gx = min(tx0 + rx, nx + 2 * kGhost - 1);
+            const int gy = min(ty0 + ry, ny + 2 * kGhost - 1);
+            const long long o = (long long)gy * pitch + gx;
+            stage_cell(idx, P.q[o], P.q[o + plane], P.q[o + 2 * plane], P.q[o + 3 * plane]);
         }
     }
     if constexpr (LEARNED)
@@ -949,7 +1055,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         }
     }
     if (P.qout) {
-        if (__syncthreads_or(bad) && tid == 0) atomicOr(P.err, 1u);
+        if (__syncthreads_or(bad) && tid == 0) atomicOr(P.err, kErrNonPhysical);
     }
     if (P.lam_out) {
         __shared__ double red[NT / 32];
@@ -965,11 +1071,14 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
     __syncthreads();
 }
 
+// One CTA per tile; the tile + halo is staged by a tensor copy described by
+// tmap (the stage's input state, see encode_state_map).
 template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED, int ORDER, bool CONS>
-__global__ void __launch_bounds__(NT) stage_kernel(const StageParams P)
+__global__ void __launch_bounds__(NT) stage_kernel(const StageParams P, const __grid_constant__ CUtensorMap tmap)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    stage_tile<T, BX, BY, NT, VISC, LEARNED, ORDER, CONS>(P, blockIdx.x * BX, blockIdx.y * BY, smem_raw);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    stage_tile<T, BX, BY, NT, VISC, LEARNED, ORDER, CONS, true>(P, blockIdx.x * BX, blockIdx.y * BY, smem_raw,
+                                                                 &tmap);
 }
 
 template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED = false, int ORDER = 7, bool CONS = false>
@@ -984,8 +1093,11 @@ cudaError_t launch_stage_t(const StageParams& p, cudaStream_t s)
         if (e != cudaSuccess) return e;
         configured = true;
     }
+    CUtensorMap map;
+    const cudaError_t e = encode_state_map(p.g, p.q, L::RW, L::RH, &map);
+    if (e != cudaSuccess) return e;
     dim3 grid((p.g.nx + BX - 1) / BX, (p.g.ny + BY - 1) / BY);
-    kern<<<grid, NT, smem, s>>>(p);
+    kern<<<grid, NT, smem, s>>>(p, map);
     return cudaGetLastError();
 }
 

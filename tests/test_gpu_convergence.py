@@ -1,0 +1,60 @@
+"""Example 1 protocol on the CUDA path: the isentropic vortex on [0,10]^2
+(strength 5, free stream (1,1,1,1)) at 32^2, 64^2 and 128^2, 100 RK stages
+(33 TVD-RK3 steps) at CFL 0.5 with dt = CFL/lambda from the device, against
+the exactly translated vortex and against the oracle's own run.
+
+With a fixed number of stages the end time halves with each refinement and
+dt ~ dx, so the observed order mixes the scheme's seventh-order spatial
+error (dominant from 32^2 to 64^2: ~8) with the third-order RK3 error
+(dominant from 64^2 to 128^2: ~4); the spatial order alone is pinned on the
+oracle at fixed time and CFL 0.2 (Table 'Order of accuracy')."""
+import numpy as np
+import pytest
+
+from paper_2305_00762_gb300 import cases as C
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle as O
+    from paper_2305_00762_gb300 import build, gbr
+    build.build()
+    O.build()
+    gbr.load()
+    return torch, O, gbr
+
+
+def test_vortex_100_stages(env):
+    torch, O, gbr = env
+    errs = []
+    for n in (32, 64, 128):
+        c = C.isentropic_vortex(n)
+        s = gbr.Solver.for_case(c)
+        s.set_state(c.Q)
+        for _ in range(33):
+            s.step_cfl(0.5)
+        Q = s.get_state()
+        t = s.time()
+        s.close()
+        cfg = O.Config(c.nx, c.ny, c.dx, c.dy, c.gamma, c.mu, c.Pr, c.bc)
+        Qo, to = c.Q.copy(), 0.0
+        for _ in range(33):
+            dt = 0.5 / O.max_wavespeed(cfg, Qo)
+            Qo, rc = O.rk3_step(cfg, Qo, dt)
+            assert rc == 0
+            to += dt
+        assert abs(t - to) < 1e-13 * to
+        scale = np.abs(Qo).reshape(4, -1).max(axis=1)
+        scale[1:3] = scale[1:3].max()
+        assert (np.abs(Q - Qo).reshape(4, -1).max(axis=1) / scale).max() < 1e-11
+        xc, _ = C.centres(n, 0.0, 10.0)
+        X, Y = np.meshgrid(xc, xc)
+        errs.append(np.abs(Q[0] - C.vortex_prims(X, Y, t)[0]).mean())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    print("density L1 errors", errs, "orders", orders)
+    assert orders[0] > 6.5 and orders[1] > 3.0
