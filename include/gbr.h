@@ -102,7 +102,13 @@ typedef enum {
      * their velocity and temperature gradients from the conservative ones by
      * the chain rule of Sec. 2.2). Order 7 only; the learned sensor is not
      * used with it (the density detector decides). */
-    GBR_OPT_VARIABLES = 5
+    GBR_OPT_VARIABLES = 5,
+    /* Failure-detection test hook: 1 makes every single-grid stage launch
+     * wait for 16 bytes more than its tile copy delivers, so each CTA's
+     * bounded staging wait gives up (after a few seconds) and the next
+     * synchronising call reports GBR_ERR_TIMEOUT; the copy itself completes,
+     * nothing faults, and gbr_set_state clears the error. 0: off (default). */
+    GBR_OPT_STALL_TEST = 6
 } gbr_option;
 
 /* Kernel classes reported by gbr_get_timing. */

@@ -38,6 +38,7 @@ struct gbr_ctx {
     int ev_used;
     int launches[GBR_KERNEL_CLASSES];
     int dropped;
+    int stall_test;  // GBR_OPT_STALL_TEST
     // learned sensor
     SensorDev* d_sensor;
     float* prob;   // per-cell sensor output scratch
@@ -164,6 +165,7 @@ StageParams stage_params(gbr_ctx* c, const double* q)
     p.sigx = c->record_flags ? c->sigx : nullptr;
     p.sigy = c->record_flags ? c->sigy : nullptr;
     p.sensor = (c->sensor && c->precision == 32) ? c->d_sensor : nullptr;
+    p.stall_bytes = c->stall_test ? 16u : 0u;
     return p;
 }
 
@@ -335,8 +337,10 @@ int gbr_residual(gbr_ctx* c, double* res, int on_device)
     if (on_device) return GBR_OK;
     GBR_TRY(cudaMemcpyAsync(res, c->R, sizeof(double) * 4 * (size_t)c->g.nx * c->g.ny, cudaMemcpyDeviceToHost,
                             c->stream));
-    GBR_TRY(cudaStreamSynchronize(c->stream));
-    return GBR_OK;
+    DevScalars h;
+    rc = read_back_errors(c, &h);  // synchronises
+    if (rc == GBR_ERR_TIMEOUT || rc == GBR_ERR_CUDA) return rc;
+    return GBR_OK;  // the non-physical flag concerns stage updates, not the residual
 }
 
 int gbr_step(gbr_ctx* c, double dt)
@@ -413,6 +417,10 @@ int gbr_set_option(gbr_ctx* c, int key, double val)
         if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;
         if (val == 1.0 && c->ph.order != 7) return GBR_ERR_UNSUPPORTED;
         c->ph.cons = (int)val;
+        return GBR_OK;
+    case GBR_OPT_STALL_TEST:
+        if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;
+        c->stall_test = (int)val;
         return GBR_OK;
     case GBR_OPT_TIMING:
         if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;

@@ -51,6 +51,7 @@ struct StageParams {
     double dt;               // host dt otherwise
     double ca, cb, cc;       // qout = ca * qn + cb * q + cc * dt * Res
     const SensorDev* sensor; // learned-sensor weights (FP32 form) or nullptr
+    unsigned stall_bytes;    // failure-detection test hook: extra bytes the tile staging waits for (0)
 };
 
 // Ghost fill of one padded state, plus the per-step scalar bookkeeping done

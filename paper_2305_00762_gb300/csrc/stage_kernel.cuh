@@ -756,7 +756,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
             }
             __syncthreads();
             if (tid == 0) {
-                mbar_arrive_expect_tx(bar, (unsigned)L::kRawBytes);
+                mbar_arrive_expect_tx(bar, (unsigned)L::kRawBytes + P.stall_bytes);
                 tma_load_3d(raw, tmap, tx0, ty0, 0, bar);
             }
             const bool ok = mbar_wait_bounded(bar);
