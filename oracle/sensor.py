@@ -82,6 +82,39 @@ def features(cfg: Config, Q) -> np.ndarray:
     return out
 
 
+def features_at(cfg: Config, Q, rows, cols, prims=None) -> np.ndarray:
+    """Features of the listed cells ([n, 50] float32, as features()); rows
+    and cols are interior indices and may reach 3 cells into the ghost
+    layers. prims: the (rho, p) pair of prims_fp32, if already computed."""
+    r, p = prims if prims is not None else prims_fp32(cfg, Q)
+    rows = np.asarray(rows, dtype=np.int64) + G
+    cols = np.asarray(cols, dtype=np.int64) + G
+    out = np.zeros((rows.size, N_IN), np.float32)
+    for fi, a in enumerate((r, p)):
+        c = a[rows, cols]
+        diffs = [a[rows + dy, cols + dx] - c for dy in range(-2, 3) for dx in range(-2, 3)]
+        m = np.zeros_like(c)
+        for d in diffs:
+            m = np.maximum(m, np.abs(d))
+        s = np.float32(1) / (m + FLOOR)
+        for k, d in enumerate(diffs):
+            out[:, 25 * fi + k] = d * s
+    return out
+
+
+def direction_flags(p, trouble_x, trouble_y):
+    """Per-direction detector flags of cells under the learned sensor, from
+    its output p and the plain per-direction tests: p < LO no flag; LO..HI
+    the plain test of that direction; p > HI the plain tests give the
+    direction, and a cell neither test marks is flagged in both."""
+    d = decision(p)
+    tx = np.asarray(trouble_x, dtype=bool)
+    ty = np.asarray(trouble_y, dtype=bool)
+    fx = np.where(d == 0, False, tx | ((d == 1) & ~ty))
+    fy = np.where(d == 0, False, ty | ((d == 1) & ~tx))
+    return fx, fy
+
+
 def forward(x, w) -> np.ndarray:
     """Network output p for features x [n, 50] (rounded to BF16 here)."""
     W1, b1, W2, b2, w3, b3 = unpack(w)

@@ -138,3 +138,93 @@ def test_fp32_learned_solution_error(env):
         print(f"{c.name}: FP32+learned density L1 rel err {err:.3e}")
         assert err <= 1e-5
         s.close()
+
+
+def _cell_inputs(O, OS, cfg, Q, w, rows, cols, prims, rho_pad):
+    """Oracle network output, FP64 plain per-direction tests and an
+    'uncertain' mask (output within 0.02 of a band edge, or psi within 1e-4
+    of 1/2, where the FP32 / BF16 path may decide the other way)."""
+    p = OS.forward(OS.features_at(cfg, Q, rows, cols, prims), w)
+    g = O.G
+    psx = np.array([O.psi(rho_pad[i + g, j + g - 2:j + g + 3]) for i, j in zip(rows, cols)])
+    psy = np.array([O.psi(rho_pad[i + g - 2:i + g + 3, j + g]) for i, j in zip(rows, cols)])
+    unsure = ((np.abs(p - OS.LO) < 0.02) | (np.abs(p - OS.HI) < 0.02) |
+              (np.abs(psx - 0.5) < 1e-4) | (np.abs(psy - 0.5) < 1e-4))
+    return p, psx < 0.5, psy < 0.5, unsure
+
+
+def _check_learned_flags(env, c, Q, nface=None, rng=None):
+    """Face flags of the fused FP32 + learned-sensor stage against the
+    decision rule applied to the oracle network and the oracle detector,
+    with the 6-cell buffer of Eq. buffer. Faces whose window touches a ghost
+    cell or an uncertain cell are skipped."""
+    torch, O, OS, gbr = env
+    from paper_2305_00762_gb300 import sensor_train as T
+    w = T.load_weights()
+    cfg = cfg_of(O, c)
+    s = gbr.Solver.for_case(c, precision=32)
+    s.set_state(Q)
+    s.set_sensor(w)
+    s.record_flags(True)
+    s.residual()
+    sx, sy = s.flags()
+    s.close()
+    prims = OS.prims_fp32(cfg, Q)
+    g = O.G
+    Qp = np.zeros((4, c.ny + 2 * g, c.nx + 2 * g))
+    Qp[:, g:g + c.ny, g:g + c.nx] = Q
+    rho_pad = O.fill_ghosts_padded(cfg, Qp)[0]
+    checked = 0
+    for axis in ("x", "y"):
+        n_along = c.nx if axis == "x" else c.ny
+        n_across = c.ny if axis == "x" else c.nx
+        if nface is None:
+            a, f = np.meshgrid(np.arange(n_across), np.arange(3, n_along - 2), indexing="ij")
+            a, f = a.ravel(), f.ravel()
+        else:  # half uniform, half on the interface at 0.8 of the extent
+            a = rng.integers(0, n_across, nface)
+            split = int(0.8 * n_along)
+            f = np.concatenate([rng.integers(3, n_along - 2, nface // 2),
+                                rng.integers(split - 4, split + 5, nface - nface // 2)])
+        off = np.arange(-3, 3)
+        along = (f[:, None] + off[None, :]).ravel()
+        across = np.repeat(a, 6)
+        rows, cols = (across, along) if axis == "x" else (along, across)
+        lin, inv = np.unique(rows * c.nx + cols, return_inverse=True)
+        p, tx, ty, unsure = _cell_inputs(O, OS, cfg, Q, w, lin // c.nx, lin % c.nx, prims, rho_pad)
+        fx, fy = OS.direction_flags(p, tx, ty)
+        flag = (fx if axis == "x" else fy)[inv].reshape(-1, 6)
+        smooth = ~flag.any(axis=1)
+        keep = ~unsure[inv].reshape(-1, 6).any(axis=1)
+        got = sx[a, f] if axis == "x" else sy[f, a]
+        assert np.array_equal(got[keep].astype(bool), smooth[keep]), axis
+        assert keep.mean() > 0.9
+        checked += int(keep.sum())
+        assert (~smooth[keep]).sum() > 10  # the check sees discontinuity faces
+    return checked
+
+
+def test_learned_flags_follow_the_decision_rule(env):
+    torch, O, OS, gbr = env
+    import os
+    from paper_2305_00762_gb300 import sensor_train as T
+    if not os.path.exists(T.DEFAULT_WEIGHTS):
+        pytest.skip("no trained sensor weights committed yet")
+    c = C.riemann_2d(160)
+    Q, _, _ = O.run(cfg_of(O, c), c.Q, 0.1, 0.5)   # the oracle's own run: developed fronts
+    n = _check_learned_flags(env, c, Q)
+    print("faces checked", n)
+
+
+def test_learned_flags_full_size_sampled(env):
+    """The 4096^2 Riemann problem in the fused inference's launch
+    configuration, on sampled faces (half of them on the quadrant
+    interfaces)."""
+    torch, O, OS, gbr = env
+    import os
+    from paper_2305_00762_gb300 import sensor_train as T
+    if not os.path.exists(T.DEFAULT_WEIGHTS):
+        pytest.skip("no trained sensor weights committed yet")
+    c = C.riemann_2d(4096)
+    n = _check_learned_flags(env, c, c.Q, nface=3000, rng=np.random.default_rng(41))
+    print("faces checked", n)

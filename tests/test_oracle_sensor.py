@@ -95,3 +95,23 @@ def test_psi_min_at_a_step_and_flat(oracle_mod, OS):
     t = OS.soft_target(np.array([0.0, 0.5 - 0.8 * OS.TAU, 0.5, 0.5 + 0.8 * OS.TAU, 1.0]))
     assert t[0] == 255 and t[-1] == 0 and t[2] == 128
     assert 0.3 * 255 < t[3] < t[2] < t[1] < 0.7 * 255 + 1
+
+
+def test_features_at_equals_features(oracle_mod, OS):
+    O = oracle_mod
+    c = C.kelvin_helmholtz(24, np.random.default_rng(2), ny=20)
+    cfg = O.Config(c.nx, c.ny, c.dx, c.dy, c.gamma, c.mu, c.Pr, c.bc)
+    full = OS.features(cfg, c.Q).reshape(c.ny, c.nx, 50)
+    rng = np.random.default_rng(3)
+    rows, cols = rng.integers(0, c.ny, 40), rng.integers(0, c.nx, 40)
+    assert np.array_equal(OS.features_at(cfg, c.Q, rows, cols), full[rows, cols])
+
+
+def test_direction_flags_rule(OS):
+    """Decision table of the learned sensor's per-direction flags."""
+    p = np.array([0.1, 0.1, 0.5, 0.5, 0.5, 0.9, 0.9, 0.9, 0.9])
+    tx = np.array([1, 0, 1, 0, 0, 1, 0, 0, 1], bool)
+    ty = np.array([1, 0, 0, 1, 0, 0, 1, 0, 1], bool)
+    fx, fy = OS.direction_flags(p, tx, ty)
+    assert list(fx) == [0, 0, 1, 0, 0, 1, 0, 1, 1]
+    assert list(fy) == [0, 0, 0, 1, 0, 0, 1, 1, 1]
