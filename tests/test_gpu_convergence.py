@@ -58,3 +58,36 @@ def test_vortex_100_stages(env):
     orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     print("density L1 errors", errs, "orders", orders)
     assert orders[0] > 6.5 and orders[1] > 3.0
+
+
+def test_vortex_evolution_seventh_order(env):
+    """The same vortex to t = 2 on the CUDA path with n_N = ceil(72 (N/32)^(7/3))
+    steps at 64^2, 128^2 and 256^2 (the RK3 error shrinks like dx^7): density
+    error order >= 6.5 over the range, and the 64^2 run equal to the oracle's
+    (363 steps) within 1e-10."""
+    import math
+    torch, O, gbr = env
+    errs = []
+    for n in (64, 128, 256):
+        c = C.isentropic_vortex(n)
+        steps = math.ceil(72 * (n / 32) ** (7 / 3))
+        s = gbr.Solver.for_case(c)
+        s.set_state(c.Q)
+        for _ in range(steps):
+            s.step(2.0 / steps)
+        Q = s.get_state()
+        s.close()
+        if n == 64:
+            cfg = O.Config(c.nx, c.ny, c.dx, c.dy, c.gamma, c.mu, c.Pr, c.bc)
+            Qo = c.Q.copy()
+            for _ in range(steps):
+                Qo, rc = O.rk3_step(cfg, Qo, 2.0 / steps)
+            scale = np.abs(Qo).reshape(4, -1).max(axis=1)
+            scale[1:3] = scale[1:3].max()
+            assert (np.abs(Q - Qo).reshape(4, -1).max(axis=1) / scale).max() < 1e-10
+        xc, _ = C.centres(n, 0.0, 10.0)
+        X, Y = np.meshgrid(xc, xc)
+        errs.append(np.abs(Q[0] - C.vortex_prims(X, Y, 2.0)[0]).mean())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    print("density L1 errors", errs, "orders", orders)
+    assert orders.min() >= 6.5, orders

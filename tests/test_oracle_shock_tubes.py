@@ -1,6 +1,8 @@
 """Example 2: the Sod and Lax shock tubes (N = 200, t = 0.2 and 0.14) against
-the exact Riemann solution: small density L1 error that falls with N, no
-oscillation beyond a few percent of the jump, MEG7-prim and MEG7-cons."""
+the exact Riemann solution: small density L1 error that falls with N, over-
+and undershoots within 1% of the exact solution's density range (Lax's
+initial density jump, 0.055, is far smaller than that range, 0.96, so the
+bound is taken on the range), MEG7-prim and MEG7-cons."""
 import numpy as np
 import pytest
 
@@ -31,8 +33,8 @@ def test_shock_tube_vs_exact(oracle_mod, which, cons):
         errs.append(np.abs(rho[0] - ex[0]).mean())
         if n == 200:
             span = ex[0].max() - ex[0].min()     # density range of the exact solution
-            assert rho[0].max() <= ex[0].max() + 0.03 * span
-            assert rho[0].min() >= ex[0].min() - 0.03 * span
+            assert rho[0].max() <= ex[0].max() + 0.01 * span
+            assert rho[0].min() >= ex[0].min() - 0.01 * span
     assert errs[0] < (0.006 if which == "sod" else 0.02), errs
     assert errs[1] < 0.75 * errs[0], errs
 

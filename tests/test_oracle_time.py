@@ -82,3 +82,27 @@ def test_nonphysical_state_is_reported(oracle_mod):
     Q[3, 5, 5] = 0.5 * (Q[1, 5, 5] ** 2 + Q[2, 5, 5] ** 2) / Q[0, 5, 5] - 0.1
     _, rc = O.rk3_step(cfg_of(O, c), Q, 1e-4)
     assert rc == O.ERR_NONPHYSICAL
+
+
+def test_vortex_evolution_seventh_order(oracle_mod):
+    """Isentropic vortex to t = 2 with N-dependent step counts
+    n_N = ceil(72 (N/32)^(7/3)), so that the RK3 error (dt^3) shrinks like
+    dx^7 and the spatial order shows in the evolved solution: the density
+    error falls at order >= 6.5 from 64^2 to 128^2 (8.1 from 32^2 to 64^2,
+    6.85 from 64^2 to 128^2 measured)."""
+    import math
+    O = oracle_mod
+    errs = []
+    for n in (32, 64, 128):
+        c = C.isentropic_vortex(n)
+        cfg = O.Config(c.nx, c.ny, c.dx, c.dy, c.gamma, c.mu, c.Pr, c.bc)
+        steps = math.ceil(72 * (n / 32) ** (7 / 3))
+        Q = c.Q.copy()
+        for _ in range(steps):
+            Q, rc = O.rk3_step(cfg, Q, 2.0 / steps)
+            assert rc == 0
+        xc, _ = C.centres(n, 0.0, 10.0)
+        X, Y = np.meshgrid(xc, xc)
+        errs.append(np.abs(Q[0] - C.vortex_prims(X, Y, 2.0)[0]).mean())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert orders[0] > 7.0 and orders[1] >= 6.5, orders
