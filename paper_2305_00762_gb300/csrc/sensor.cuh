@@ -111,9 +111,30 @@ __device__ __forceinline__ void sensor_warp16(const SensorDev& W, CellPtrs cells
     const float *rl, *pl, *rh, *ph;
     cells(g, rl, pl);
     cells(g + 8, rh, ph);
-    float srl, spl, srh, sph;
-    sensor_scales(rl, pl, st, srl, spl);
-    sensor_scales(rh, ph, st, srh, sph);
+    // Normalisation denominators: the four lanes of a quad hold the same two
+    // cells; each takes every fourth neighbour and the quad combines the
+    // maxima (a maximum does not depend on the order).
+    float mrl = 0.f, mpl = 0.f, mrh = 0.f, mph = 0.f;
+    {
+        const float rcl = rl[0], pcl = pl[0], rch = rh[0], pch = ph[0];
+#pragma unroll
+        for (int k = t; k < 25; k += 4) {
+            const int o = (k / 5 - 2) * st + (k % 5 - 2);
+            mrl = fmaxf(mrl, fabsf(rl[o] - rcl));
+            mpl = fmaxf(mpl, fabsf(pl[o] - pcl));
+            mrh = fmaxf(mrh, fabsf(rh[o] - rch));
+            mph = fmaxf(mph, fabsf(ph[o] - pch));
+        }
+#pragma unroll
+        for (int m = 1; m <= 2; m <<= 1) {
+            mrl = fmaxf(mrl, __shfl_xor_sync(0xffffffffu, mrl, m));
+            mpl = fmaxf(mpl, __shfl_xor_sync(0xffffffffu, mpl, m));
+            mrh = fmaxf(mrh, __shfl_xor_sync(0xffffffffu, mrh, m));
+            mph = fmaxf(mph, __shfl_xor_sync(0xffffffffu, mph, m));
+        }
+    }
+    const float srl = 1.f / (mrl + kSensorFloor), spl = 1.f / (mpl + kSensorFloor);
+    const float srh = 1.f / (mrh + kSensorFloor), sph = 1.f / (mph + kSensorFloor);
     // layer 1: [16 x 64] x [64 x 32]
     float acc1[4][4];
 #pragma unroll
