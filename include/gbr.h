@@ -25,10 +25,11 @@
  *
  * Errors. Every call returns int: GBR_OK (0) or a negative gbr_status. No
  * call aborts, traps or prints. Errors raised asynchronously on the device
- * (a non-physical state) are reported by the next synchronising call
- * (gbr_max_wavespeed, gbr_get_state with a host buffer, gbr_sync). Calls with
- * a NULL context or out-of-range arguments return GBR_ERR_ARG and change
- * nothing.
+ * (a non-physical state; a tile-staging wait that gave up, GBR_ERR_TIMEOUT)
+ * are reported by the next synchronising call (gbr_max_wavespeed,
+ * gbr_get_state with a host buffer, gbr_sync) and stay set until
+ * gbr_set_state. Calls with a NULL context or out-of-range arguments return
+ * GBR_ERR_ARG and change nothing.
  *
  * Streams. All work is issued on the context's stream (the legacy default
  * stream until gbr_set_stream). Host-buffer transfers synchronise that stream.
@@ -149,7 +150,8 @@ int gbr_get_state(gbr_ctx *ctx, double *Q, int on_device);
 /* Res(Q) of the current state, Eqs. eqn-differencing_residual and deriv:
  * Res = -(F_{j+1/2} - F_{j-1/2})/dx - (G_{i+1/2} - G_{i-1/2})/dy with the
  * MEG7 convective flux (Secs. 2.2-2.4) and the alpha-damping viscous flux
- * (Sec. 2.1). res: [4][ny][nx] float64. */
+ * (Sec. 2.1). res: [4][ny][nx] float64. With a host buffer the call
+ * synchronises and reports GBR_ERR_TIMEOUT if the tile staging gave up. */
 int gbr_residual(gbr_ctx *ctx, double *res, int on_device);
 
 /* One third-order TVD Runge-Kutta step of size dt > 0 (Sec. 2.5, Eq. rk):
