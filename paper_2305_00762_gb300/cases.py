@@ -112,7 +112,6 @@ def riemann_2d(n, ny=None, t_end=0.3, cfl=0.5, split=(0.8, 0.8)):
     ny = n if ny is None else ny
     xc, dx = centres(n, 0.0, 1.0)
     yc, dy = centres(ny, 0.0, 1.0)
-    X, Y = np.meshgrid(xc, yc)
     s11 = 4.0 / np.sqrt(11.0)
     states = {  # (rho, u, v, p) as printed in Example 9
         "ur": (1.5, 0.0, 0.0, 1.5),
@@ -120,13 +119,11 @@ def riemann_2d(n, ny=None, t_end=0.3, cfl=0.5, split=(0.8, 0.8)):
         "ll": (77.0 / 558.0, s11, s11, 9.0 / 310.0),
         "lr": (33.0 / 62.0, 0.0, s11, 0.3),
     }
-    right = X > split[0]
-    top = Y > split[1]
-    prim = np.zeros((4, ny, n))
-    for key, mask in (("ur", right & top), ("ul", ~right & top),
-                      ("ll", ~right & ~top), ("lr", right & ~top)):
-        for m in range(4):
-            prim[m][mask] = states[key][m]
+    # quadrant index 2*top + right: 0 = lower left, 1 = lower right,
+    # 2 = upper left, 3 = upper right
+    quad = (2 * (yc > split[1])[:, None] + (xc > split[0])[None, :]).astype(np.int8)
+    table = np.array([states["ll"], states["lr"], states["ul"], states["ur"]]).T  # [4 fields][4 quadrants]
+    prim = np.stack([table[m][quad] for m in range(4)])
     Q = prim_to_cons(*prim, 1.4)
     return Case("riemann_2d", np.ascontiguousarray(Q), dx, dy, 1.4, 0.0, 0.72,
                 (BC_TRANSMISSIVE,) * 4, t_end, cfl, {"split": split})

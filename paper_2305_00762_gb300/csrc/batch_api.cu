@@ -34,6 +34,8 @@ struct gbr_batch {
     int timing;
     SensorDev* d_sensor;      // learned-sensor weights (null until set)
     int sensor;               // 1: use them (FP32 only)
+    unsigned char* dec_pool;  // the cases' learned-sensor decisions (padded layouts)
+    int total_dtiles;         // sensor-pass tiles of all cases
 };
 
 namespace {
@@ -96,10 +98,14 @@ int upload(gbr_batch* b)
 
 const SensorDev* sensor_of(gbr_batch* b) { return (b->precision == 32 && b->sensor) ? b->d_sensor : nullptr; }
 
+// Stage k of every running case; with the learned sensor, its decision pass
+// over the stage's input state first.
 int stage(gbr_batch* b, int k, cudaStream_t s)
 {
+    const SensorDev* w = sensor_of(b);
+    if (w) TRY(launch_batch_sensor_decide(b->d_cases, b->n, b->total_dtiles, k, w, s));
     cudaError_t e = b->precision == 32
-                        ? launch_batch_stage_f32(b->shape, b->d_cases, b->n, b->total_tiles, k, s, sensor_of(b))
+                        ? launch_batch_stage_f32(b->shape, b->d_cases, b->n, b->total_tiles, k, s, w)
                         : launch_batch_stage_f64(b->shape, b->d_cases, b->n, b->total_tiles, k, s);
     return st(e);
 }
@@ -157,6 +163,7 @@ int gbr_batch_create(int n, const int* nx, const int* ny, const double* dx, cons
     b->cases.resize(n);
     int rc = st(cudaGetDevice(&b->device));
     long long total = 0, ghosts = 0;
+    int dtiles = 0;
     for (int k = 0; k < n && rc == GBR_OK; ++k) {
         BatchCase& c = b->cases[k];
         memset(&c, 0, sizeof(c));
@@ -174,9 +181,15 @@ int gbr_batch_create(int n, const int* nx, const int* ny, const double* dx, cons
         c.t_end = 1e300;
         c.ghost_begin = ghosts;
         ghosts += ghost_count(c.g);
+        int dtx = 0, dt = 0;
+        sensor_decide_tiles(c.g, &dtx, &dt);
+        c.dtiles_x = dtx;
+        c.dtile_begin = dtiles;
+        dtiles += dt;
         total += 12 * c.g.plane;  // 3 states x 4 planes
     }
     b->total_ghosts = ghosts;
+    b->total_dtiles = dtiles;
     if (rc == GBR_OK) rc = st(cudaMalloc(&b->pool, sizeof(double) * (size_t)total));
     if (rc == GBR_OK) rc = st(cudaMemset(b->pool, 0, sizeof(double) * (size_t)total));
     if (rc == GBR_OK) rc = st(cudaMalloc(&b->d_scal, sizeof(DevScalars) * n));
@@ -215,6 +228,7 @@ int gbr_batch_destroy(gbr_batch* b)
     cudaFree(b->d_scal);
     cudaFree(b->d_cases);
     cudaFree(b->d_sensor);
+    cudaFree(b->dec_pool);
     cudaGetLastError();
     delete b;
     return GBR_OK;
@@ -306,6 +320,7 @@ int gbr_batch_step_cfl(gbr_batch* b, double cfl, int nsteps)
         // prepares the persistent kernel without launching it)
         TRY(b->precision == 32 ? launch_batch_stage_f32(b->shape, b->d_cases, b->n, -1, 0, b->stream, sensor_of(b))
                                : launch_batch_stage_f64(b->shape, b->d_cases, b->n, -1, 0, b->stream));
+        if (sensor_of(b)) TRY(launch_batch_sensor_decide(b->d_cases, b->n, -1, 0, sensor_of(b), b->stream));
         // The descriptors must be on the device before the capture stream
         // replays anything: order the capture stream after the caller's.
         TRY(cudaStreamSynchronize(b->stream));
@@ -412,6 +427,20 @@ int gbr_batch_set_sensor_weights(gbr_batch* b, const float* w, int n)
     SensorDev h;
     pack_sensor(w, &h);
     if (!b->d_sensor) TRY(cudaMalloc(&b->d_sensor, sizeof(SensorDev)));
+    if (!b->dec_pool) {
+        size_t bytes = 0;
+        for (const auto& c : b->cases) bytes += (size_t)c.g.pitch * (c.g.ny + 2 * kGhost);
+        TRY(cudaMalloc(&b->dec_pool, bytes));
+        TRY(cudaMemsetAsync(b->dec_pool, 2, bytes, b->stream));  // "unsure" outside the written regions
+        size_t off = 0;
+        for (auto& c : b->cases) {
+            c.dec = b->dec_pool + off;
+            off += (size_t)c.g.pitch * (c.g.ny + 2 * kGhost);
+        }
+        b->dirty = true;
+        const int rc = upload(b);
+        if (rc != GBR_OK) return rc;
+    }
     TRY(cudaMemcpyAsync(b->d_sensor, &h, sizeof(SensorDev), cudaMemcpyHostToDevice, b->stream));
     TRY(cudaStreamSynchronize(b->stream));
     return GBR_OK;

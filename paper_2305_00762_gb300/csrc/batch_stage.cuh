@@ -49,6 +49,8 @@ __global__ void __launch_bounds__(NT) batch_stage_kernel(const BatchCase* __rest
         P.cb = cbc;
         P.cc = cbc;
         P.sensor = sensor;
+        P.dec = C.dec;
+        P.stall_bytes = 0;
         stage_tile<T, BX, BY, NT, false, LEARNED>(P, tx * BX, ty * BY, smem_raw);
     }
 }

@@ -41,7 +41,8 @@ struct gbr_ctx {
     int stall_test;  // GBR_OPT_STALL_TEST
     // learned sensor
     SensorDev* d_sensor;
-    float* prob;   // per-cell sensor output scratch
+    float* prob;          // per-cell sensor output scratch
+    unsigned char* dec;   // learned-sensor decisions of the stage input (padded layout)
 };
 
 namespace {
@@ -171,7 +172,14 @@ StageParams stage_params(gbr_ctx* c, const double* q)
 
 int stage(gbr_ctx* c, const StageParams& p)
 {
-    Timed tm(c, GBR_KERNEL_STAGE);
+    Timed tm(c, GBR_KERNEL_STAGE);  // includes the learned sensor's decision pass
+    if (c->precision == 32 && p.sensor) {
+        StageParams q = p;
+        q.dec = c->dec;
+        cudaError_t e = launch_sensor_decide(c->g, c->ph.gamma, p.q, p.sensor, c->dec, c->stream);
+        if (e == cudaSuccess) e = launch_stage_f32(q, c->stream);
+        return cuda_status(e);
+    }
     cudaError_t e = (c->precision == 32) ? launch_stage_f32(p, c->stream) : launch_stage_f64(p, c->stream);
     return cuda_status(e);
 }
@@ -279,6 +287,7 @@ int gbr_destroy(gbr_ctx* c)
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     cudaFree(c->d_sensor);
     cudaFree(c->prob);
+    cudaFree(c->dec);
     cudaGetLastError();
     delete c;
     return GBR_OK;
@@ -474,6 +483,11 @@ int gbr_set_sensor_weights(gbr_ctx* c, const float* w, int n)
     SensorDev h;
     pack_sensor(w, &h);
     if (!c->d_sensor) GBR_TRY(cudaMalloc(&c->d_sensor, sizeof(SensorDev)));
+    if (!c->dec) {
+        const size_t bytes = (size_t)c->g.pitch * (c->g.ny + 2 * kGhost);
+        GBR_TRY(cudaMalloc(&c->dec, bytes));
+        GBR_TRY(cudaMemsetAsync(c->dec, 2, bytes, c->stream));  // "unsure" outside the written region
+    }
     GBR_TRY(cudaMemcpyAsync(c->d_sensor, &h, sizeof(SensorDev), cudaMemcpyHostToDevice, c->stream));
     GBR_TRY(cudaStreamSynchronize(c->stream));
     return GBR_OK;

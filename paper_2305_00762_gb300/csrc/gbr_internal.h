@@ -51,6 +51,7 @@ struct StageParams {
     double dt;               // host dt otherwise
     double ca, cb, cc;       // qout = ca * qn + cb * q + cc * dt * Res
     const SensorDev* sensor; // learned-sensor weights (FP32 form) or nullptr
+    const unsigned char* dec;  // learned-sensor decisions of padded cells [3, n+9) (pitch g.pitch), with sensor
     unsigned stall_bytes;    // failure-detection test hook: extra bytes the tile staging waits for (0)
 };
 
@@ -75,6 +76,8 @@ struct BatchCase {
     Physics ph;
     int bc[4];
     double* q[3];        // Q^n, Q^(1), Q^(2) (padded)
+    unsigned char* dec;  // learned-sensor decisions (padded layout) or nullptr
+    int dtiles_x, dtile_begin;  // sensor-pass tiles of this case: per row, first batch tile
     DevScalars* ds;      // lam[0] = wavespeed of Q^n, dt, t, err
     double t_end;        // the case stops (dt = 0) once t reaches t_end
     int tiles_x, tiles;  // tiles of this case for the current tile shape
@@ -111,6 +114,17 @@ cudaError_t encode_state_map(const Grid& g, const double* q, int box_w, int box_
 
 cudaError_t launch_sensor_tile(const Grid& g, double gamma, const double* q, const SensorDev* w, float* prob,
                                void* feat_bf16, unsigned char* label, unsigned char* target, cudaStream_t s);
+// The learned sensor's decision pass of one padded state (ghosts filled):
+// dec[y * pitch + x] for padded cells x in [3, nx + 9), y in [3, ny + 9):
+// 1 = discontinuity (p > 0.7), 0 = smooth (p < 0.3), 2 = unsure.
+cudaError_t launch_sensor_decide(const Grid& g, double gamma, const double* q, const SensorDev* w,
+                                 unsigned char* dec, cudaStream_t s);
+// Sensor-pass tiles of a grid (the tile grid over its decision region).
+void sensor_decide_tiles(const Grid& g, int* tiles_x, int* tiles);
+// The decision pass of buffer `buf` of every running case of a batch
+// (persistent; total_tiles = sum of the cases' sensor-pass tiles).
+cudaError_t launch_batch_sensor_decide(const BatchCase* cases, int ncases, int total_tiles, int buf,
+                                       const SensorDev* w, cudaStream_t s);
 cudaError_t launch_sensor_train(const void* X_bf16, const unsigned char* y, long long n, int steps, int batch,
                                 float lr, float pos_weight, unsigned long long seed, float* w, float* grad, float* m,
                                 float* v, float* loss, cudaStream_t s);

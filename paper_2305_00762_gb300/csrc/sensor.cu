@@ -36,60 +36,78 @@ void pack_sensor(const float* w, SensorDev* out)
 }
 
 // ---------------------------------------------------------------------------
-// Per-cell sensor output, features and plain labels of a padded state.
+// Per-cell sensor output, decisions, features and plain labels of a padded
+// state. A tile covers kTX x kTY cells of one of two index spaces: the
+// interior cells (origin = padded cell kGhost, extent nx x ny), or the
+// decision region (origin = padded cell 3, extent (nx + 6) x (ny + 6): every
+// cell whose detector flag a stage tile reads).
 // ---------------------------------------------------------------------------
 constexpr int kTX = 32, kTY = 16, kH = 2, kRW = kTX + 2 * kH, kRH = kTY + 2 * kH;
+constexpr int kDecOrigin = 3;
 
 struct SensorTileParams {
     Grid g;
     double gamma;
     const double* q;        // padded state, ghosts filled
-    const SensorDev* w;     // weights (eval) or nullptr
+    const SensorDev* w;     // weights (eval, decisions) or nullptr
     float* prob;            // [ny][nx] network output, or nullptr
     __nv_bfloat16* feat;    // [ny*nx][64] features, or nullptr
     unsigned char* label;   // [ny*nx] plain-detector label, or nullptr
     unsigned char* target;  // [ny*nx] soft target in units of 1/255, or nullptr
+    unsigned char* dec;     // decision-region mode: decisions (padded layout), else nullptr
 };
 
-__global__ void __launch_bounds__(256) sensor_tile_kernel(const SensorTileParams P)
+struct SensorTileSmem {
+    float sr[kRH * kRW], sp[kRH * kRW];
+    SensorDev w;
+};
+
+__device__ void sensor_tile(const SensorTileParams& P, const int tx0, const int ty0, SensorTileSmem& S)
 {
-    __shared__ float sr[kRH * kRW], sp[kRH * kRW];
-    __shared__ SensorDev sw;
-    const int tx0 = blockIdx.x * kTX, ty0 = blockIdx.y * kTY;
+    const bool decide = P.dec != nullptr;
+    const int org = decide ? kDecOrigin : kGhost;  // padded index of the space's cell 0
+    const int ni = decide ? P.g.ny + 2 * kDecOrigin : P.g.ny;
+    const int nj = decide ? P.g.nx + 2 * kDecOrigin : P.g.nx;
     const int nx = P.g.nx, ny = P.g.ny;
     const float gm1 = (float)(P.gamma - 1.0);
-    // stage the region as FP32 primitives exactly as the FP32 stage kernel does
+    // stage the region as FP32 primitives exactly as the FP32 stage kernel
+    // does (clamped to the padded extent; clamped cells feed no output)
     for (int idx = threadIdx.x; idx < kRH * kRW; idx += blockDim.x) {
         const int ry = idx / kRW, rx = idx - ry * kRW;
-        const int gx = min(tx0 + rx + kGhost - kH, nx + 2 * kGhost - 1);
-        const int gy = min(ty0 + ry + kGhost - kH, ny + 2 * kGhost - 1);
+        const int gx = min(tx0 + rx + org - kH, nx + 2 * kGhost - 1);
+        const int gy = min(ty0 + ry + org - kH, ny + 2 * kGhost - 1);
         const long long o = (long long)gy * P.g.pitch + gx;
-        const float r = (float)P.q[o], ir = 1.f / r;
-        const float u = (float)P.q[o + P.g.plane] * ir, v = (float)P.q[o + 2 * P.g.plane] * ir;
-        sr[idx] = r;
-        sp[idx] = gm1 * ((float)P.q[o + 3 * P.g.plane] - 0.5f * r * (u * u + v * v));
+        float r, u, v, pr;
+        prims_of(P.q[o], P.q[o + P.g.plane], P.q[o + 2 * P.g.plane], P.q[o + 3 * P.g.plane], gm1, r, u, v, pr);
+        S.sr[idx] = r;
+        S.sp[idx] = pr;
     }
-    if (P.w) load_sensor(&sw, P.w);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     for (int chunk = warp; chunk < kTX * kTY / 16; chunk += blockDim.x >> 5) {
         auto cells = [&](int i, const float*& r, const float*& p) {
             const int c = chunk * 16 + i, cy = c / kTX, cx = c - cy * kTX;
-            r = sr + (cy + kH) * kRW + (cx + kH);
-            p = sp + (cy + kH) * kRW + (cx + kH);
+            r = S.sr + (cy + kH) * kRW + (cx + kH);
+            p = S.sp + (cy + kH) * kRW + (cx + kH);
         };
-        if (P.prob) {
+        if (P.prob || decide) {
             float plo, phi;
-            sensor_warp16(sw, cells, kRW, plo, phi);
+            sensor_warp16(S.w, cells, kRW, plo, phi);
             if (t == 0) {
                 for (int h = 0; h < 2; ++h) {
                     const int c = chunk * 16 + g + 8 * h, cy = c / kTX, cx = c - cy * kTX;
                     const int i = ty0 + cy, j = tx0 + cx;
-                    if (i < ny && j < nx) P.prob[(long long)i * nx + j] = h ? phi : plo;
+                    if (i >= ni || j >= nj) continue;
+                    const float pv = h ? phi : plo;
+                    if (decide)
+                        P.dec[(long long)(i + org) * P.g.pitch + (j + org)] =
+                            pv > kSensorHi ? 1 : (pv < kSensorLo ? 0 : 2);
+                    else
+                        P.prob[(long long)i * nx + j] = pv;
                 }
             }
         }
-        if (P.feat) {  // one cell per lane pair: lanes 0..15 write 64 features each
+        if (P.feat) {  // one cell per lane: lanes 0..15 write 64 features each
             if (lane < 16) {
                 const int c = chunk * 16 + lane, cy = c / kTX, cx = c - cy * kTX;
                 const int i = ty0 + cy, j = tx0 + cx;
@@ -118,28 +136,113 @@ __global__ void __launch_bounds__(256) sensor_tile_kernel(const SensorTileParams
             }
             if (P.target) {
                 const double psi = fmin(detector_psi(r, 1), detector_psi(r, P.g.pitch));
-                const double t = 1.0 / (1.0 + exp((psi - 0.5) / kSensorTau));
-                P.target[(long long)i * nx + j] = (unsigned char)floor(255.0 * t + 0.5);
+                const double tt = 1.0 / (1.0 + exp((psi - 0.5) / kSensorTau));
+                P.target[(long long)i * nx + j] = (unsigned char)floor(255.0 * tt + 0.5);
             }
         }
     }
 }
 
+__global__ void __launch_bounds__(256) sensor_tile_kernel(const SensorTileParams P)
+{
+    __shared__ SensorTileSmem S;
+    if (P.w) load_sensor(&S.w, P.w);
+    sensor_tile(P, blockIdx.x * kTX, blockIdx.y * kTY, S);
+}
+
 cudaError_t launch_sensor_tile(const Grid& g, double gamma, const double* q, const SensorDev* w, float* prob,
                                void* feat_bf16, unsigned char* label, unsigned char* target, cudaStream_t s)
 {
-    __nv_bfloat16* feat = static_cast<__nv_bfloat16*>(feat_bf16);
     SensorTileParams P;
     P.g = g;
     P.gamma = gamma;
     P.q = q;
     P.w = w;
     P.prob = prob;
-    P.feat = feat;
+    P.feat = static_cast<__nv_bfloat16*>(feat_bf16);
     P.label = label;
     P.target = target;
+    P.dec = nullptr;
     dim3 grid((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY);
     sensor_tile_kernel<<<grid, 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+void sensor_decide_tiles(const Grid& g, int* tiles_x, int* tiles)
+{
+    const int tx = (g.nx + 2 * kDecOrigin + kTX - 1) / kTX, ty = (g.ny + 2 * kDecOrigin + kTY - 1) / kTY;
+    *tiles_x = tx;
+    *tiles = tx * ty;
+}
+
+cudaError_t launch_sensor_decide(const Grid& g, double gamma, const double* q, const SensorDev* w,
+                                 unsigned char* dec, cudaStream_t s)
+{
+    if (!w || !dec) return cudaErrorInvalidValue;
+    SensorTileParams P;
+    P.g = g;
+    P.gamma = gamma;
+    P.q = q;
+    P.w = w;
+    P.prob = nullptr;
+    P.feat = nullptr;
+    P.label = nullptr;
+    P.target = nullptr;
+    P.dec = dec;
+    int tx, tiles;
+    sensor_decide_tiles(g, &tx, &tiles);
+    dim3 grid(tx, tiles / tx);
+    sensor_tile_kernel<<<grid, 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+// Persistent decision pass over every running case of a batch: CTA k takes
+// sensor-pass tiles k, k + gridDim.x, ... of the concatenated tile list.
+__global__ void __launch_bounds__(256) batch_sensor_decide_kernel(const BatchCase* __restrict__ cases, int ncases,
+                                                                  int total_tiles, int buf, const SensorDev* w)
+{
+    __shared__ SensorTileSmem S;
+    load_sensor(&S.w, w);
+    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+        int lo = 0, hi = ncases - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cases[mid].dtile_begin <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchCase& C = cases[lo];
+        if (C.ds->dt == 0.0) continue;  // stopped case; uniform over the CTA
+        const int local = tile - C.dtile_begin;
+        const int ty = local / C.dtiles_x, tx = local - ty * C.dtiles_x;
+        SensorTileParams P;
+        P.g = C.g;
+        P.gamma = C.ph.gamma;
+        P.q = C.q[buf];
+        P.w = w;
+        P.prob = nullptr;
+        P.feat = nullptr;
+        P.label = nullptr;
+        P.target = nullptr;
+        P.dec = C.dec;
+        __syncthreads();  // the previous tile's readers of S are done
+        sensor_tile(P, tx * kTX, ty * kTY, S);
+    }
+}
+
+cudaError_t launch_batch_sensor_decide(const BatchCase* cases, int ncases, int total_tiles, int buf,
+                                       const SensorDev* w, cudaStream_t s)
+{
+    static int blocks = 0;
+    if (blocks == 0) {
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sensor_decide_kernel, 256, 0);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        blocks = (per_sm > 0 ? per_sm : 1) * sms;
+    }
+    if (total_tiles < 0) return cudaSuccess;  // prepare only
+    batch_sensor_decide_kernel<<<blocks, 256, 0, s>>>(cases, ncases, total_tiles, buf, w);
     return cudaGetLastError();
 }
 

@@ -54,19 +54,17 @@ struct TileLayout {
     static constexpr int oEnd = oQc + (CONS ? 4 * NU : 0);
 
     // learned sensor: per-cell decisions on the bounding box of both
-    // detector regions, rows and columns [3, B+9), and the weights
+    // detector regions, rows and columns [3, B+9)
     static constexpr int BOXW = BX + 6, BOXH = BY + 6, NBOX = BOXW * BOXH;
 
     template <typename T, int NT>
     static constexpr int nT() { return oEnd; }  // elements of T
     template <typename T, int NT>
     static constexpr size_t bytes() { return sizeof(T) * (size_t)nT<T, NT>() + (size_t)(NPX + NPY) + 16; }
-    template <typename T, int NT>
-    static constexpr size_t sensor_offset() { return (bytes<T, NT>() + NBOX + 15) / 16 * 16; }
     template <typename T, int NT, bool LEARNED>
     static constexpr size_t total_bytes()
     {
-        return LEARNED ? sensor_offset<T, NT>() + sizeof(SensorDev) : bytes<T, NT>();
+        return LEARNED ? (bytes<T, NT>() + NBOX + 15) / 16 * 16 : bytes<T, NT>();
     }
 
     // TMA staging: the FP64 conservative tile + halo lands as [4][RH][RW]
@@ -157,6 +155,19 @@ __device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf
 // a^2 + b^2, symmetric in a and b to the last bit.
 template <typename T>
 __device__ __forceinline__ T sumsq(T a, T b) { return rmul(a, a) + rmul(b, b); }
+
+// Eq. pressure: primitives (rho, u, v, p) of a conservative state, in T,
+// rounded alike wherever it is inlined (the stage kernels' staging and the
+// learned sensor's).
+template <typename T>
+__device__ __forceinline__ void prims_of(double q0, double q1, double q2, double q3, T gm1, T& r, T& u, T& v, T& p)
+{
+    r = T(q0);
+    const T ir = T(1) / r;
+    u = T(q1) * ir;
+    v = T(q2) * ir;
+    p = gm1 * rfma(-rmul(T(0.5), r), sumsq(u, v), T(q3));
+}
 
 // Eq. six: dx-scaled sixth-order gradient at s[0] along stride st.
 template <typename T>
@@ -721,11 +732,8 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
     // Phase 0: stage the tile + halo as primitive variables (Eq. pressure).
     // Region cell (rx, ry) is padded cell (tx0 + rx, ty0 + ry).
     auto stage_cell = [&](int idx, double q0, double q1, double q2, double q3) {
-        const T r = T(q0);
-        const T ir = T(1) / r;
-        const T u = T(q1) * ir;
-        const T v = T(q2) * ir;
-        const T p = ph.gm1 * (T(q3) - T(0.5) * r * sumsq(u, v));
+        T r, u, v, p;
+        prims_of(q0, q1, q2, q3, ph.gm1, r, u, v, p);
         sU[idx] = r;
         sU[NU + idx] = u;
         sU[2 * NU + idx] = v;
@@ -782,8 +790,20 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
             stage_cell(idx, P.q[o], P.q[o + plane], P.q[o + 2 * plane], P.q[o + 3 * plane]);
         }
     }
-    if constexpr (LEARNED)
-        load_sensor(reinterpret_cast<SensorDev*>(smem_raw + L::template sensor_offset<T, NT>()), P.sensor);
+    if constexpr (LEARNED) {
+        // The learned sensor's per-cell decisions (1 = trouble, 0 = smooth,
+        // 2 = unsure: the plain detector decides below) of the detector's
+        // bounding box, written by the sensor pass for padded cells
+        // [3, n + 9) in each direction; box cell (bx, by) is padded cell
+        // (tx0 + bx + 3, ty0 + by + 3). Cells past that range (ragged last
+        // tiles) only feed results that are never stored.
+        unsigned char* const sT = sPY + L::NPY;
+        for (int c = tid; c < L::NBOX; c += NT) {
+            const int by = c / L::BOXW, bx = c - by * L::BOXW;
+            const int gx = min(tx0 + bx + 3, nx + 8), gy = min(ty0 + by + 3, ny + 8);
+            sT[c] = P.dec[(long long)gy * pitch + gx];
+        }
+    }
     __syncthreads();
 
     // Phase 1: per-cell quantities, each computed once per tile.
@@ -808,28 +828,6 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         for (int idx = tid; idx < L::NPY; idx += NT) {  // y detector
             const int a = idx / BX, b = idx - a * BX;
             sPY[idx] = trouble_cell(sU + (a + 3) * RW + (b + 6), RW) ? 1 : 0;
-        }
-    } else {
-        // Learned sensor on the tensor cores, 16 cells per warp: 1 = trouble,
-        // 0 = smooth, 2 = unsure (the plain detector decides below).
-        unsigned char* const sT = sPY + L::NPY;
-        const SensorDev& W = *reinterpret_cast<const SensorDev*>(smem_raw + L::template sensor_offset<T, NT>());
-        const int nchunks = (L::NBOX + 15) / 16;
-        for (int chunk = tid >> 5; chunk < nchunks; chunk += NT / 32) {
-            auto cells = [&](int i, const float*& r, const float*& p) {
-                const int c = min(chunk * 16 + i, L::NBOX - 1);
-                const int by = c / L::BOXW, bx = c - by * L::BOXW;
-                r = reinterpret_cast<const float*>(sU) + (by + 3) * RW + (bx + 3);
-                p = reinterpret_cast<const float*>(sU) + 3 * NU + (by + 3) * RW + (bx + 3);
-            };
-            float plo, phi;
-            sensor_warp16(W, cells, RW, plo, phi);
-            if ((tid & 3) == 0) {
-                const int g = (tid & 31) >> 2;
-                const int c0 = chunk * 16 + g, c1 = c0 + 8;
-                if (c0 < L::NBOX) sT[c0] = plo > kSensorHi ? 1 : (plo < kSensorLo ? 0 : 2);
-                if (c1 < L::NBOX) sT[c1] = phi > kSensorHi ? 1 : (phi < kSensorLo ? 0 : 2);
-            }
         }
     }
     for (int idx = tid; idx < L::NFX; idx += NT) {  // cell x-fluxes F^c (Sec. 1)

@@ -202,13 +202,20 @@ def _sample_mask(Q, rng, n=4000):
     return m
 
 
-@pytest.mark.parametrize("which", ["riemann4096", "vst2048x1024"])
+FULL = {"riemann4096": lambda: C.riemann_2d(4096),
+        "vst2048x1024": lambda: C.viscous_shock_tube(2048, 1024),
+        "riemann8192x6144": lambda: C.riemann_2d(8192, 6144)}
+
+
+@pytest.mark.parametrize("which", list(FULL))
 def test_full_size_sampled(env, which):
-    """Configs 3 and 4 at full size: the residual at sampled cells (all
-    boundary cells plus random interior ones), computed one by one by the
-    oracle from the same state."""
+    """Configs 3 and 4 at full size, and a 8192 x 6144 grid (50 M cells,
+    padded planes of 50.5 M doubles: index arithmetic far past the benchmark's
+    sizes, ragged in y): the residual at sampled cells (all boundary cells
+    plus random interior ones), computed one by one by the oracle from the
+    same state."""
     torch, O, gbr = env
-    c = C.riemann_2d(4096) if which == "riemann4096" else C.viscous_shock_tube(2048, 1024)
+    c = FULL[which]()
     cfg = cfg_of(O, c)
     s = gbr.Solver.for_case(c)
     s.set_state(c.Q)
