@@ -20,8 +20,10 @@ __device__ __forceinline__ int batch_case_of(const BatchCase* cases, int ncases,
     return lo;
 }
 
+// Register budgets for the CTAs per SM that shared memory allows: three in
+// FP32 (80 registers, the single-grid FP32 kernel's count), two in FP64.
 template <typename T, int BX, int BY, int NT, bool LEARNED>
-__global__ void __launch_bounds__(NT) batch_stage_kernel(const BatchCase* __restrict__ cases, int ncases,
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) batch_stage_kernel(const BatchCase* __restrict__ cases, int ncases,
                                                          int total_tiles, int stage, const SensorDev* sensor)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
