@@ -30,6 +30,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -252,12 +254,46 @@ def run_ensemble(args, torch, gbr, cases, st, sensor_w=None):
     rc = b.sync(allow=(gbr.GBR_ERR_NONPHYSICAL,))
     t, dt = b.times(allow=(gbr.GBR_ERR_NONPHYSICAL,))
     b.close()
+    l1 = ensemble_accuracy(torch, gbr, cases, table, st, sensor_w)
     return {"value": 3.0 * cells * args.steps / (ms * 1e-3), "unit": METRIC, "grids": len(table),
             "cells": cells, "ms_per_step": ms / args.steps, "precision": "fp32",
             "learned_sensor": sensor_w is not None,
             "tile": list(shape), "graph": True, "dt_min": float(dt.min()), "dt_max": float(dt.max()),
             "status": gbr.error_string(rc),
-            "sizes": {str(n): sum(1 for _, m, _ in table if m == n) for n in (256, 512, 1024, 2048)}}
+            "sizes": {str(n): sum(1 for _, m, _ in table if m == n) for n in (256, 512, 1024, 2048)},
+            "density_l1_vs_fp64": l1}
+
+
+def ensemble_accuracy(torch, gbr, cases, table, st, sensor_w, nsteps=20):
+    """Per-case density L1 error of the batched FP32 (+ learned sensor) form
+    against the same batch in FP64, whose steps equal the oracle's to 1e-12
+    relative: the FP64 batch takes nsteps CFL steps, then the FP32 batch runs
+    every case to the time its FP64 twin reached (the last step clipped), so
+    both are compared at equal times."""
+    def batch(precision):
+        ens = [cases.make_ensemble_case(kind, n, prm) for kind, n, prm in table]
+        bb = gbr.Batch(ens, precision=precision, stream=st.cuda_stream)
+        if precision == 32 and sensor_w is not None:
+            bb.set_sensor(sensor_w)
+        for k, c in enumerate(ens):
+            bb.set_state(k, torch.from_numpy(c.Q).cuda())
+        return bb
+    b64 = batch(64)
+    b64.step_cfl(CFL, nsteps)
+    t64, _ = b64.times()
+    b32 = batch(32)
+    b32.set_end_times(t64)
+    b32.step_cfl(CFL, nsteps + 4)
+    t32, _ = b32.times()
+    errs = []
+    for k, (_, n, _) in enumerate(table):
+        r64 = b64.get_state(k)[0]
+        r32 = b32.get_state(k)[0]
+        errs.append(float(np.abs(r32 - r64).sum() / np.abs(r64).sum()))
+    b64.close()
+    b32.close()
+    return {"per_case": errs, "max": max(errs), "median": float(np.median(errs)), "steps": nsteps,
+            "time_mismatch_max": float(np.abs(t32 - t64).max())}
 
 
 def time_steps(torch, solver, steps, flush, profile=False):
