@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--ensemble-cases", type=int, default=64)
+    ap.add_argument("--no-4096", action="store_true", help="skip the 4096^2 FP32 + learned-sensor measurement")
     return ap.parse_args()
 
 
@@ -264,6 +265,36 @@ def run_ensemble(args, torch, gbr, cases, st, sensor_w=None):
             "density_l1_vs_fp64": l1}
 
 
+def run_learned_4096(torch, gbr, cases, st, sensor_w, warmup=20, steps=10):
+    """The learned sensor's inference fused into the FP32 stages on the
+    4096^2 Riemann problem (16.8 M cells, 0.54 GB per state: inputs exceed
+    L2): 10 steps after 20 warm-up steps from the initial data."""
+    c = cases.riemann_2d(4096)
+    s = gbr.Solver.for_case(c, stream=st.cuda_stream, precision=32)
+    s.set_state(torch.from_numpy(c.Q).cuda())
+    s.set_sensor(sensor_w)
+    for _ in range(warmup):
+        s.step_cfl(CFL)
+    s.sync()
+    s.timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        s.step_cfl(CFL)
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    tm, _ = s.get_timing()
+    rc = s.sync(allow=(gbr.GBR_ERR_NONPHYSICAL,))
+    t = s.time()
+    s.close()
+    cells = c.nx * c.ny
+    return {"value": 3.0 * cells * steps / (ms * 1e-3), "unit": METRIC, "ms_per_step": ms / steps,
+            "stage_ms_avg": tm["stage"][0] / max(tm["stage"][1], 1), "t_end": t, "steps": steps,
+            "warmup": warmup, "status": gbr.error_string(rc)}
+
+
 def ensemble_accuracy(torch, gbr, cases, table, st, sensor_w, nsteps=20):
     """Per-case density L1 error of the batched FP32 (+ learned sensor) form
     against the same batch in FP64, whose steps equal the oracle's to 1e-12
@@ -467,6 +498,8 @@ def main():
             "stage_ms_avg": rl["timing"]["stage"][0] / max(rl["timing"]["stage"][1], 1),
             "sensor": "MLP 50-32-32-1, BF16 mma.sync, fallback band [0.3, 0.7]",
             "density_l1_vs_fp64_20_steps": acc.get((32, True)), "clocks": rl["clocks"]}
+    if not args.no_4096 and sensor_w is not None:
+        line["fp32_learned_4096"] = run_learned_4096(torch, gbr, cases, st, sensor_w)
     if not args.no_ensemble:
         line["ensemble"] = run_ensemble(args, torch, gbr, cases, st, sensor_w)
     if not args.no_cpu_baseline:

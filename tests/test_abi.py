@@ -50,3 +50,34 @@ def test_bad_arguments_rejected_without_device(lib):
     assert lib.gbr_create(64, 64, 1.4, 0.0, 0.72, ctypes.byref(neg), ctypes.byref(out)) == gbr.GBR_ERR_ARG
     assert lib.gbr_step(None, 0.1) == gbr.GBR_ERR_ARG
     assert lib.gbr_destroy(None) == gbr.GBR_OK
+
+
+def test_degenerate_sizes_and_options_rejected(lib):
+    """Empty and oversized grids, unknown boundary kinds and options, and the
+    other entry points' argument checks, all before any device call."""
+    from paper_2305_00762_gb300 import gbr
+    out = ctypes.c_void_p()
+    ok = gbr.gbr_bc(1, 1, 1, 1, 0.1, 0.1)
+    for nx, ny in ((0, 64), (64, 0), (-3, 64), (5, 5), (1 << 16, 1 << 16)):  # last: > 2^31 cells
+        assert lib.gbr_create(nx, ny, 1.4, 0.0, 0.72, ctypes.byref(ok), ctypes.byref(out)) == gbr.GBR_ERR_ARG
+    bad = gbr.gbr_bc(4, 4, 1, 1, 0.1, 0.1)
+    assert lib.gbr_create(64, 64, 1.4, 0.0, 0.72, ctypes.byref(bad), ctypes.byref(out)) == gbr.GBR_ERR_ARG
+    assert lib.gbr_create(64, 64, 1.4, 0.0, 0.0, ctypes.byref(ok), ctypes.byref(out)) == gbr.GBR_ERR_ARG
+    assert lib.gbr_create(64, 64, 1.4, 0.0, 0.72, None, ctypes.byref(out)) == gbr.GBR_ERR_ARG
+    assert lib.gbr_set_option(None, gbr.GBR_OPT_PRECISION, ctypes.c_double(32.0)) == gbr.GBR_ERR_ARG
+    assert lib.gbr_residual(None, None, 0) == gbr.GBR_ERR_ARG
+    assert lib.gbr_step_cfl(None, ctypes.c_double(0.5), ctypes.c_double(1.0)) == gbr.GBR_ERR_ARG
+    assert lib.gbr_set_sensor_weights(None, None, 0) == gbr.GBR_ERR_ARG
+    # batches: no grids, a grid below the ghost width
+    nx = (ctypes.c_int * 1)(5)
+    ny = (ctypes.c_int * 1)(64)
+    d = (ctypes.c_double * 1)(0.1)
+    bcs = (ctypes.c_int * 4)(1, 1, 1, 1)
+    bout = ctypes.c_void_p()
+    assert lib.gbr_batch_create(0, nx, ny, d, d, bcs, ctypes.c_double(1.4), ctypes.byref(bout)) == gbr.GBR_ERR_ARG
+    assert lib.gbr_batch_create(1, nx, ny, d, d, bcs, ctypes.c_double(1.4), ctypes.byref(bout)) == gbr.GBR_ERR_ARG
+    # the allocation-free step: a grid larger than its fixed scratch
+    big = gbr.gbr_bc(1, 1, 1, 1, 0.1, 0.1)
+    assert lib.gbr_step_static(ctypes.c_void_p(16), ctypes.c_void_p(16), 4096, 4096, ctypes.c_double(1.4),
+                               ctypes.c_double(0.0), ctypes.c_double(0.72), ctypes.byref(big),
+                               ctypes.c_double(1e-3), None) == gbr.GBR_ERR_ARG
