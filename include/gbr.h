@@ -65,7 +65,14 @@ typedef enum {
     GBR_BC_PERIODIC = 0,     /* wrap around */
     GBR_BC_TRANSMISSIVE = 1, /* zero gradient: copy of the nearest interior cell */
     GBR_BC_NOSLIP_WALL = 2,  /* mirror; both velocity components change sign */
-    GBR_BC_SYMMETRY = 3      /* mirror; the normal velocity changes sign */
+    GBR_BC_SYMMETRY = 3,     /* mirror; the normal velocity changes sign */
+    /* The side is described by gbr_set_side (single-grid solvers only;
+     * transmissive until set): fixed inflow states, and kinds that change
+     * along the side at a point that may move with time, as the double Mach
+     * reflection of Woodward and Colella needs (Example 8). */
+    GBR_BC_CUSTOM = 4,
+    /* Only inside gbr_side: ghost cells hold a fixed primitive state. */
+    GBR_BC_FIXED = 5
 } gbr_bc_kind;
 
 /* Boundary kinds per side and the uniform cell sizes (the grid is
@@ -74,6 +81,22 @@ typedef struct {
     int west, east, south, north; /* gbr_bc_kind */
     double dx, dy;                /* > 0 */
 } gbr_bc;
+
+/* A GBR_BC_CUSTOM side. Cells along the side are split at the tangential
+ * coordinate s0 + speed * t (t: the stage's simulated time, see gbr_step;
+ * coordinates of cell centres measured from the grid's lower-left corner,
+ * i.e. (j + 1/2) dx along the south and north sides, (i + 1/2) dy along the
+ * west and east sides). Ghost cells beside cells below the split point take
+ * kind_lo, the others kind_hi: GBR_BC_TRANSMISSIVE, GBR_BC_NOSLIP_WALL,
+ * GBR_BC_SYMMETRY, or GBR_BC_FIXED with the primitive state lo / hi
+ * (rho > 0, u, v, p > 0). A corner ghost cell takes the south / north side's
+ * fixed state if that side is fixed there, else the image across that side
+ * of the west / east ghost cell (which is itself fixed or an image). */
+typedef struct {
+    int kind_lo, kind_hi;
+    double s0, speed;
+    double lo[4], hi[4];
+} gbr_side;
 
 /* Options for gbr_set_option. */
 typedef enum {
@@ -165,6 +188,17 @@ int gbr_step(gbr_ctx *ctx, double dt);
  * (Sec. 2.5), so that consecutive steps need no host synchronisation; the
  * simulated time advances by that dt (gbr_get_time). cfl > 0, dt_max > 0. */
 int gbr_step_cfl(gbr_ctx *ctx, double cfl, double dt_max);
+
+/* Describe side `side` (0 west, 1 east, 2 south, 3 north), which must have
+ * been created as GBR_BC_CUSTOM. Read during the call; applies to all later
+ * ghost fills. The RK stages of a step from time t with step dt see the
+ * boundary at t, t + dt and t + dt/2 (the stage abscissae of Eq. rk). */
+int gbr_set_side(gbr_ctx *ctx, int side, const gbr_side *s);
+
+/* Set the simulated time of the current state (gbr_set_state resets it to
+ * 0): the time GBR_BC_CUSTOM sides see, e.g. when a run resumes from a
+ * saved state. Asynchronous, in stream order. */
+int gbr_set_time(gbr_ctx *ctx, double t);
 
 /* Simulated time accumulated by gbr_step / gbr_step_cfl since the last
  * gbr_set_state (synchronises). */

@@ -34,6 +34,7 @@ _lock = threading.Lock()
 _lib = None
 
 BC_PERIODIC, BC_TRANSMISSIVE, BC_NOSLIP_WALL, BC_SYMMETRY = 0, 1, 2, 3
+BC_CUSTOM, BC_FIXED = 4, 5  # a side described by Config.sides; inside it, a fixed primitive state
 ERR_ARG, ERR_NONPHYSICAL = -1, -3
 G = 6
 
@@ -55,12 +56,19 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+class _Side(ctypes.Structure):
+    _fields_ = [("kind_lo", ctypes.c_int), ("kind_hi", ctypes.c_int),
+                ("s0", ctypes.c_double), ("speed", ctypes.c_double),
+                ("lo", ctypes.c_double * 4), ("hi", ctypes.c_double * 4)]
+
+
 class _Cfg(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("mu", ctypes.c_double),
                 ("Pr", ctypes.c_double), ("bc", ctypes.c_int * 4),
-                ("order", ctypes.c_int), ("cons", ctypes.c_int)]
+                ("order", ctypes.c_int), ("cons", ctypes.c_int),
+                ("t", ctypes.c_double), ("side", _Side * 4)]
 
 
 def lib():
@@ -138,10 +146,20 @@ class Config:
     bc: tuple = (BC_PERIODIC,) * 4   # west, east, south, north
     order: int = 7
     cons: int = 0                    # 1: MEG7-cons (conservative reconstruction)
+    t: float = 0.0                   # time of the state (moving custom sides)
+    # per side: None, or (kind_lo, kind_hi, s0, speed, lo (rho,u,v,p), hi) for BC_CUSTOM sides
+    sides: tuple = (None, None, None, None)
 
     def c(self) -> _Cfg:
+        sides = (_Side * 4)()
+        for k, sd in enumerate(self.sides):
+            if sd is not None:
+                klo, khi, s0, speed, lo, hi = sd
+                sides[k] = _Side(klo, khi, s0, speed, (ctypes.c_double * 4)(*lo), (ctypes.c_double * 4)(*hi))
+            else:
+                sides[k] = _Side(BC_TRANSMISSIVE, BC_TRANSMISSIVE, 0.0, 0.0)
         return _Cfg(self.nx, self.ny, self.dx, self.dy, self.gamma, self.mu,
-                    self.Pr, (ctypes.c_int * 4)(*self.bc), self.order, self.cons)
+                    self.Pr, (ctypes.c_int * 4)(*self.bc), self.order, self.cons, self.t, sides)
 
 
 # ---- scalar building blocks (pins) ----------------------------------------
@@ -284,11 +302,12 @@ def set_num_threads(n: int) -> None:
 def run(cfg: Config, Q, t_end: float, cfl: float, max_steps: int = 10**9):
     """Advance to t_end with dt = min(cfl/lambda, t_end - t) per step
     (Sec. 2.5). Returns (Q, t, steps)."""
+    import dataclasses
     Q = _state(cfg, Q).copy()
     t, n = 0.0, 0
     while t < t_end * (1 - 1e-14) and n < max_steps:
         dt = min(cfl / max_wavespeed(cfg, Q), t_end - t)
-        Q, rc = rk3_step(cfg, Q, dt)
+        Q, rc = rk3_step(dataclasses.replace(cfg, t=t), Q, dt)
         if rc != 0:
             raise RuntimeError("oracle: non-physical state")
         t += dt

@@ -45,6 +45,14 @@
  *      rho', p'; heat conductivity mu/(Pr (gamma-1)) (Eq. visc-interface).
  *  R9  G = 6 ghost layers: the LC bound at j+1/2 uses d_{j-1}, which uses
  *      Phi'_{j-2}, which uses Phi_{j-5}.
+ *  R23 positivity fallback: a reconstructed face state with rho <= 0 or
+ *      p <= 0 is replaced by the state of the cell on its side of the face
+ *      (first order there); the paper prints no such rule, but the double
+ *      Mach reflection (Example 8) reconstructs a negative pressure at the
+ *      shock's foot in its first step without it. States that stay positive
+ *      are untouched.
+ *  R24 time-dependent boundaries: the RK stages of a step from t with step
+ *      dt see the boundary at t, t + dt and t + dt/2 (Eq. rk's stage times).
  *  R20 MEG7-cons (Sec. 2.2, conservative reconstruction): Q and its
  *      sixth-order gradients are projected with the left eigenvectors of the
  *      conservative flux Jacobian frozen at the same mean state as in R2
@@ -59,7 +67,25 @@
 
 #define OR_G 6 /* ghost layers, reading R9 */
 
-enum { OR_BC_PERIODIC = 0, OR_BC_TRANSMISSIVE = 1, OR_BC_NOSLIP_WALL = 2, OR_BC_SYMMETRY = 3 };
+enum {
+    OR_BC_PERIODIC = 0,
+    OR_BC_TRANSMISSIVE = 1,
+    OR_BC_NOSLIP_WALL = 2,
+    OR_BC_SYMMETRY = 3,
+    OR_BC_CUSTOM = 4, /* described by or_cfg.side[] */
+    OR_BC_FIXED = 5   /* inside a side description: a fixed primitive state */
+};
+
+/* A custom side (the double Mach reflection of Woodward and Colella,
+ * Example 8, needs them): the ghost cells beside interior cell k of the side
+ * (centre at (k + 1/2) h along it) take kind_lo when that centre lies below
+ * s0 + speed * t, else kind_hi; OR_BC_FIXED holds the primitive state lo or
+ * hi. */
+typedef struct {
+    int kind_lo, kind_hi;
+    double s0, speed;
+    double lo[4], hi[4];
+} or_side;
 enum { OR_OK = 0, OR_ERR_ARG = -1, OR_ERR_NONPHYSICAL = -3, OR_ERR_NOMEM = -7 };
 
 typedef struct {
@@ -69,6 +95,8 @@ typedef struct {
     int bc[4];                /* west, east, south, north (OR_BC_*) */
     int order;                /* 7 = MEG7 (Eq. grb / flux-full); 4 = alpha=4, beta=0 subset */
     int cons;                 /* 0 = MEG7-prim (reconstruct U), 1 = MEG7-cons (reconstruct Q) */
+    double t;                 /* time of the state (custom sides may move with it) */
+    or_side side[4];          /* descriptions of OR_BC_CUSTOM sides */
 } or_cfg;
 
 /* ---------------------------------------------------------------------- */
@@ -339,6 +367,26 @@ static int ghost_source(int k, int n, int bc_lo, int bc_hi, int *flip_normal, in
 /* Ghost-cell boundary conditions (Sec. 3, ghost cell approach): first the x
  * ghosts of the interior rows, then the y ghosts of every column, so corner
  * ghosts take the y image of the x ghosts. Qp: 4 padded planes. */
+/* Kind of side `sd` beside the cell with tangential index k (centre at
+ * (k + 1/2) h) at time t; a fixed state is returned as a conservative vector
+ * in q. Non-custom sides return their own kind. */
+static int side_kind(const or_cfg *c, int sd, int k, double h, double q[4])
+{
+    if (c->bc[sd] != OR_BC_CUSTOM)
+        return c->bc[sd];
+    const or_side *S = &c->side[sd];
+    int lo = (k + 0.5) * h < S->s0 + S->speed * c->t;
+    int kind = lo ? S->kind_lo : S->kind_hi;
+    if (kind == OR_BC_FIXED) {
+        const double *w = lo ? S->lo : S->hi;
+        q[0] = w[0];
+        q[1] = w[0] * w[1];
+        q[2] = w[0] * w[2];
+        q[3] = w[3] / (c->gamma - 1.0) + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2]);
+    }
+    return kind;
+}
+
 void or_fill_ghosts(const or_cfg *c, double *Qp)
 {
     const int nx = c->nx, ny = c->ny;
@@ -348,8 +396,16 @@ void or_fill_ghosts(const or_cfg *c, double *Qp)
             if (j >= 0 && j < nx)
                 continue;
             int fn, ft;
-            int s = ghost_source(j, nx, c->bc[0], c->bc[1], &fn, &ft);
-            ptrdiff_t d = pidx(c, j, i), o = pidx(c, s, i);
+            double fixed[4];
+            int kind = side_kind(c, j < 0 ? 0 : 1, i, c->dy, fixed);
+            ptrdiff_t d = pidx(c, j, i);
+            if (kind == OR_BC_FIXED) {
+                for (int m = 0; m < 4; ++m)
+                    Qp[m * N + d] = fixed[m];
+                continue;
+            }
+            int s = ghost_source(j, nx, j < 0 ? kind : c->bc[0], j < 0 ? c->bc[1] : kind, &fn, &ft);
+            ptrdiff_t o = pidx(c, s, i);
             Qp[0 * N + d] = Qp[0 * N + o];
             Qp[1 * N + d] = fn ? -Qp[1 * N + o] : Qp[1 * N + o]; /* x momentum is normal */
             Qp[2 * N + d] = ft ? -Qp[2 * N + o] : Qp[2 * N + o];
@@ -359,10 +415,18 @@ void or_fill_ghosts(const or_cfg *c, double *Qp)
     for (int i = -OR_G; i < ny + OR_G; ++i) {
         if (i >= 0 && i < ny)
             continue;
-        int fn, ft;
-        int s = ghost_source(i, ny, c->bc[2], c->bc[3], &fn, &ft);
         for (int j = -OR_G; j < nx + OR_G; ++j) {
-            ptrdiff_t d = pidx(c, j, i), o = pidx(c, j, s);
+            int fn, ft;
+            double fixed[4];
+            int kind = side_kind(c, i < 0 ? 2 : 3, j, c->dx, fixed);
+            ptrdiff_t d = pidx(c, j, i);
+            if (kind == OR_BC_FIXED) {
+                for (int m = 0; m < 4; ++m)
+                    Qp[m * N + d] = fixed[m];
+                continue;
+            }
+            int s = ghost_source(i, ny, i < 0 ? kind : c->bc[2], i < 0 ? c->bc[3] : kind, &fn, &ft);
+            ptrdiff_t o = pidx(c, j, s);
             Qp[0 * N + d] = Qp[0 * N + o];
             Qp[1 * N + d] = ft ? -Qp[1 * N + o] : Qp[1 * N + o];
             Qp[2 * N + d] = fn ? -Qp[2 * N + o] : Qp[2 * N + o]; /* y momentum is normal */
@@ -513,6 +577,15 @@ static void face_flux(const or_cfg *c, const double *const P[4], const double *c
         cons_to_prim(g, qL, UL);
         cons_to_prim(g, qR, UR);
     }
+    /* Reading R23: a face state with rho <= 0 or p <= 0 (characteristic
+     * reconstruction across a strong shock, e.g. at the foot of the double
+     * Mach reflection) is replaced by the adjacent cell's state. */
+    if (!(UL[0] > 0.0 && UL[3] > 0.0))
+        for (int m = 0; m < 4; ++m)
+            UL[m] = U[5][m];
+    if (!(UR[0] > 0.0 && UR[3] > 0.0))
+        for (int m = 0; m < 4; ++m)
+            UR[m] = U[6][m];
 
     /* Hybrid face fluxes (Sec. 2.4): F(f) of Eqs. flux-full/flux-right where
      * sigma = 1, F(Q_L), F(Q_R) of the MEG7 states where sigma = 0. */
@@ -594,9 +667,17 @@ static int cfg_ok(const or_cfg *c)
         return 0;
     if (c->cons != 0 && c->cons != 1)
         return 0;
-    for (int k = 0; k < 4; ++k)
-        if (c->bc[k] < 0 || c->bc[k] > 3)
+    for (int k = 0; k < 4; ++k) {
+        if (c->bc[k] < 0 || c->bc[k] > OR_BC_CUSTOM)
             return 0;
+        if (c->bc[k] == OR_BC_CUSTOM) {
+            const int kk[2] = {c->side[k].kind_lo, c->side[k].kind_hi};
+            for (int h = 0; h < 2; ++h)
+                if (kk[h] != OR_BC_TRANSMISSIVE && kk[h] != OR_BC_NOSLIP_WALL && kk[h] != OR_BC_SYMMETRY
+                    && kk[h] != OR_BC_FIXED)
+                    return 0;
+        }
+    }
     if ((c->bc[0] == OR_BC_PERIODIC) != (c->bc[1] == OR_BC_PERIODIC))
         return 0;
     if ((c->bc[2] == OR_BC_PERIODIC) != (c->bc[3] == OR_BC_PERIODIC))
@@ -727,6 +808,10 @@ int or_rk3_step(const or_cfg *c, double *Q, double dt)
     }
     int rc = OR_OK, bad = 0;
     memcpy(Q0, Q, sizeof(double) * n);
+    /* the stages see the boundaries at t, t + dt and t + dt/2 (Eq. rk) */
+    or_cfg c2 = *c, c3 = *c;
+    c2.t = c->t + dt;
+    c3.t = c->t + 0.5 * dt;
     /* Q(1) = Qn + dt Res(Qn) */
     rc = or_residual(c, Q0, R, NULL, NULL, NULL);
     for (size_t k = 0; k < n && rc == OR_OK; ++k)
@@ -737,7 +822,7 @@ int or_rk3_step(const or_cfg *c, double *Q, double dt)
         bad |= !physical(c->gamma, q);
     }
     if (rc == OR_OK)
-        rc = or_residual(c, Qs, R, NULL, NULL, NULL);
+        rc = or_residual(&c2, Qs, R, NULL, NULL, NULL);
     for (size_t k = 0; k < n && rc == OR_OK; ++k)
         Qs[k] = 0.75 * Q0[k] + 0.25 * Qs[k] + 0.25 * dt * R[k];
     for (size_t e = 0; e < cells && rc == OR_OK; ++e) {
@@ -746,7 +831,7 @@ int or_rk3_step(const or_cfg *c, double *Q, double dt)
     }
     /* Q(n+1) = 1/3 Qn + 2/3 Q(2) + 2/3 dt Res(Q(2)) */
     if (rc == OR_OK)
-        rc = or_residual(c, Qs, R, NULL, NULL, NULL);
+        rc = or_residual(&c3, Qs, R, NULL, NULL, NULL);
     for (size_t k = 0; k < n && rc == OR_OK; ++k)
         Q[k] = Q0[k] / 3.0 + 2.0 / 3.0 * Qs[k] + 2.0 / 3.0 * dt * R[k];
     for (size_t e = 0; e < cells && rc == OR_OK; ++e) {

@@ -218,6 +218,57 @@ def shock_tube(n, left, right, t_end, ny=8, x_split=0.5, gamma=1.4, cfl=0.5):
                 {"left": left, "right": right, "x_split": x_split})
 
 
+BC_CUSTOM, BC_FIXED = 4, 5   # a side described by meta["sides"]; a fixed primitive state
+
+
+def double_mach(nx=1024, ny=None, t_end=0.2, cfl=0.5):
+    """Example 8 (Woodward and Colella): [0,4] x [0,1], a Mach 10 shock at
+    60 degrees to the wall, post-shock (8, 8.25 cos 30, -8.25 sin 30, 116.5),
+    pre-shock (1.4, 0, 0, 1). Boundaries: post-shock inflow on the west,
+    transmissive east, south post-shock for x < 1/6 and a reflecting wall
+    (mirror, normal velocity reversed) beyond, north post-shock up to the
+    exact shock position 1/6 + (1 + 20 t)/sqrt(3) and pre-shock beyond.
+    meta["sides"][k] = (kind_lo, kind_hi, s0, speed, lo, hi) of a custom
+    side, positions measured from the grid's lower-left corner."""
+    ny = nx // 4 if ny is None else ny
+    xc, dx = centres(nx, 0.0, 4.0)
+    yc, dy = centres(ny, 0.0, 1.0)
+    X, Y = np.meshgrid(xc, yc)
+    c30, s30, r3 = np.cos(np.pi / 6), np.sin(np.pi / 6), np.sqrt(3.0)
+    post = (8.0, 8.25 * c30, -8.25 * s30, 116.5)
+    pre = (1.4, 0.0, 0.0, 1.0)
+    behind = X < 1.0 / 6.0 + Y / r3
+    prim = [np.where(behind, post[m], pre[m]) for m in range(4)]
+    Q = prim_to_cons(*prim, 1.4)
+    sides = ((BC_FIXED, BC_FIXED, 0.0, 0.0, post, post), None,
+             (BC_FIXED, BC_SYMMETRY, 1.0 / 6.0, 0.0, post, pre),
+             (BC_FIXED, BC_FIXED, 1.0 / 6.0 + 1.0 / r3, 20.0 / r3, post, pre))
+    return Case("double_mach", np.ascontiguousarray(Q), dx, dy, 1.4, 0.0, 0.72,
+                (BC_CUSTOM, BC_TRANSMISSIVE, BC_CUSTOM, BC_CUSTOM), t_end, cfl,
+                {"sides": sides, "post": post, "pre": pre, "shock_speed": 10.0})
+
+
+def shock_entropy_2d(nx=400, ny=None, t_end=1.8, cfl=0.5, theta=np.pi / 6):
+    """Example 7: [-5,5] x [-1,1]; a Mach 3 shock at x = -4 with post-shock
+    (3.857143, 2.629369, 0, 10.3333) runs into rho = 1 + 0.2 sin(10 x cos theta
+    + 10 y sin theta), u = v = 0, p = 1. Boundaries: post-shock inflow on the
+    west, transmissive elsewhere."""
+    ny = nx // 5 if ny is None else ny
+    xc, dx = centres(nx, -5.0, 5.0)
+    yc, dy = centres(ny, -1.0, 1.0)
+    X, Y = np.meshgrid(xc, yc)
+    post = (3.857143, 2.629369, 0.0, 10.3333)
+    behind = X < -4.0
+    rho = np.where(behind, post[0], 1.0 + 0.2 * np.sin(10.0 * X * np.cos(theta) + 10.0 * Y * np.sin(theta)))
+    u = np.where(behind, post[1], 0.0)
+    p = np.where(behind, post[3], 1.0)
+    Q = prim_to_cons(rho, u, np.zeros_like(rho), p, 1.4)
+    sides = ((BC_FIXED, BC_FIXED, 0.0, 0.0, post, post), None, None, None)
+    return Case("shock_entropy_2d", np.ascontiguousarray(Q), dx, dy, 1.4, 0.0, 0.72,
+                (BC_CUSTOM, BC_TRANSMISSIVE, BC_TRANSMISSIVE, BC_TRANSMISSIVE), t_end, cfl,
+                {"sides": sides, "post": post, "theta": theta})
+
+
 SOD = ((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 0.2)           # Example 2, Sod
 LAX = ((0.445, 0.698, 3.528), (0.5, 0.0, 0.571), 0.14)   # Example 2, Lax (t = 0.14)
 

@@ -22,10 +22,29 @@ __global__ void ghost_kernel(const GhostParams P)
         }
         d->dt = dt;
         d->t += dt;
+        d->ts[P.next] = d->ts[P.cur] + dt;
         d->lam[P.next] = 0ull;
     }
     if (id >= total) return;
-    fill_ghost(P.g, P.q, P.bc, id);
+    // Boundary time of this stage: the step's start time ts[cur] (not written
+    // by this launch) plus c_stage dt (dt was written by an earlier launch
+    // whenever c_stage != 0).
+    const double t = P.ds->ts[P.cur] + (P.c_stage != 0.0 ? P.c_stage * P.ds->dt : 0.0);
+    fill_ghost(P.g, P.q, P.bc, id, P.side, P.dx, P.dy, t);
+}
+
+// Simulated time of the current state: the reported time and the step start
+// time (slot cur) that time-dependent boundaries read.
+__global__ void set_time_kernel(DevScalars* d, int cur, double t)
+{
+    d->t = t;
+    d->ts[cur] = t;
+}
+
+cudaError_t launch_set_time(DevScalars* d, int cur, double t, cudaStream_t s)
+{
+    set_time_kernel<<<1, 1, 0, s>>>(d, cur, t);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ghosts(const GhostParams& p, cudaStream_t s)

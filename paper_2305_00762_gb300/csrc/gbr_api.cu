@@ -1,5 +1,7 @@
 // Host implementation of the C ABI declared in include/gbr.h.
 #include <cuda_runtime.h>
+
+#include <cmath>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -39,6 +41,7 @@ struct gbr_ctx {
     int launches[GBR_KERNEL_CLASSES];
     int dropped;
     int stall_test;  // GBR_OPT_STALL_TEST
+    SideBC side[4];  // GBR_BC_CUSTOM sides (transmissive until gbr_set_side)
     // learned sensor
     SensorDev* d_sensor;
     float* prob;          // per-cell sensor output scratch
@@ -77,7 +80,7 @@ bool bc_ok(const gbr_bc* bc)
 {
     const int k[4] = {bc->west, bc->east, bc->south, bc->north};
     for (int i = 0; i < 4; ++i)
-        if (k[i] < GBR_BC_PERIODIC || k[i] > GBR_BC_SYMMETRY) return false;
+        if (k[i] < GBR_BC_PERIODIC || k[i] > GBR_BC_CUSTOM) return false;
     if ((bc->west == GBR_BC_PERIODIC) != (bc->east == GBR_BC_PERIODIC)) return false;
     if ((bc->south == GBR_BC_PERIODIC) != (bc->north == GBR_BC_PERIODIC)) return false;
     return bc->dx > 0.0 && bc->dy > 0.0;
@@ -137,12 +140,17 @@ struct Timed {
     }
 };
 
-int ghosts(gbr_ctx* c, double* q, int mode, double dt, double cfl, double dt_max)
+int ghosts(gbr_ctx* c, double* q, int mode, double dt, double cfl, double dt_max, double c_stage = 0.0)
 {
     Timed tm(c, GBR_KERNEL_GHOST);
     GhostParams p;
+    memset(&p, 0, sizeof(p));
     p.g = c->g;
     p.q = q;
+    for (int k = 0; k < 4; ++k) p.side[k] = c->side[k];
+    p.dx = c->ph.dx;
+    p.dy = c->ph.dy;
+    p.c_stage = c_stage;
     for (int k = 0; k < 4; ++k) p.bc[k] = c->bc[k];
     p.ds = c->ds;
     p.mode = mode;
@@ -200,7 +208,7 @@ int rk3_step(gbr_ctx* c, int mode, double dt, double cfl, double dt_max)
     p.cb = 1.0;
     p.cc = 1.0;
     if ((rc = stage(c, p)) != GBR_OK) return rc;
-    if ((rc = ghosts(c, c->Qa, 0, 0, 0, 0)) != GBR_OK) return rc;
+    if ((rc = ghosts(c, c->Qa, 0, 0, 0, 0, 1.0)) != GBR_OK) return rc;  // stage 2 at t + dt
     p = stage_params(c, c->Qa);
     p.qout = c->Qb;
     p.dt = dt;
@@ -209,7 +217,7 @@ int rk3_step(gbr_ctx* c, int mode, double dt, double cfl, double dt_max)
     p.cb = 0.25;
     p.cc = 0.25;
     if ((rc = stage(c, p)) != GBR_OK) return rc;
-    if ((rc = ghosts(c, c->Qb, 0, 0, 0, 0)) != GBR_OK) return rc;
+    if ((rc = ghosts(c, c->Qb, 0, 0, 0, 0, 0.5)) != GBR_OK) return rc;  // stage 3 at t + dt/2
     p = stage_params(c, c->Qb);
     p.qout = c->Qn;  // each cell reads its own Q^n before writing it
     p.dt = dt;
@@ -250,6 +258,11 @@ int gbr_create(int nx, int ny, double gamma, double mu, double Pr, const gbr_bc*
     c->bc[1] = bc->east;
     c->bc[2] = bc->south;
     c->bc[3] = bc->north;
+    for (int k = 0; k < 4; ++k) {
+        c->side[k].kind_lo = c->side[k].kind_hi = GBR_BC_TRANSMISSIVE;
+        c->side[k].s0 = 0.0;
+        c->side[k].speed = 0.0;
+    }
     c->precision = 64;
     c->stream = 0;
     int rc = cuda_status(cudaGetDevice(&c->device));
@@ -391,6 +404,44 @@ int gbr_max_wavespeed(gbr_ctx* c, double* lambda)
     memcpy(&v, &bits, sizeof(v));
     *lambda = v;
     return rc;
+}
+
+int gbr_set_time(gbr_ctx* c, double t)
+{
+    if (!c || !std::isfinite(t)) return GBR_ERR_ARG;
+    if (!c->have_state) return GBR_ERR_STATE;
+    DeviceGuard dg(c->device);
+    return cuda_status(launch_set_time(c->ds, c->lam_cur, t, c->stream));
+}
+
+int gbr_set_side(gbr_ctx* c, int side, const gbr_side* sd)
+{
+    if (!c || !sd || side < 0 || side > 3 || c->bc[side] != GBR_BC_CUSTOM) return GBR_ERR_ARG;
+    const int kinds[2] = {sd->kind_lo, sd->kind_hi};
+    const double* prim[2] = {sd->lo, sd->hi};
+    SideBC b;
+    memset(&b, 0, sizeof(b));
+    for (int h = 0; h < 2; ++h) {
+        const int k = kinds[h];
+        if (k != GBR_BC_TRANSMISSIVE && k != GBR_BC_NOSLIP_WALL && k != GBR_BC_SYMMETRY && k != GBR_BC_FIXED)
+            return GBR_ERR_ARG;
+        double* q = h ? b.qhi : b.qlo;
+        if (k == GBR_BC_FIXED) {
+            const double r = prim[h][0], u = prim[h][1], v = prim[h][2], p = prim[h][3];
+            if (!(r > 0.0) || !(p > 0.0) || !std::isfinite(u) || !std::isfinite(v)) return GBR_ERR_ARG;
+            q[0] = r;
+            q[1] = r * u;
+            q[2] = r * v;
+            q[3] = p / (c->ph.gamma - 1.0) + 0.5 * r * (u * u + v * v);
+        }
+    }
+    if (!std::isfinite(sd->s0) || !std::isfinite(sd->speed)) return GBR_ERR_ARG;
+    b.kind_lo = sd->kind_lo;
+    b.kind_hi = sd->kind_hi;
+    b.s0 = sd->s0;
+    b.speed = sd->speed;
+    c->side[side] = b;
+    return GBR_OK;
 }
 
 int gbr_set_option(gbr_ctx* c, int key, double val)

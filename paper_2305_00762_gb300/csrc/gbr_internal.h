@@ -15,8 +15,17 @@ struct DevScalars {
     unsigned long long lam[2];  // CFL wavespeed of a state, bits of a double >= 0
     double dt;                  // step size used by the current step
     double t;                   // simulated time since the last set_state
-    unsigned int err;           // bit 0: non-physical stage state
+    unsigned int err;           // bit 0: non-physical stage state, bit 1: a bounded wait gave up
     unsigned int pad;
+    double ts[2];               // time at the start of the step, slot cur (read by time-dependent boundaries)
+};
+
+// A GBR_BC_CUSTOM side on the device: kinds below / above the split point
+// s0 + speed t along the side, fixed states as conservative vectors.
+struct SideBC {
+    int kind_lo, kind_hi;
+    double s0, speed;
+    double qlo[4], qhi[4];
 };
 
 // Padded state geometry: plane m of a state starts at base + m * plane; the
@@ -66,6 +75,9 @@ struct GhostParams {
     int mode;
     int cur, next;
     double dt, cfl, dt_max;
+    SideBC side[4];     // GBR_BC_CUSTOM sides
+    double dx, dy;      // cell sizes (positions along custom sides)
+    double c_stage;     // stage abscissa: the boundary time is ts[cur] + c_stage dt
 };
 
 // One grid of a batch, as the device sees it. tiles_x / tile_begin describe
@@ -90,6 +102,7 @@ struct TileShape {
 };
 
 cudaError_t launch_ghosts(const GhostParams& p, cudaStream_t s);
+cudaError_t launch_set_time(DevScalars* d, int cur, double t, cudaStream_t s);
 // Ghost cells of buffer `buf` (0, 1, 2) of every case; with mode 2 the first
 // ncases threads also form each case's dt = min(cfl / lam, t_end - t), advance
 // its time and clear its wavespeed slot.

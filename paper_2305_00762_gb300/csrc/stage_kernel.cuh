@@ -491,6 +491,21 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
         unR = crb * (wR[3] - wR[0]);
         utR = wR[2];
         pR = c2 * (wR[0] + wR[3]);
+        // positivity fallback: a face state with rho <= 0 or p <= 0 takes the
+        // adjacent cell's state (characteristic reconstruction across a
+        // strong shock, e.g. the foot of the double Mach reflection)
+        if (!(rL > T(0) && pL > T(0))) {
+            rL = in.u[0][0];
+            unL = in.u[1][0];
+            utL = in.u[2][0];
+            pL = in.u[3][0];
+        }
+        if (!(rR > T(0) && pR > T(0))) {
+            rR = in.u[0][su];
+            unR = in.u[1][su];
+            utR = in.u[2][su];
+            pR = in.u[3][su];
+        }
         EL = pL * P.igm1 + T(0.5) * rL * (unL * unL + utL * utL);
         ER = pR * P.igm1 + T(0.5) * rR * (unR * unR + utR * utR);
         QL[0] = rL;
@@ -530,6 +545,29 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
             unR = QR[1] * ir;
             utR = QR[2] * ir;
             pR = P.gm1 * (ER - T(0.5) * rR * (unR * unR + utR * utR));
+        }
+        // positivity fallback (as for MEG7-prim): the adjacent cell's state
+        if (!(rL > T(0) && pL > T(0))) {
+            rL = in.u[0][0];
+            unL = in.u[1][0];
+            utL = in.u[2][0];
+            pL = in.u[3][0];
+            EL = pL * P.igm1 + T(0.5) * rL * (unL * unL + utL * utL);
+            QL[0] = rL;
+            QL[1] = rL * unL;
+            QL[2] = rL * utL;
+            QL[3] = EL;
+        }
+        if (!(rR > T(0) && pR > T(0))) {
+            rR = in.u[0][su];
+            unR = in.u[1][su];
+            utR = in.u[2][su];
+            pR = in.u[3][su];
+            ER = pR * P.igm1 + T(0.5) * rR * (unR * unR + utR * utR);
+            QR[0] = rR;
+            QR[1] = rR * unR;
+            QR[2] = rR * utR;
+            QR[3] = ER;
         }
     }
 

@@ -19,6 +19,7 @@ from . import build as _build
 GBR_OK, GBR_ERR_ARG, GBR_ERR_CUDA, GBR_ERR_NONPHYSICAL = 0, -1, -2, -3
 GBR_ERR_TIMEOUT, GBR_ERR_STATE, GBR_ERR_NOMEM, GBR_ERR_UNSUPPORTED = -4, -5, -6, -7
 GBR_BC_PERIODIC, GBR_BC_TRANSMISSIVE, GBR_BC_NOSLIP_WALL, GBR_BC_SYMMETRY = 0, 1, 2, 3
+GBR_BC_CUSTOM, GBR_BC_FIXED = 4, 5
 GBR_OPT_PRECISION, GBR_OPT_RECORD_FLAGS, GBR_OPT_SENSOR, GBR_OPT_TIMING, GBR_OPT_ORDER = 0, 1, 2, 3, 4
 GBR_OPT_VARIABLES, GBR_OPT_STALL_TEST = 5, 6
 GBR_KERNEL_STAGE, GBR_KERNEL_GHOST, GBR_KERNEL_WAVESPEED, GBR_KERNEL_CLASSES = 0, 1, 2, 3
@@ -38,6 +39,11 @@ class GbrError(RuntimeError):
 class gbr_bc(ctypes.Structure):
     _fields_ = [("west", ctypes.c_int), ("east", ctypes.c_int), ("south", ctypes.c_int),
                 ("north", ctypes.c_int), ("dx", ctypes.c_double), ("dy", ctypes.c_double)]
+
+
+class gbr_side(ctypes.Structure):
+    _fields_ = [("kind_lo", ctypes.c_int), ("kind_hi", ctypes.c_int), ("s0", ctypes.c_double),
+                ("speed", ctypes.c_double), ("lo", ctypes.c_double * 4), ("hi", ctypes.c_double * 4)]
 
 
 def lib_path() -> str:
@@ -66,6 +72,8 @@ def load():
         "gbr_get_time": (ip, [vp, ctypes.POINTER(dp)]),
         "gbr_max_wavespeed": (ip, [vp, ctypes.POINTER(dp)]),
         "gbr_set_option": (ip, [vp, ip, dp]),
+        "gbr_set_side": (ip, [vp, ip, ctypes.POINTER(gbr_side)]),
+        "gbr_set_time": (ip, [vp, dp]),
         "gbr_get_flags": (ip, [vp, vp, vp, ip]),
         "gbr_get_timing": (ip, [vp, ctypes.POINTER(dp), ctypes.POINTER(ip), ctypes.POINTER(ip)]),
         "gbr_sync": (ip, [vp]),
@@ -187,6 +195,14 @@ def gbr_set_option(ctx, key, val):
     return _check(load().gbr_set_option(ctx, int(key), float(val)), "gbr_set_option")
 
 
+def gbr_set_side(ctx, side, kind_lo, kind_hi, s0=0.0, speed=0.0, lo=(1.0, 0.0, 0.0, 1.0), hi=(1.0, 0.0, 0.0, 1.0)):
+    """Describe a GBR_BC_CUSTOM side (see gbr_side in gbr.h); lo, hi are
+    primitive states (rho, u, v, p) used by GBR_BC_FIXED."""
+    sd = gbr_side(int(kind_lo), int(kind_hi), float(s0), float(speed), (ctypes.c_double * 4)(*lo),
+                  (ctypes.c_double * 4)(*hi))
+    return _check(load().gbr_set_side(ctx, int(side), ctypes.byref(sd)), "gbr_set_side")
+
+
 def gbr_get_flags(ctx, sigx, sigy, nx, ny):
     _expect(sigx, "uint8", (ny, nx + 1))
     _expect(sigy, "uint8", (ny + 1, nx))
@@ -304,7 +320,11 @@ class Solver:
 
     @classmethod
     def for_case(cls, case, **kw):
-        return cls(case.nx, case.ny, case.dx, case.dy, case.gamma, case.mu, case.Pr, case.bc, **kw)
+        s = cls(case.nx, case.ny, case.dx, case.dy, case.gamma, case.mu, case.Pr, case.bc, **kw)
+        for k, sd in enumerate((case.meta or {}).get("sides", (None,) * 4)):
+            if sd is not None:
+                gbr_set_side(s.ctx, k, *sd)
+        return s
 
     def close(self):
         if self.ctx is not None:
@@ -340,6 +360,9 @@ class Solver:
 
     def time(self):
         return gbr_get_time(self.ctx)
+
+    def set_time(self, t):
+        _check(load().gbr_set_time(self.ctx, float(t)), "gbr_set_time")
 
     def max_wavespeed(self, allow=()):
         return gbr_max_wavespeed(self.ctx, allow)[0]

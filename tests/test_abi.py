@@ -60,14 +60,16 @@ def test_degenerate_sizes_and_options_rejected(lib):
     ok = gbr.gbr_bc(1, 1, 1, 1, 0.1, 0.1)
     for nx, ny in ((0, 64), (64, 0), (-3, 64), (5, 5), (1 << 16, 1 << 16)):  # last: > 2^31 cells
         assert lib.gbr_create(nx, ny, 1.4, 0.0, 0.72, ctypes.byref(ok), ctypes.byref(out)) == gbr.GBR_ERR_ARG
-    bad = gbr.gbr_bc(4, 4, 1, 1, 0.1, 0.1)
-    assert lib.gbr_create(64, 64, 1.4, 0.0, 0.72, ctypes.byref(bad), ctypes.byref(out)) == gbr.GBR_ERR_ARG
+    for k in (5, 6, -1):   # GBR_BC_FIXED only inside a gbr_side; 6, -1 unknown
+        bad = gbr.gbr_bc(k, 1, 1, 1, 0.1, 0.1)
+        assert lib.gbr_create(64, 64, 1.4, 0.0, 0.72, ctypes.byref(bad), ctypes.byref(out)) == gbr.GBR_ERR_ARG
     assert lib.gbr_create(64, 64, 1.4, 0.0, 0.0, ctypes.byref(ok), ctypes.byref(out)) == gbr.GBR_ERR_ARG
     assert lib.gbr_create(64, 64, 1.4, 0.0, 0.72, None, ctypes.byref(out)) == gbr.GBR_ERR_ARG
     assert lib.gbr_set_option(None, gbr.GBR_OPT_PRECISION, ctypes.c_double(32.0)) == gbr.GBR_ERR_ARG
     assert lib.gbr_residual(None, None, 0) == gbr.GBR_ERR_ARG
     assert lib.gbr_step_cfl(None, ctypes.c_double(0.5), ctypes.c_double(1.0)) == gbr.GBR_ERR_ARG
     assert lib.gbr_set_sensor_weights(None, None, 0) == gbr.GBR_ERR_ARG
+    assert lib.gbr_set_side(None, 0, None) == gbr.GBR_ERR_ARG
     # batches: no grids, a grid below the ghost width
     nx = (ctypes.c_int * 1)(5)
     ny = (ctypes.c_int * 1)(64)
