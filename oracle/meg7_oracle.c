@@ -45,13 +45,13 @@
  *      rho', p'; heat conductivity mu/(Pr (gamma-1)) (Eq. visc-interface).
  *  R9  G = 6 ghost layers: the LC bound at j+1/2 uses d_{j-1}, which uses
  *      Phi'_{j-2}, which uses Phi_{j-5}.
- *  R23 positivity fallback: a reconstructed face state with rho <= 0 or
+ *  R22 positivity fallback: a reconstructed face state with rho <= 0 or
  *      p <= 0 is replaced by the state of the cell on its side of the face
  *      (first order there); the paper prints no such rule, but the double
  *      Mach reflection (Example 8) reconstructs a negative pressure at the
  *      shock's foot in its first step without it. States that stay positive
  *      are untouched.
- *  R24 time-dependent boundaries: the RK stages of a step from t with step
+ *  R23 time-dependent boundaries: the RK stages of a step from t with step
  *      dt see the boundary at t, t + dt and t + dt/2 (Eq. rk's stage times).
  *  R20 MEG7-cons (Sec. 2.2, conservative reconstruction): Q and its
  *      sixth-order gradients are projected with the left eigenvectors of the
@@ -577,7 +577,7 @@ static void face_flux(const or_cfg *c, const double *const P[4], const double *c
         cons_to_prim(g, qL, UL);
         cons_to_prim(g, qR, UR);
     }
-    /* Reading R23: a face state with rho <= 0 or p <= 0 (characteristic
+    /* Reading R22: a face state with rho <= 0 or p <= 0 (characteristic
      * reconstruction across a strong shock, e.g. at the foot of the double
      * Mach reflection) is replaced by the adjacent cell's state. */
     if (!(UL[0] > 0.0 && UL[3] > 0.0))
