@@ -4,6 +4,7 @@
 
 #include "ghost.cuh"
 #include "gbr_internal.h"
+#include "stage_kernel.cuh"
 
 namespace gbr {
 
@@ -102,26 +103,22 @@ __device__ __forceinline__ double warp_max_d(double v)
 // lambda = max over interior cells of max((|u|+c)/dx, (|v|+c)/dy, 4 nu/dx^2,
 // 4 nu/dy^2): grid-stride per thread, warp shuffle, block, one atomic max on
 // the bit pattern (valid for non-negative doubles).
+// Standalone CFL wavespeed of a padded state in the precision T of the
+// stage arithmetic (the same per-cell function as the stage epilogue).
+template <typename T>
 __global__ void wavespeed_kernel(const Grid g, const Physics ph, const double* __restrict__ q,
                                  unsigned long long* lam)
 {
     const long long n = (long long)g.nx * g.ny;
-    const double idx_ = 1.0 / ph.dx, idy = 1.0 / ph.dy;
+    const T gamma = T(ph.gamma), gm1 = T(ph.gamma - 1.0), mu = T(ph.mu);
+    const T idx_ = T(1.0 / ph.dx), idy = T(1.0 / ph.dy);
     double m = 0.0;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(e / g.nx), j = (int)(e - (long long)i * g.nx);
         const long long o = (long long)(i + kGhost) * g.pitch + (j + kGhost);
-        const double r = q[o], ir = 1.0 / r;
-        const double u = q[o + g.plane] * ir, v = q[o + 2 * g.plane] * ir;
-        const double p = (ph.gamma - 1.0) * (q[o + 3 * g.plane] - 0.5 * r * (u * u + v * v));
-        const double c = sqrt(ph.gamma * p * ir);
-        double l = fmax((fabs(u) + c) * idx_, (fabs(v) + c) * idy);
-        if (ph.mu > 0.0) {
-            const double nu4 = 4.0 * ph.mu * ir;
-            l = fmax(l, fmax(nu4 * idx_ * idx_, nu4 * idy * idy));
-        }
-        m = fmax(m, l);
+        m = fmax(m, cell_wavespeed<T>(q[o], q[o + g.plane], q[o + 2 * g.plane], q[o + 3 * g.plane], gamma, gm1, mu,
+                                      idx_, idy));
     }
     __shared__ double red[32];
     m = warp_max_d(m);
@@ -135,14 +132,17 @@ __global__ void wavespeed_kernel(const Grid g, const Physics ph, const double* _
 }
 
 cudaError_t launch_wavespeed(const Grid& g, const Physics& ph, const double* q, unsigned long long* lam,
-                             cudaStream_t s)
+                             int precision, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(lam, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const long long n = (long long)g.nx * g.ny;
     int nb = (int)((n + 255) / 256);
     if (nb > 152 * 8) nb = 152 * 8;
-    wavespeed_kernel<<<nb, 256, 0, s>>>(g, ph, q, lam);
+    if (precision == 32)
+        wavespeed_kernel<float><<<nb, 256, 0, s>>>(g, ph, q, lam);
+    else
+        wavespeed_kernel<double><<<nb, 256, 0, s>>>(g, ph, q, lam);
     return cudaGetLastError();
 }
 

@@ -5,6 +5,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/gbr.h"
 #include "ghost.cuh"
 #include "gbr_internal.h"
@@ -136,6 +138,48 @@ int check_errors(gbr_batch* b, std::vector<DevScalars>& h)
     for (const auto& d : h)
         if (d.err & 1u) return GBR_ERR_NONPHYSICAL;
     return GBR_OK;
+}
+
+// Body of gbr_batch_step_cfl (arguments already checked).
+int batch_step_cfl(gbr_batch* b, double cfl, int nsteps)
+{
+    DeviceGuard dg(b->device);
+    int rc = upload(b);
+    if (rc != GBR_OK) return rc;
+    if (!b->graph || b->g_nsteps != nsteps || b->g_cfl != cfl || b->g_precision != b->precision ||
+        b->g_shape != b->shape || b->g_sensor != (sensor_of(b) != nullptr)) {
+        drop_graph(b);
+        // first-use kernel setup outside the capture (a negative tile count
+        // prepares the persistent kernel without launching it)
+        TRY(b->precision == 32 ? launch_batch_stage_f32(b->shape, b->d_cases, b->n, -1, 0, b->stream, sensor_of(b))
+                               : launch_batch_stage_f64(b->shape, b->d_cases, b->n, -1, 0, b->stream));
+        if (sensor_of(b)) TRY(launch_batch_sensor_decide(b->d_cases, b->n, -1, 0, sensor_of(b), b->stream));
+        // The descriptors must be on the device before the capture stream
+        // replays anything: order the capture stream after the caller's.
+        TRY(cudaStreamSynchronize(b->stream));
+        TRY(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
+        int erc = GBR_OK;
+        for (int s = 0; s < nsteps && erc == GBR_OK; ++s) erc = enqueue_step(b, cfl, b->capture);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->capture, &g);
+        if (erc != GBR_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return erc != GBR_OK ? erc : GBR_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            b->graph = nullptr;
+            return st(e);
+        }
+        b->g_nsteps = nsteps;
+        b->g_cfl = cfl;
+        b->g_precision = b->precision;
+        b->g_shape = b->shape;
+        b->g_sensor = sensor_of(b) != nullptr;
+    }
+    return st(cudaGraphLaunch(b->graph, b->stream));
 }
 
 }  // namespace
@@ -278,7 +322,7 @@ int gbr_batch_set_state(gbr_batch* b, int k, const double* Q, int on_device)
                               sizeof(double) * c.g.pitch, Q + (size_t)m * c.g.nx * c.g.ny, sizeof(double) * c.g.nx,
                               sizeof(double) * c.g.nx, c.g.ny, kind, b->stream));
     TRY(cudaMemsetAsync(c.ds, 0, sizeof(DevScalars), b->stream));
-    TRY(launch_wavespeed(c.g, c.ph, c.q[0], &c.ds->lam[0], b->stream));
+    TRY(launch_wavespeed(c.g, c.ph, c.q[0], &c.ds->lam[0], b->precision, b->stream));
     if (!on_device) TRY(cudaStreamSynchronize(b->stream));
     return GBR_OK;
 }
@@ -310,44 +354,12 @@ int gbr_batch_set_end_times(gbr_batch* b, const double* t_end)
 int gbr_batch_step_cfl(gbr_batch* b, double cfl, int nsteps)
 {
     if (!b || !(cfl > 0.0) || nsteps < 1) return GBR_ERR_ARG;
-    DeviceGuard dg(b->device);
-    int rc = upload(b);
-    if (rc != GBR_OK) return rc;
-    if (!b->graph || b->g_nsteps != nsteps || b->g_cfl != cfl || b->g_precision != b->precision ||
-        b->g_shape != b->shape || b->g_sensor != (sensor_of(b) != nullptr)) {
-        drop_graph(b);
-        // first-use kernel setup outside the capture (a negative tile count
-        // prepares the persistent kernel without launching it)
-        TRY(b->precision == 32 ? launch_batch_stage_f32(b->shape, b->d_cases, b->n, -1, 0, b->stream, sensor_of(b))
-                               : launch_batch_stage_f64(b->shape, b->d_cases, b->n, -1, 0, b->stream));
-        if (sensor_of(b)) TRY(launch_batch_sensor_decide(b->d_cases, b->n, -1, 0, sensor_of(b), b->stream));
-        // The descriptors must be on the device before the capture stream
-        // replays anything: order the capture stream after the caller's.
-        TRY(cudaStreamSynchronize(b->stream));
-        TRY(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
-        int erc = GBR_OK;
-        for (int s = 0; s < nsteps && erc == GBR_OK; ++s) erc = enqueue_step(b, cfl, b->capture);
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(b->capture, &g);
-        if (erc != GBR_OK || e != cudaSuccess) {
-            if (g) cudaGraphDestroy(g);
-            cudaGetLastError();
-            return erc != GBR_OK ? erc : GBR_ERR_CUDA;
-        }
-        e = cudaGraphInstantiate(&b->graph, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-            b->graph = nullptr;
-            return st(e);
-        }
-        b->g_nsteps = nsteps;
-        b->g_cfl = cfl;
-        b->g_precision = b->precision;
-        b->g_shape = b->shape;
-        b->g_sensor = sensor_of(b) != nullptr;
-    }
-    return st(cudaGraphLaunch(b->graph, b->stream));
+    nvtxRangePushA("gbr batch steps");
+    const int rc = batch_step_cfl(b, cfl, nsteps);
+    nvtxRangePop();
+    return rc;
 }
+
 
 int gbr_batch_get_times(gbr_batch* b, double* t, double* dt)
 {

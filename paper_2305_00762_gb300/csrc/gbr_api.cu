@@ -9,6 +9,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/gbr.h"
 #include "gbr_internal.h"
 #include "sensor.cuh"
@@ -61,6 +63,13 @@ struct DeviceGuard {  // make the context's device current for one call
     {
         if (prev >= 0) cudaSetDevice(prev);
     }
+};
+
+// NVTX range of a host call (visible in Nsight timelines; a no-op without a
+// profiler attached).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
 };
 
 int cuda_status(cudaError_t e)
@@ -180,6 +189,7 @@ StageParams stage_params(gbr_ctx* c, const double* q)
 
 int stage(gbr_ctx* c, const StageParams& p)
 {
+    Range r("gbr stage");
     Timed tm(c, GBR_KERNEL_STAGE);  // includes the learned sensor's decision pass
     if (c->precision == 32 && p.sensor) {
         StageParams q = p;
@@ -197,6 +207,7 @@ int stage(gbr_ctx* c, const StageParams& p)
 // the device word formed by the first ghost fill.
 int rk3_step(gbr_ctx* c, int mode, double dt, double cfl, double dt_max)
 {
+    Range r("gbr step");
     int rc;
     const double* dt_dev = (mode == 2) ? &c->ds->dt : nullptr;
     if ((rc = ghosts(c, c->Qn, mode, dt, cfl, dt_max)) != GBR_OK) return rc;
@@ -323,7 +334,7 @@ int gbr_set_state(gbr_ctx* c, const double* Q, int on_device)
     c->lam_cur = 0;
     {
         Timed tm(c, GBR_KERNEL_WAVESPEED);
-        GBR_TRY(launch_wavespeed(c->g, c->ph, c->Qn, &c->ds->lam[0], c->stream));
+        GBR_TRY(launch_wavespeed(c->g, c->ph, c->Qn, &c->ds->lam[0], c->precision, c->stream));
     }
     if (!on_device) GBR_TRY(cudaStreamSynchronize(c->stream));
     c->have_state = 1;
@@ -349,6 +360,7 @@ int gbr_get_state(gbr_ctx* c, double* Q, int on_device)
 int gbr_residual(gbr_ctx* c, double* res, int on_device)
 {
     if (!c || !res) return GBR_ERR_ARG;
+    Range r("gbr residual");
     if (!c->have_state) return GBR_ERR_STATE;
     DeviceGuard dg(c->device);
     int rc = ghosts(c, c->Qn, 0, 0, 0, 0);

@@ -141,8 +141,8 @@ cudaError_t launch_batch_sensor_decide(const BatchCase* cases, int ncases, int t
 cudaError_t launch_sensor_train(const void* X_bf16, const unsigned char* y, long long n, int steps, int batch,
                                 float lr, float pos_weight, unsigned long long seed, float* w, float* grad, float* m,
                                 float* v, float* loss, cudaStream_t s);
-cudaError_t launch_wavespeed(const Grid& g, const Physics& ph, const double* q,
-                             unsigned long long* lam, cudaStream_t s);
+cudaError_t launch_wavespeed(const Grid& g, const Physics& ph, const double* q, unsigned long long* lam,
+                             int precision, cudaStream_t s);
 cudaError_t launch_stage_f64(const StageParams& p, cudaStream_t s);
 cudaError_t launch_stage_f32(const StageParams& p, cudaStream_t s);
 cudaError_t launch_stage_cons_f64(const StageParams& p, cudaStream_t s);

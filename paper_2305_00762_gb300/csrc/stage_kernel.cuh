@@ -169,6 +169,26 @@ __device__ __forceinline__ void prims_of(double q0, double q1, double q2, double
     p = gm1 * rfma(-rmul(T(0.5), r), sumsq(u, v), T(q3));
 }
 
+// Sec. 2.5: CFL wavespeed of one cell state, max((|u| + c)/dx, (|v| + c)/dy)
+// (and the viscous bound 4 nu / dx^2 when mu > 0), in T. Every operation is
+// contraction-free or explicitly rounded, so the stage epilogue and the
+// standalone reduction give the same bits (a resumed run picks the same dt).
+template <typename T>
+__device__ __forceinline__ double cell_wavespeed(double q0, double q1, double q2, double q3, T gamma, T gm1, T mu,
+                                                 T inv_dx, T inv_dy)
+{
+    T r, u, v, p;
+    prims_of(q0, q1, q2, q3, gm1, r, u, v, p);
+    const T ir = T(1) / r;
+    const T cs = tsqrt(gamma * p * ir);
+    T l = tmax((tabs(u) + cs) * inv_dx, (tabs(v) + cs) * inv_dy);
+    if (mu > T(0)) {
+        const T nu4 = T(4) * mu * ir;
+        l = tmax(l, tmax(nu4 * inv_dx * inv_dx, nu4 * inv_dy * inv_dy));
+    }
+    return double(l);
+}
+
 // Eq. six: dx-scaled sixth-order gradient at s[0] along stride st.
 template <typename T>
 __device__ __forceinline__ T grad6(const T* s, int st)
@@ -1076,18 +1096,9 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
             const bool ok = isfinite(qv[0]) && isfinite(qv[1]) && isfinite(qv[2]) && isfinite(qv[3]) &&
                             qv[0] > 0.0 && 2.0 * qv[0] * qv[3] - (qv[1] * qv[1] + qv[2] * qv[2]) > 0.0;
             bad |= !ok;
-            if (P.lam_out) {  // Sec. 2.5 wavespeed of the new state
-                const T r = T(qv[0]), ir = T(1) / r;
-                const T u = T(qv[1]) * ir, v = T(qv[2]) * ir;
-                const T p = ph.gm1 * (T(qv[3]) - T(0.5) * r * sumsq(u, v));
-                const T cs = tsqrt(ph.gamma * p * ir);
-                T l = tmax((tabs(u) + cs) * inv_dx, (tabs(v) + cs) * inv_dy);
-                if (P.ph.mu > 0.0) {
-                    const T nu4 = T(4) * ph.mu * ir;
-                    l = tmax(l, tmax(nu4 * inv_dx * inv_dx, nu4 * inv_dy * inv_dy));
-                }
-                lam = fmax(lam, double(l));
-            }
+            if (P.lam_out)  // Sec. 2.5 wavespeed of the new state
+                lam = fmax(lam, cell_wavespeed<T>(qv[0], qv[1], qv[2], qv[3], ph.gamma, ph.gm1, ph.mu, inv_dx,
+                                                  inv_dy));
         }
     }
     if (P.qout) {

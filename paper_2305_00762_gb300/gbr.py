@@ -308,6 +308,11 @@ class Solver:
     def __init__(self, nx, ny, dx, dy, gamma=1.4, mu=0.0, Pr=0.72, bc=(GBR_BC_PERIODIC,) * 4,
                  precision=64, stream=None, order=7, cons=False):
         self.nx, self.ny = int(nx), int(ny)
+        # construction arguments and custom sides, kept for checkpoints
+        self.params = {"nx": int(nx), "ny": int(ny), "dx": float(dx), "dy": float(dy), "gamma": float(gamma),
+                       "mu": float(mu), "Pr": float(Pr), "bc": tuple(int(k) for k in bc),
+                       "precision": int(precision), "order": int(order), "cons": bool(cons)}
+        self.sides = [None] * 4
         self.ctx = gbr_create(nx, ny, gamma, mu, Pr, bc, dx, dy)
         if stream is not None:
             gbr_set_stream(self.ctx, stream)
@@ -323,8 +328,13 @@ class Solver:
         s = cls(case.nx, case.ny, case.dx, case.dy, case.gamma, case.mu, case.Pr, case.bc, **kw)
         for k, sd in enumerate((case.meta or {}).get("sides", (None,) * 4)):
             if sd is not None:
-                gbr_set_side(s.ctx, k, *sd)
+                s.set_side(k, *sd)
         return s
+
+    def set_side(self, k, kind_lo, kind_hi, s0=0.0, speed=0.0, lo=(1.0, 0.0, 0.0, 1.0), hi=(1.0, 0.0, 0.0, 1.0)):
+        gbr_set_side(self.ctx, k, kind_lo, kind_hi, s0, speed, lo, hi)
+        self.sides[k] = (int(kind_lo), int(kind_hi), float(s0), float(speed), tuple(map(float, lo)),
+                         tuple(map(float, hi)))
 
     def close(self):
         if self.ctx is not None:

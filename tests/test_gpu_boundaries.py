@@ -104,3 +104,31 @@ def test_double_mach_paper_grid(env, cons):
         assert abs(xc[j] - xs) < 2 * c.dx, (yc[i], xc[j], xs)
     print(f"double Mach {'cons' if cons else 'prim'} 1024x256 to t=0.2: {steps} steps, {wall:.2f} s "
           f"(host loop with a time read per step), rho in [{Q[0].min():.3f}, {Q[0].max():.3f}]")
+
+
+def test_checkpoint_resume_is_bitwise(env, tmp_path):
+    """Ten CFL steps of the double Mach reflection in one run, against five
+    steps, a checkpoint file, a new solver resumed from it and five more
+    steps: identical to the last bit (state and time)."""
+    torch, O, gbr = env
+    from paper_2305_00762_gb300 import checkpoint
+    c = C.double_mach(96, 24)
+    a = gbr.Solver.for_case(c, cons=True)
+    a.set_state(c.Q)
+    for _ in range(10):
+        a.step_cfl(0.5)
+    Qa, ta = a.get_state(), a.time()
+    a.close()
+    b = gbr.Solver.for_case(c, cons=True)
+    b.set_state(c.Q)
+    for _ in range(5):
+        b.step_cfl(0.5)
+    path = str(tmp_path / "dmr.npz")
+    checkpoint.save(b, path, step=5)
+    b.close()
+    r, step = checkpoint.resume(path)
+    assert step == 5
+    for _ in range(5):
+        r.step_cfl(0.5)
+    assert np.array_equal(r.get_state(), Qa) and r.time() == ta
+    r.close()
