@@ -1119,9 +1119,19 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
 }
 
 // One CTA per tile; the tile + halo is staged by a tensor copy described by
-// tmap (the stage's input state, see encode_state_map).
+// tmap (the stage's input state, see encode_state_map). Each instance is
+// held to the register budget of the CTAs per SM that its shared memory
+// allows (FP64: 2, 1 for MEG7-cons; FP32: 3, 2 viscous or MEG7-cons): small
+// source changes could otherwise push the allocation over the budget and cut
+// the resident warps.
+template <typename T, bool VISC, bool CONS>
+constexpr int stage_min_blocks()
+{
+    return sizeof(T) == 8 ? (CONS ? 1 : 2) : ((VISC || CONS) ? 2 : 3);
+}
+
 template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED, int ORDER, bool CONS>
-__global__ void __launch_bounds__(NT) stage_kernel(const StageParams P, const __grid_constant__ CUtensorMap tmap)
+__global__ void __launch_bounds__(NT, stage_min_blocks<T, VISC, CONS>()) stage_kernel(const StageParams P, const __grid_constant__ CUtensorMap tmap)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     stage_tile<T, BX, BY, NT, VISC, LEARNED, ORDER, CONS, true>(P, blockIdx.x * BX, blockIdx.y * BY, smem_raw,
