@@ -69,6 +69,7 @@ def peaks():
 # of the plain smooth-region path comes from paper_2305_00762_gb300.costs,
 # which derives it term by term.
 FP64_PEAK_GFLOPS = 1250.0     # GB300 FP64 (non-tensor) nominal, 152 SMs
+FP32_PEAK_GFLOPS = 80550.0    # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
 # DRAM bytes (read + write) per launch of the FP64 stage kernel on the default
 # 1024^2 workload, mean over the three stages of a step, from an ncu capture of
 # `bench.py --steps 3 --warmup 1 --no-cpu-baseline --no-ensemble --no-4096 --profile`
@@ -482,6 +483,9 @@ def main():
                       "stage_ms_avg": r32["timing"]["stage"][0] / max(r32["timing"]["stage"][1], 1),
                       "hbm_frac": bytes_cell * cells / (r32["timing"]["stage"][0] /
                                                         max(r32["timing"]["stage"][1], 1) * 1e-3) / 1e9 / hbm_peak,
+                      "alu_frac_fp32": flop_cell * cells / (r32["timing"]["stage"][0] /
+                                                            max(r32["timing"]["stage"][1], 1) * 1e-3) / 1e9
+                      / FP32_PEAK_GFLOPS,
                       "clocks": r32["clocks"],
                       "density_l1_vs_fp64_20_steps": acc.get((32, False))},
         "e2e": {"value": e2e_rate, "unit": METRIC,

@@ -292,7 +292,9 @@ typedef struct gbr_batch gbr_batch; /* opaque, library-owned */
 
 /* Create a batch of n >= 1 grids: grid k has nx[k] x ny[k] interior cells
  * (>= GBR_GHOST), cell sizes dx[k], dy[k] > 0 and boundary kinds
- * bc[4k .. 4k+3] (west, east, south, north); all share gamma > 1 (inviscid).
+ * bc[4k .. 4k+3] (west, east, south, north: GBR_BC_PERIODIC to
+ * GBR_BC_SYMMETRY; custom sides are for single-grid solvers only); all share
+ * gamma > 1 (inviscid).
  * Host arrays, read during the call only. Precision defaults to 64. */
 int gbr_batch_create(int n, const int *nx, const int *ny, const double *dx, const double *dy, const int *bc,
                      double gamma, gbr_batch **out);
