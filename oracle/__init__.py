@@ -68,7 +68,8 @@ class _Cfg(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("mu", ctypes.c_double),
                 ("Pr", ctypes.c_double), ("bc", ctypes.c_int * 4),
                 ("order", ctypes.c_int), ("cons", ctypes.c_int),
-                ("t", ctypes.c_double), ("side", _Side * 4)]
+                ("t", ctypes.c_double), ("side", _Side * 4),
+                ("riemann", ctypes.c_int)]
 
 
 def lib():
@@ -94,8 +95,9 @@ def lib():
                          "or_flux_recon4_left", "or_psi"):
                 getattr(L, name).restype = ctypes.c_double
                 getattr(L, name).argtypes = [dp]
-            L.or_hllc.restype = None
-            L.or_hllc.argtypes = [ctypes.c_double, dp, dp, dp, dp, dp]
+            for name in ("or_hllc", "or_hllc_lm"):
+                getattr(L, name).restype = None
+                getattr(L, name).argtypes = [ctypes.c_double, dp, dp, dp, dp, dp]
             L.or_residual.restype = ctypes.c_int
             L.or_residual.argtypes = [cp, dp, dp, u8, u8, u8]
             L.or_rk3_step.restype = ctypes.c_int
@@ -149,6 +151,7 @@ class Config:
     t: float = 0.0                   # time of the state (moving custom sides)
     # per side: None, or (kind_lo, kind_hi, s0, speed, lo (rho,u,v,p), hi) for BC_CUSTOM sides
     sides: tuple = (None, None, None, None)
+    riemann: int = 0                 # 1: shock-stable HLLC-LM (reading R24)
 
     def c(self) -> _Cfg:
         sides = (_Side * 4)()
@@ -159,7 +162,8 @@ class Config:
             else:
                 sides[k] = _Side(BC_TRANSMISSIVE, BC_TRANSMISSIVE, 0.0, 0.0)
         return _Cfg(self.nx, self.ny, self.dx, self.dy, self.gamma, self.mu,
-                    self.Pr, (ctypes.c_int * 4)(*self.bc), self.order, self.cons, self.t, sides)
+                    self.Pr, (ctypes.c_int * 4)(*self.bc), self.order, self.cons, self.t, sides,
+                    self.riemann)
 
 
 # ---- scalar building blocks (pins) ----------------------------------------
@@ -205,10 +209,11 @@ def psi(rho5):
     return lib().or_psi(_dp(_vec(rho5, 5)))
 
 
-def hllc(gamma, WL, WR, FL, FR):
+def hllc(gamma, WL, WR, FL, FR, lm=False):
+    """HLLC face flux (reading R7), or the shock-stable HLLC-LM (R24) if lm."""
     out = np.zeros(4)
-    lib().or_hllc(float(gamma), _dp(_vec(WL, 4)), _dp(_vec(WR, 4)),
-                  _dp(_vec(FL, 4)), _dp(_vec(FR, 4)), _dp(out))
+    f = lib().or_hllc_lm if lm else lib().or_hllc
+    f(float(gamma), _dp(_vec(WL, 4)), _dp(_vec(WR, 4)), _dp(_vec(FL, 4)), _dp(_vec(FR, 4)), _dp(out))
     return out
 
 

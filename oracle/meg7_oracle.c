@@ -51,6 +51,13 @@
  *      Mach reflection (Example 8) reconstructs a negative pressure at the
  *      shock's foot in its first step without it. States that stay positive
  *      are untouched.
+ *  R24 shock-stable HLLC (Examples 7 and 8 cite Fleischmann, Adami and Adams
+ *      2020 without restating it): the HLLC-LM flux of that work, in the
+ *      |A| form of R7. The acoustic terms |S_L|(Q*_L-Q_L) and |S_R|(Q_R-Q*_R)
+ *      are scaled by phi = sin(pi/2 min(1, Ma/Ma_lim)), Ma = max(|u_L|/c_L,
+ *      |u_R|/c_R) with the face-normal velocities, Ma_lim = 0.1; S_L, S_R,
+ *      S* and the star states are those of R7. phi = 1 (Ma >= Ma_lim, every
+ *      supersonic face) gives R7 exactly.
  *  R23 time-dependent boundaries: the RK stages of a step from t with step
  *      dt see the boundary at t, t + dt and t + dt/2 (Eq. rk's stage times).
  *  R20 MEG7-cons (Sec. 2.2, conservative reconstruction): Q and its
@@ -97,7 +104,11 @@ typedef struct {
     int cons;                 /* 0 = MEG7-prim (reconstruct U), 1 = MEG7-cons (reconstruct Q) */
     double t;                 /* time of the state (custom sides may move with it) */
     or_side side[4];          /* descriptions of OR_BC_CUSTOM sides */
+    int riemann;              /* 0 = HLLC (R7), 1 = shock-stable HLLC-LM (R24) */
 } or_cfg;
+
+#define OR_MA_LIMIT 0.1               /* Ma_lim of reading R24 */
+#define OR_HALF_PI 1.5707963267948966 /* pi / 2 rounded to double */
 
 /* ---------------------------------------------------------------------- */
 /* Scalar building blocks, each one equation of the paper.                 */
@@ -292,10 +303,12 @@ static void euler_flux(double gamma, const double *w, double *f)
     f[3] = w[1] * (q[3] + w[3]);
 }
 
-/* Eq. Riemann_revisit with HLLC (reading R7). WL, WR: primitive left/right
- * face states (rho, un, ut, p); FL, FR: the face fluxes that enter the central
- * part (hybrid F^c_L, F^c_R). Writes the numerical flux Fh. */
-void or_hllc(double gamma, const double *WL, const double *WR, const double *FL, const double *FR, double *Fh)
+/* Eq. Riemann_revisit with HLLC (reading R7), or with the HLLC-LM flux of
+ * reading R24 if lm != 0. WL, WR: primitive left/right face states
+ * (rho, un, ut, p); FL, FR: the face fluxes that enter the central part
+ * (hybrid F^c_L, F^c_R). Writes the numerical flux Fh. */
+static void hllc_face(double gamma, int lm, const double *WL, const double *WR, const double *FL, const double *FR,
+                      double *Fh)
 {
     double QL[4], QR[4];
     prim_to_cons(gamma, WL, QL);
@@ -325,10 +338,29 @@ void or_hllc(double gamma, const double *WL, const double *WR, const double *FL,
     QsR[1] = kR * Ss;
     QsR[2] = kR * vR;
     QsR[3] = kR * (QR[3] / rR + (Ss - uR) * (Ss + pR / (rR * (SR - uR))));
+    /* reading R24: the acoustic wave speeds of the dissipation scaled by phi */
+    double aL = fabs(SL), aR = fabs(SR);
+    if (lm) {
+        double Ma = fmax(fabs(uL) / cL, fabs(uR) / cR);
+        double z = fmin(1.0, Ma / OR_MA_LIMIT);
+        double phi = z < 1.0 ? sin(OR_HALF_PI * z) : 1.0;
+        aL *= phi;
+        aR *= phi;
+    }
     for (int m = 0; m < 4; ++m) {
-        double adq = fabs(SL) * (QsL[m] - QL[m]) + fabs(Ss) * (QsR[m] - QsL[m]) + fabs(SR) * (QR[m] - QsR[m]);
+        double adq = aL * (QsL[m] - QL[m]) + fabs(Ss) * (QsR[m] - QsL[m]) + aR * (QR[m] - QsR[m]);
         Fh[m] = 0.5 * (FL[m] + FR[m]) - 0.5 * adq;
     }
+}
+
+void or_hllc(double gamma, const double *WL, const double *WR, const double *FL, const double *FR, double *Fh)
+{
+    hllc_face(gamma, 0, WL, WR, FL, FR, Fh);
+}
+
+void or_hllc_lm(double gamma, const double *WL, const double *WR, const double *FL, const double *FR, double *Fh)
+{
+    hllc_face(gamma, 1, WL, WR, FL, FR, Fh);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -607,7 +639,7 @@ static void face_flux(const or_cfg *c, const double *const P[4], const double *c
         euler_flux(g, UL, FL);
         euler_flux(g, UR, FR);
     }
-    or_hllc(g, UL, UR, FL, FR, Fh);
+    hllc_face(g, c->riemann, UL, UR, FL, FR, Fh);
 
     if (c->mu > 0.0) {
         /* Sec. 2.1 with reading R8. T = gamma p / rho and its dx-scaled
@@ -666,6 +698,8 @@ static int cfg_ok(const or_cfg *c)
     if (c->order != 7 && c->order != 4)
         return 0;
     if (c->cons != 0 && c->cons != 1)
+        return 0;
+    if (c->riemann != 0 && c->riemann != 1)
         return 0;
     for (int k = 0; k < 4; ++k) {
         if (c->bc[k] < 0 || c->bc[k] > OR_BC_CUSTOM)
