@@ -98,7 +98,7 @@ extern "C" int gbr_step_static(const double* Q_in, double* Q_out, int nx, int ny
     double* Q1 = Qn + 4 * g.plane;
     double* Q2 = Q1 + 4 * g.plane;
 
-    Physics ph;
+    Physics ph{};  // value-initialised: MEG7-prim, HLLC
     ph.gamma = gamma;
     ph.mu = mu;
     ph.Pr = Pr;
