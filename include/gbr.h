@@ -132,7 +132,15 @@ typedef enum {
      * bounded staging wait gives up (after a few seconds) and the next
      * synchronising call reports GBR_ERR_TIMEOUT; the copy itself completes,
      * nothing faults, and gbr_set_state clears the error. 0: off (default). */
-    GBR_OPT_STALL_TEST = 6
+    GBR_OPT_STALL_TEST = 6,
+    /* Riemann solver of Eq. Riemann_revisit: 0 = HLLC (default); 1 = the
+     * shock-stable HLLC of Fleischmann, Adami and Adams (2020), which
+     * Examples 7 and 8 use against the carbuncle: the HLLC-LM flux, whose
+     * acoustic terms |S_L|(Q*_L - Q_L) and |S_R|(Q_R - Q*_R) are scaled by
+     * phi = sin(pi/2 min(1, Ma / 0.1)), Ma = max(|u_L|/c_L, |u_R|/c_R) over
+     * the face-normal velocities. Faces at Ma >= 0.1 (every supersonic face)
+     * keep plain HLLC. All precisions and reconstructions; batches too. */
+    GBR_OPT_RIEMANN = 7
 } gbr_option;
 
 /* Kernel classes reported by gbr_get_timing. */
@@ -305,8 +313,8 @@ int gbr_batch_destroy(gbr_batch *b);
 /* Issue all later work of the batch on `stream` (NULL = legacy default). */
 int gbr_batch_set_stream(gbr_batch *b, void *stream);
 
-/* GBR_OPT_PRECISION (64 or 32, as for a single grid), GBR_OPT_SENSOR or
- * GBR_OPT_TIMING. */
+/* GBR_OPT_PRECISION (64 or 32, as for a single grid), GBR_OPT_SENSOR,
+ * GBR_OPT_TIMING or GBR_OPT_RIEMANN (for every case). */
 int gbr_batch_set_option(gbr_batch *b, int key, double val);
 
 /* Set grid k's state ([4][ny_k][nx_k] float64); resets its time to 0 and

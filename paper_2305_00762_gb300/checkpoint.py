@@ -33,7 +33,8 @@ def resume(path: str, stream=None) -> tuple:
     """A solver positioned at the checkpoint, and the checkpoint's step count."""
     Q, h = load(path)
     s = gbr.Solver(h["nx"], h["ny"], h["dx"], h["dy"], h["gamma"], h["mu"], h["Pr"], tuple(h["bc"]),
-                   precision=h["precision"], stream=stream, order=h["order"], cons=h["cons"])
+                   precision=h["precision"], stream=stream, order=h["order"], cons=h["cons"],
+                   riemann=h.get("riemann", 0))
     for k, sd in enumerate(h["sides"]):
         if sd is not None:
             s.set_side(k, *sd)

@@ -308,6 +308,12 @@ int gbr_batch_set_option(gbr_batch* b, int key, double val)
         b->timing = (int)val;
         return GBR_OK;
     }
+    if (key == GBR_OPT_RIEMANN) {  // every case; the descriptors go up before the next launch
+        if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;
+        for (BatchCase& c : b->cases) c.ph.riemann = (int)val;
+        b->dirty = true;
+        return GBR_OK;
+    }
     return GBR_ERR_ARG;
 }
 

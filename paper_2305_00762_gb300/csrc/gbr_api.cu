@@ -494,6 +494,10 @@ int gbr_set_option(gbr_ctx* c, int key, double val)
         if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;
         c->stall_test = (int)val;
         return GBR_OK;
+    case GBR_OPT_RIEMANN:
+        if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;
+        c->ph.riemann = (int)val;
+        return GBR_OK;
     case GBR_OPT_TIMING:
         if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;
         c->timing = (int)val;

@@ -40,6 +40,7 @@ struct Physics {
     double gamma, mu, Pr, dx, dy;
     int order;  // 7: MEG7 (alpha = 38/7, beta = 3/190); 4: the alpha = 4, beta = 0 member
     int cons;   // 0: MEG7-prim (reconstruct U); 1: MEG7-cons (reconstruct Q)
+    int riemann;  // 0: HLLC; 1: shock-stable HLLC-LM (Fleischmann et al. 2020)
 };
 
 struct SensorDev;

@@ -21,7 +21,7 @@ GBR_ERR_TIMEOUT, GBR_ERR_STATE, GBR_ERR_NOMEM, GBR_ERR_UNSUPPORTED = -4, -5, -6,
 GBR_BC_PERIODIC, GBR_BC_TRANSMISSIVE, GBR_BC_NOSLIP_WALL, GBR_BC_SYMMETRY = 0, 1, 2, 3
 GBR_BC_CUSTOM, GBR_BC_FIXED = 4, 5
 GBR_OPT_PRECISION, GBR_OPT_RECORD_FLAGS, GBR_OPT_SENSOR, GBR_OPT_TIMING, GBR_OPT_ORDER = 0, 1, 2, 3, 4
-GBR_OPT_VARIABLES, GBR_OPT_STALL_TEST = 5, 6
+GBR_OPT_VARIABLES, GBR_OPT_STALL_TEST, GBR_OPT_RIEMANN = 5, 6, 7
 GBR_KERNEL_STAGE, GBR_KERNEL_GHOST, GBR_KERNEL_WAVESPEED, GBR_KERNEL_CLASSES = 0, 1, 2, 3
 GBR_GHOST = 6
 GBR_STATIC_SCRATCH_DOUBLES = 1 << 20
@@ -306,12 +306,13 @@ class Solver:
     """Convenience owner of one gbr context (marshalling only)."""
 
     def __init__(self, nx, ny, dx, dy, gamma=1.4, mu=0.0, Pr=0.72, bc=(GBR_BC_PERIODIC,) * 4,
-                 precision=64, stream=None, order=7, cons=False):
+                 precision=64, stream=None, order=7, cons=False, riemann=0):
         self.nx, self.ny = int(nx), int(ny)
         # construction arguments and custom sides, kept for checkpoints
         self.params = {"nx": int(nx), "ny": int(ny), "dx": float(dx), "dy": float(dy), "gamma": float(gamma),
                        "mu": float(mu), "Pr": float(Pr), "bc": tuple(int(k) for k in bc),
-                       "precision": int(precision), "order": int(order), "cons": bool(cons)}
+                       "precision": int(precision), "order": int(order), "cons": bool(cons),
+                       "riemann": int(riemann)}
         self.sides = [None] * 4
         self.ctx = gbr_create(nx, ny, gamma, mu, Pr, bc, dx, dy)
         if stream is not None:
@@ -322,6 +323,8 @@ class Solver:
             gbr_set_option(self.ctx, GBR_OPT_ORDER, order)
         if cons:
             gbr_set_option(self.ctx, GBR_OPT_VARIABLES, 1)
+        if riemann:
+            gbr_set_option(self.ctx, GBR_OPT_RIEMANN, riemann)
 
     @classmethod
     def for_case(cls, case, **kw):

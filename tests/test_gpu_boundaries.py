@@ -71,15 +71,17 @@ def test_custom_sides_parity(env, name, make, cons):
     s.close()
 
 
-@pytest.mark.parametrize("cons", [False, True], ids=["prim", "cons"])
-def test_double_mach_paper_grid(env, cons):
-    """1024 x 256 to t = 0.2 (Example 8): positive throughout, and the
-    incident shock, away from the wall, within two cells of its exact
-    position x_s(y, t) = 1/6 + (y + 20 t)/sqrt(3) on rows y in [0.6, 0.95]."""
+@pytest.mark.parametrize("cons,riemann", [(False, 0), (True, 0), (False, 1), (True, 1)],
+                         ids=["prim", "cons", "prim-lm", "cons-lm"])
+def test_double_mach_paper_grid(env, cons, riemann):
+    """1024 x 256 to t = 0.2 (Example 8, with HLLC and with the shock-stable
+    HLLC-LM the example names): positive throughout, and the incident shock,
+    away from the wall, within two cells of its exact position
+    x_s(y, t) = 1/6 + (y + 20 t)/sqrt(3) on rows y in [0.6, 0.95]."""
     torch, O, gbr = env
     import time
     c = C.double_mach(1024, 256)
-    s = gbr.Solver.for_case(c, cons=cons)
+    s = gbr.Solver.for_case(c, cons=cons, riemann=riemann)
     s.set_state(c.Q)
     steps = 0
     t0 = time.perf_counter()
@@ -102,7 +104,7 @@ def test_double_mach_paper_grid(env, cons):
         j = np.nonzero(Q[0, i] < 0.5 * (8.0 + 1.4))[0][0]
         xs = 1.0 / 6.0 + (yc[i] + 20.0 * 0.2) / np.sqrt(3.0)
         assert abs(xc[j] - xs) < 2 * c.dx, (yc[i], xc[j], xs)
-    print(f"double Mach {'cons' if cons else 'prim'} 1024x256 to t=0.2: {steps} steps, {wall:.2f} s "
+    print(f"double Mach {'cons' if cons else 'prim'}{'-lm' if riemann else ''} 1024x256 to t=0.2: {steps} steps, {wall:.2f} s "
           f"(host loop with a time read per step), rho in [{Q[0].min():.3f}, {Q[0].max():.3f}]")
 
 

@@ -139,37 +139,17 @@ def test_hllc_lm_grid_invariants(oracle_mod):
         assert abs(R[m].sum()) <= 1e-13 * np.abs(R[m]).sum()
 
 
-def _quirk_state(nx, ny, mach, rng):
-    """A Mach `mach` shock at x = 10 cells moving into gas at rest
-    (rho 1.4, p 1), Rankine-Hugoniot post-shock state behind it, and 1e-6
-    seeded density noise ahead of it: the odd-even decoupling problem of
-    Quirk (1994) on a uniform grid."""
-    r1, p1 = 1.4, 1.0
-    m2 = mach * mach
-    r2 = r1 * (G + 1) * m2 / ((G - 1) * m2 + 2)
-    p2 = p1 * (2 * G * m2 - (G - 1)) / (G + 1)
-    u2 = mach * np.sqrt(G * p1 / r1) * (1 - r1 / r2)
-    W = np.zeros((4, ny, nx))
-    W[0], W[3] = r1, p1
-    W[0][:, :10], W[1][:, :10], W[3][:, :10] = r2, u2, p2
-    W[0][:, 10:] *= 1 + 1e-6 * rng.standard_normal((ny, nx - 10))
-    Q = np.empty_like(W)
-    Q[0], Q[1], Q[2] = W[0], W[0] * W[1], W[0] * W[2]
-    Q[3] = W[3] / (G - 1) + 0.5 * W[0] * (W[1] ** 2 + W[2] ** 2)
-    return Q
-
-
 def test_hllc_lm_suppresses_odd_even_decoupling(oracle_mod):
-    """The reason Examples 7 and 8 switch solvers: behind a grid-aligned Mach 6
-    shock, plain HLLC amplifies 1e-6 noise into O(1e-2) row-to-row density
-    differences within 200 steps, HLLC-LM keeps them two orders smaller."""
+    """The reason Examples 7 and 8 switch solvers (Quirk's odd-even
+    decoupling problem): behind a grid-aligned Mach 6 shock, plain HLLC
+    amplifies 1e-6 density noise into O(1e-2) row-to-row density differences
+    within 200 steps, HLLC-LM keeps them two orders smaller."""
     O = oracle_mod
-    nx, ny = 160, 16
-    Q0 = _quirk_state(nx, ny, 6.0, np.random.default_rng(94))
+    case = C.odd_even_shock(160, 16, mach=6.0, seed=94)
     dev = {}
     for rm in (0, 1):
-        c = O.Config(nx, ny, 1.0, 1.0, G, 0.0, 0.72, (1, 1, 3, 3), 7, riemann=rm)
-        q = Q0
+        c = _cfg(O, case, rm)
+        q = case.Q
         for _ in range(200):
             q, rc = O.rk3_step(c, q, 0.5 / O.max_wavespeed(c, q))
             assert rc == 0
