@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fp_convert.cuh"
 #include "gbr_internal.h"
 #include "sensor.cuh"
 
@@ -164,11 +165,11 @@ __device__ __forceinline__ T sumsq(T a, T b) { return rmul(a, a) + rmul(b, b); }
 template <typename T>
 __device__ __forceinline__ void prims_of(double q0, double q1, double q2, double q3, T gm1, T& r, T& u, T& v, T& p)
 {
-    r = T(q0);
+    r = from_f64<T>(q0);
     const T ir = T(1) / r;
-    u = T(q1) * ir;
-    v = T(q2) * ir;
-    p = gm1 * rfma(-rmul(T(0.5), r), sumsq(u, v), T(q3));
+    u = from_f64<T>(q1) * ir;
+    v = from_f64<T>(q2) * ir;
+    p = gm1 * rfma(-rmul(T(0.5), r), sumsq(u, v), from_f64<T>(q3));
 }
 
 // Sec. 2.5: CFL wavespeed of one cell state, max((|u| + c)/dx, (|v| + c)/dy)
@@ -176,8 +177,8 @@ __device__ __forceinline__ void prims_of(double q0, double q1, double q2, double
 // contraction-free or explicitly rounded, so the stage epilogue and the
 // standalone reduction give the same bits (a resumed run picks the same dt).
 template <typename T>
-__device__ __forceinline__ double cell_wavespeed(double q0, double q1, double q2, double q3, T gamma, T gm1, T mu,
-                                                 T inv_dx, T inv_dy)
+__device__ __forceinline__ T cell_wavespeed_t(double q0, double q1, double q2, double q3, T gamma, T gm1, T mu,
+                                              T inv_dx, T inv_dy)
 {
     T r, u, v, p;
     prims_of(q0, q1, q2, q3, gm1, r, u, v, p);
@@ -188,7 +189,25 @@ __device__ __forceinline__ double cell_wavespeed(double q0, double q1, double q2
         const T nu4 = T(4) * mu * ir;
         l = tmax(l, tmax(nu4 * inv_dx * inv_dx, nu4 * inv_dy * inv_dy));
     }
-    return double(l);
+    return l;
+}
+template <typename T>
+__device__ __forceinline__ double cell_wavespeed(double q0, double q1, double q2, double q3, T gamma, T gm1, T mu,
+                                                 T inv_dx, T inv_dy)
+{
+    return to_f64(cell_wavespeed_t<T>(q0, q1, q2, q3, gamma, gm1, mu, inv_dx, inv_dy));
+}
+// max with fmax semantics (a NaN operand is ignored), in T
+__device__ __forceinline__ double tmax_nan(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float tmax_nan(float a, float b) { return fmaxf(a, b); }
+
+// IEEE predicates of an FP64 value from its bits (integer pipes):
+// finite, and 0 < x (NaN excluded, +inf included).
+__device__ __forceinline__ bool finite_bits(double x) { return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000; }
+__device__ __forceinline__ bool positive_bits(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b <= 0x7ff0000000000000LL;
 }
 
 // Eq. six: dx-scaled sixth-order gradient at s[0] along stride st.
@@ -816,9 +835,9 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         sU[3 * NU + idx] = p;
         if constexpr (CONS) {
             sQc[idx] = r;
-            sQc[NU + idx] = T(q1);
-            sQc[2 * NU + idx] = T(q2);
-            sQc[3 * NU + idx] = T(q3);
+            sQc[NU + idx] = from_f64<T>(q1);
+            sQc[2 * NU + idx] = from_f64<T>(q2);
+            sQc[3 * NU + idx] = from_f64<T>(q3);
         }
     };
     bool staged = false;
@@ -1082,7 +1101,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
     // Phase 3: residual (Eq. deriv) and the FP64 stage update (Eq. rk).
     const double dt = P.dt_ptr ? *P.dt_ptr : P.dt;
     const double cdt = P.cc * dt;
-    double lam = 0.0;
+    T lam = T(0);  // max in T, widened once (the same value as widening each cell's)
     bool bad = false;
     for (int idx = tid; idx < BX * BY; idx += NT) {
         const int r = idx / BX, c = idx - r * BX;
@@ -1093,7 +1112,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         for (int m = 0; m < 4; ++m) {
             const T dF = sHX[m * L::NHX + r * L::HXW + c + 1] - sHX[m * L::NHX + r * L::HXW + c];
             const T dG = sHY[m * L::NHY + (r + 1) * BX + c] - sHY[m * L::NHY + r * BX + c];
-            res[m] = double(-(rmul(dF, inv_dx) + rmul(dG, inv_dy)));
+            res[m] = to_f64(-(rmul(dF, inv_dx) + rmul(dG, inv_dy)));
         }
         if (P.res) {
 #pragma unroll
@@ -1110,13 +1129,15 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
             }
 #pragma unroll
             for (int m = 0; m < 4; ++m) P.qout[o + m * plane] = qv[m];
-            // Positivity in FP64: rho > 0 and p > 0 <=> 2 rho E > |rho u|^2.
-            const bool ok = isfinite(qv[0]) && isfinite(qv[1]) && isfinite(qv[2]) && isfinite(qv[3]) &&
-                            qv[0] > 0.0 && 2.0 * qv[0] * qv[3] - (qv[1] * qv[1] + qv[2] * qv[2]) > 0.0;
+            // Positivity in FP64: rho > 0 and p > 0 <=> 2 rho E > |rho u|^2
+            // (the comparisons on the bits, off the FP64 pipe).
+            const double e2 = 2.0 * qv[0] * qv[3] - (qv[1] * qv[1] + qv[2] * qv[2]);
+            const bool ok = finite_bits(qv[0]) && finite_bits(qv[1]) && finite_bits(qv[2]) && finite_bits(qv[3]) &&
+                            positive_bits(qv[0]) && positive_bits(e2);
             bad |= !ok;
             if (P.lam_out)  // Sec. 2.5 wavespeed of the new state
-                lam = fmax(lam, cell_wavespeed<T>(qv[0], qv[1], qv[2], qv[3], ph.gamma, ph.gm1, ph.mu, inv_dx,
-                                                  inv_dy));
+                lam = tmax_nan(lam, cell_wavespeed_t<T>(qv[0], qv[1], qv[2], qv[3], ph.gamma, ph.gm1, ph.mu,
+                                                        inv_dx, inv_dy));
         }
     }
     if (P.qout) {
@@ -1124,8 +1145,8 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
     }
     if (P.lam_out) {
         __shared__ double red[NT / 32];
-        lam = warp_max(lam);
-        if ((tid & 31) == 0) red[tid >> 5] = lam;
+        const double lmax = warp_max(to_f64(lam));
+        if ((tid & 31) == 0) red[tid >> 5] = lmax;
         __syncthreads();
         if (tid < 32) {
             double v = (tid < NT / 32) ? red[tid] : 0.0;
