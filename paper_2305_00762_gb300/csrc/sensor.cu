@@ -58,8 +58,10 @@ struct SensorTileParams {
 };
 
 struct SensorTileSmem {
-    float sr[kRH * kRW], sp[kRH * kRW];
-    SensorDev w;
+    float sr[kRH * kRW], sp[kRH * kRW];  // staged rho, p (tile + 2-cell halo)
+    float hr[2 * kRH * kTX], hp[2 * kRH * kTX];  // max, then min, over 5 columns
+    float scr[kTY * kTX], scp[kTY * kTX];  // per-cell normalisation scales
+    alignas(16) SensorDev w;                   // ldmatrix rows need 16-byte alignment
 };
 
 __device__ void sensor_tile(const SensorTileParams& P, const int tx0, const int ty0, SensorTileSmem& S)
@@ -83,12 +85,57 @@ __device__ void sensor_tile(const SensorTileParams& P, const int tx0, const int 
         S.sp[idx] = pr;
     }
     __syncthreads();
+    const bool features = P.prob || decide || P.feat;
+    if (features) {
+        // Normalisation scales 1/(max_k |q_k - q_c| + floor) over each cell's
+        // 5 x 5 window, from separable window maxima and minima: rounding is
+        // monotone, so max_k RN(q_k - q_c) = RN(max_k q_k - q_c) (likewise
+        // for the minimum) and the scales are those of the direct 25-term
+        // maximum, bit for bit.
+        for (int idx = threadIdx.x; idx < kRH * kTX; idx += blockDim.x) {
+            const int ry = idx / kTX, cx = idx - ry * kTX;
+            const float* r = S.sr + ry * kRW + cx;
+            const float* p = S.sp + ry * kRW + cx;
+            float rmx = r[0], rmn = r[0], pmx = p[0], pmn = p[0];
+#pragma unroll
+            for (int d = 1; d < 5; ++d) {
+                rmx = fmaxf(rmx, r[d]);
+                rmn = fminf(rmn, r[d]);
+                pmx = fmaxf(pmx, p[d]);
+                pmn = fminf(pmn, p[d]);
+            }
+            S.hr[idx] = rmx;
+            S.hr[kRH * kTX + idx] = rmn;
+            S.hp[idx] = pmx;
+            S.hp[kRH * kTX + idx] = pmn;
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < kTY * kTX; c += blockDim.x) {
+            const int cy = c / kTX, cx = c - cy * kTX;
+            float rmx = S.hr[c], rmn = S.hr[kRH * kTX + c], pmx = S.hp[c], pmn = S.hp[kRH * kTX + c];
+#pragma unroll
+            for (int d = 1; d < 5; ++d) {
+                const int o = c + d * kTX;
+                rmx = fmaxf(rmx, S.hr[o]);
+                rmn = fminf(rmn, S.hr[kRH * kTX + o]);
+                pmx = fmaxf(pmx, S.hp[o]);
+                pmn = fminf(pmn, S.hp[kRH * kTX + o]);
+            }
+            const float rc = S.sr[(cy + kH) * kRW + cx + kH], pc = S.sp[(cy + kH) * kRW + cx + kH];
+            const float mr = fmaxf(0.f, fmaxf(rmx - rc, rc - rmn)), mp = fmaxf(0.f, fmaxf(pmx - pc, pc - pmn));
+            S.scr[c] = 1.f / (mr + kSensorFloor);
+            S.scp[c] = 1.f / (mp + kSensorFloor);
+        }
+        __syncthreads();
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    for (int chunk = warp; chunk < kTX * kTY / 16; chunk += blockDim.x >> 5) {
-        auto cells = [&](int i, const float*& r, const float*& p) {
+    for (int chunk = warp; features && chunk < kTX * kTY / 16; chunk += blockDim.x >> 5) {
+        auto cells = [&](int i, const float*& r, const float*& p, float& sr, float& sp) {
             const int c = chunk * 16 + i, cy = c / kTX, cx = c - cy * kTX;
             r = S.sr + (cy + kH) * kRW + (cx + kH);
             p = S.sp + (cy + kH) * kRW + (cx + kH);
+            sr = S.scr[c];
+            sp = S.scp[c];
         };
         if (P.prob || decide) {
             float plo, phi;
@@ -114,9 +161,8 @@ __device__ void sensor_tile(const SensorTileParams& P, const int tx0, const int 
                 if (i < ny && j < nx) {
                     const float* r;
                     const float* p;
-                    cells(lane, r, p);
                     float s1, s2;
-                    sensor_scales(r, p, kRW, s1, s2);
+                    cells(lane, r, p, s1, s2);
                     uint32_t* out = reinterpret_cast<uint32_t*>(P.feat + ((long long)i * nx + j) * kSensorK);
                     for (int k = 0; k < kSensorK; k += 2)
                         out[k / 2] = pack_bf16(sensor_feature(r, p, kRW, s1, s2, k),

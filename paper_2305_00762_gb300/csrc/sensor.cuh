@@ -60,29 +60,24 @@ __device__ __forceinline__ void mma_bf16_16816(float d[4], const uint32_t a[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// Four 8x8 BF16 matrices from shared memory, one row address per lane (lanes
+// 8j..8j+7 give the rows of matrix j); lane l receives row l/4, columns
+// 2(l%4), 2(l%4)+1 of each: the B fragments of mma m16n8k16 when the rows are
+// the n index and the columns 8 consecutive k of a [n][k] weight array.
+__device__ __forceinline__ void ldmatrix_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const void* row)
+{
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(row));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
 // Copy the sensor weights into shared memory (all threads of the block).
 __device__ __forceinline__ void load_sensor(SensorDev* dst, const SensorDev* src)
 {
     const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
     uint32_t* d = reinterpret_cast<uint32_t*>(dst);
     for (int i = threadIdx.x; i < (int)(sizeof(SensorDev) / 4); i += blockDim.x) d[i] = s[i];
-}
-
-// Normalisation denominators of one cell from its 5x5 neighbourhood:
-// rho at r[dy*st + dx], p at p[...] (pointers at the cell).
-__device__ __forceinline__ void sensor_scales(const float* r, const float* p, int st, float& sr, float& sp)
-{
-    const float rc = r[0], pc = p[0];
-    float mr = 0.f, mp = 0.f;
-#pragma unroll
-    for (int dy = -2; dy <= 2; ++dy)
-#pragma unroll
-        for (int dx = -2; dx <= 2; ++dx) {
-            mr = fmaxf(mr, fabsf(r[dy * st + dx] - rc));
-            mp = fmaxf(mp, fabsf(p[dy * st + dx] - pc));
-        }
-    sr = 1.f / (mr + kSensorFloor);
-    sp = 1.f / (mp + kSensorFloor);
 }
 
 // Feature k of a cell (0 <= k < 64) given its scales.
@@ -100,41 +95,22 @@ __device__ __forceinline__ float sensor_feature(const float* r, const float* p, 
 }
 
 // The network on 16 cells of one warp. Row i (0..15) is the cell whose
-// density / pressure pointers are rho_of(i), p_of(i) (a functor returning the
-// pointers). Returns, for the two rows this lane holds (lane/4 and lane/4+8),
-// the outputs p (valid in every lane of a quad).
+// density / pressure pointers are rho_of(i), p_of(i) and whose normalisation
+// scales 1/(max|q_k - q_c| + floor) are sr, sp (a functor returning the
+// pointers and the scales). Returns, for the two rows this lane holds (lane/4
+// and lane/4+8), the outputs p (valid in every lane of a quad).
 template <typename CellPtrs>
 __device__ __forceinline__ void sensor_warp16(const SensorDev& W, CellPtrs cells, int st, float& out_lo,
                                               float& out_hi)
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const float *rl, *pl, *rh, *ph;
-    cells(g, rl, pl);
-    cells(g + 8, rh, ph);
-    // Normalisation denominators: the four lanes of a quad hold the same two
-    // cells; each takes every fourth neighbour and the quad combines the
-    // maxima (a maximum does not depend on the order).
-    float mrl = 0.f, mpl = 0.f, mrh = 0.f, mph = 0.f;
-    {
-        const float rcl = rl[0], pcl = pl[0], rch = rh[0], pch = ph[0];
-#pragma unroll
-        for (int k = t; k < 25; k += 4) {
-            const int o = (k / 5 - 2) * st + (k % 5 - 2);
-            mrl = fmaxf(mrl, fabsf(rl[o] - rcl));
-            mpl = fmaxf(mpl, fabsf(pl[o] - pcl));
-            mrh = fmaxf(mrh, fabsf(rh[o] - rch));
-            mph = fmaxf(mph, fabsf(ph[o] - pch));
-        }
-#pragma unroll
-        for (int m = 1; m <= 2; m <<= 1) {
-            mrl = fmaxf(mrl, __shfl_xor_sync(0xffffffffu, mrl, m));
-            mpl = fmaxf(mpl, __shfl_xor_sync(0xffffffffu, mpl, m));
-            mrh = fmaxf(mrh, __shfl_xor_sync(0xffffffffu, mrh, m));
-            mph = fmaxf(mph, __shfl_xor_sync(0xffffffffu, mph, m));
-        }
-    }
-    const float srl = 1.f / (mrl + kSensorFloor), spl = 1.f / (mpl + kSensorFloor);
-    const float srh = 1.f / (mrh + kSensorFloor), sph = 1.f / (mph + kSensorFloor);
+    float srl, spl, srh, sph;
+    cells(g, rl, pl, srl, spl);
+    cells(g + 8, rh, ph, srh, sph);
+    // B fragments: lane l addresses row (l & 7) of matrix l >> 3; matrices 0, 1
+    // are k-halves of n-tile 2np, matrices 2, 3 those of n-tile 2np + 1.
+    const int bn = 8 * (lane >> 4) + (lane & 7), bk = 8 * ((lane >> 3) & 1);
     // layer 1: [16 x 64] x [64 x 32]
     float acc1[4][4];
 #pragma unroll
@@ -154,11 +130,11 @@ __device__ __forceinline__ void sensor_warp16(const SensorDev& W, CellPtrs cells
         a[2] = pack_bf16(sensor_feature(rl, pl, st, srl, spl, k1), sensor_feature(rl, pl, st, srl, spl, k1 + 1));
         a[3] = pack_bf16(sensor_feature(rh, ph, st, srh, sph, k1), sensor_feature(rh, ph, st, srh, sph, k1 + 1));
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const __nv_bfloat16* wb = W.w1t + (8 * nt + g) * kW1Pitch;
-            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wb + k0);
-            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wb + k1);
-            mma_bf16_16816(acc1[nt], a, b0, b1);
+        for (int np = 0; np < 2; ++np) {
+            uint32_t b[4];
+            ldmatrix_x4(b[0], b[1], b[2], b[3], W.w1t + (16 * np + bn) * kW1Pitch + 16 * ks + bk);
+            mma_bf16_16816(acc1[2 * np], a, b[0], b[1]);
+            mma_bf16_16816(acc1[2 * np + 1], a, b[2], b[3]);
         }
     }
     // ReLU, round to BF16: the accumulator tiles of columns 16ks..16ks+15 are
@@ -174,18 +150,29 @@ __device__ __forceinline__ void sensor_warp16(const SensorDev& W, CellPtrs cells
     // layer 2: [16 x 32] x [32 x 32], then the 32 -> 1 output layer
     float zl = 0.f, zh = 0.f;
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-        const int n0 = 8 * nt + 2 * t;
-        float acc[4] = {W.b2[n0], W.b2[n0 + 1], W.b2[n0], W.b2[n0 + 1]};
+    for (int np = 0; np < 2; ++np) {
+        float acc[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int n0 = 8 * (2 * np + h) + 2 * t;
+            acc[h][0] = W.b2[n0];
+            acc[h][1] = W.b2[n0 + 1];
+            acc[h][2] = W.b2[n0];
+            acc[h][3] = W.b2[n0 + 1];
+        }
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) {
-            const __nv_bfloat16* wb = W.w2t + (8 * nt + g) * kW2Pitch;
-            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wb + 16 * ks + 2 * t);
-            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wb + 16 * ks + 8 + 2 * t);
-            mma_bf16_16816(acc, a2[ks], b0, b1);
+            uint32_t b[4];
+            ldmatrix_x4(b[0], b[1], b[2], b[3], W.w2t + (16 * np + bn) * kW2Pitch + 16 * ks + bk);
+            mma_bf16_16816(acc[0], a2[ks], b[0], b[1]);
+            mma_bf16_16816(acc[1], a2[ks], b[2], b[3]);
         }
-        zl += fmaxf(acc[0], 0.f) * W.w3[n0] + fmaxf(acc[1], 0.f) * W.w3[n0 + 1];
-        zh += fmaxf(acc[2], 0.f) * W.w3[n0] + fmaxf(acc[3], 0.f) * W.w3[n0 + 1];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // n-tiles in order 0..3, as the output layer's sum
+            const int n0 = 8 * (2 * np + h) + 2 * t;
+            zl += fmaxf(acc[h][0], 0.f) * W.w3[n0] + fmaxf(acc[h][1], 0.f) * W.w3[n0 + 1];
+            zh += fmaxf(acc[h][2], 0.f) * W.w3[n0] + fmaxf(acc[h][3], 0.f) * W.w3[n0 + 1];
+        }
     }
     zl += __shfl_xor_sync(0xffffffffu, zl, 1);
     zl += __shfl_xor_sync(0xffffffffu, zl, 2);
