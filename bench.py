@@ -78,6 +78,28 @@ FP32_PEAK_GFLOPS = 80550.0    # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 G
 F64_STAGE_DRAM_BYTES_1024 = 59.77e6
 
 
+def fma_peaks():
+    """Measured FP64 and FP32 fused multiply-add throughput (GFLOP/s) of the
+    current device, from the FMA-chain probe library (built beside libgbr),
+    or None if it cannot run."""
+    import ctypes
+    from paper_2305_00762_gb300 import build as B
+    try:
+        L = ctypes.CDLL(B.PROBE_LIB)
+        f = L.gbr_probe_fma_gflops
+        f.restype = ctypes.c_int
+        f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        out = {}
+        for prec, iters in ((64, 4096), (32, 65536)):
+            g = ctypes.c_double(0.0)
+            if f(prec, iters, ctypes.byref(g)) != 0:
+                return None
+            out[prec] = g.value
+        return out
+    except OSError:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during a region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -464,6 +486,8 @@ def main():
     hbm = bytes_cell * cells / stage_avg_s / 1e9                  # GB/s
     pk = peaks()
     hbm_peak = pk.get("hbm_gbs", 6800.0)
+    fma = fma_peaks()   # after the timed regions
+    fp32_alu = flop_cell * cells / (r32["timing"]["stage"][0] / max(r32["timing"]["stage"][1], 1) * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r64["ms"] / args.steps, "higher_is_better": True,
@@ -477,15 +501,18 @@ def main():
                      "traffic": F64_STAGE_DRAM_BYTES_1024 if args.n == 1024 else None, "traffic_unit": "bytes/launch",
                      "kernel": "stage_kernel<double> (fused residual + RK stage)",
                      "flop_per_cell_update": flop_cell, "stage_ms_avg": stage_avg_s * 1e3,
-                     "hbm_achieved_gbs": hbm, "hbm_peak_gbs": hbm_peak, "hbm_frac": hbm / hbm_peak},
+                     "hbm_achieved_gbs": hbm, "hbm_peak_gbs": hbm_peak, "hbm_frac": hbm / hbm_peak,
+                     "peak_source": "nominal: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                     "peak_measured": fma[64] if fma else None,
+                     "frac_of_measured": achieved / fma[64] if fma else None},
         "fp32_form": {"value": r32["rate"], "ms_per_step": r32["ms"] / args.steps,
                       "speedup_vs_fp64": r64["ms"] / r32["ms"],
                       "stage_ms_avg": r32["timing"]["stage"][0] / max(r32["timing"]["stage"][1], 1),
                       "hbm_frac": bytes_cell * cells / (r32["timing"]["stage"][0] /
                                                         max(r32["timing"]["stage"][1], 1) * 1e-3) / 1e9 / hbm_peak,
-                      "alu_frac_fp32": flop_cell * cells / (r32["timing"]["stage"][0] /
-                                                            max(r32["timing"]["stage"][1], 1) * 1e-3) / 1e9
-                      / FP32_PEAK_GFLOPS,
+                      "alu_frac_fp32": fp32_alu / FP32_PEAK_GFLOPS,
+                      "alu_peak_fp32_measured": fma[32] if fma else None,
+                      "alu_frac_fp32_of_measured": fp32_alu / fma[32] if fma else None,
                       "clocks": r32["clocks"],
                       "density_l1_vs_fp64_20_steps": acc.get((32, False))},
         "e2e": {"value": e2e_rate, "unit": METRIC,

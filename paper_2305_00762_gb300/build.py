@@ -12,6 +12,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgbr.so")
+# the benchmark's FMA-throughput probe, a library of its own
+PROBE_SRC = os.path.join(HERE, "probe", "alu_peak.cu")
+PROBE_LIB = os.path.join(OUT, "libgbr_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -58,6 +61,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         tmp = LIB + ".tmp"
         run([nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs)
         os.replace(tmp, LIB)
+    if force or _stale(PROBE_LIB, [PROBE_SRC]):
+        tmp = PROBE_LIB + ".tmp"
+        run([nvcc()] + ARCH + FLAGS + ["-shared", "-cudart", "static", "-o", tmp, PROBE_SRC])
+        os.replace(tmp, PROBE_LIB)
     return LIB
 
 
