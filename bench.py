@@ -55,6 +55,8 @@ def parse():
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--ensemble-cases", type=int, default=64)
     ap.add_argument("--no-4096", action="store_true", help="skip the 4096^2 FP32 + learned-sensor measurement")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the scheme variants and the viscous shock-tube workload")
     return ap.parse_args()
 
 
@@ -350,7 +352,71 @@ def ensemble_accuracy(torch, gbr, cases, table, st, sensor_w, nsteps=20):
             "time_mismatch_max": float(np.abs(t32 - t64).max())}
 
 
-def time_steps(torch, solver, steps, flush, profile=False):
+def run_variants(torch, gbr, case, q_start, st, flush, plain_rate, steps=10, warmup=3):
+    """The scheme's other members on the benchmark's workload and window
+    state, FP64: MEG7-cons, the fourth-order member of the family, and the
+    shock-stable HLLC-LM Riemann solver."""
+    cells = case.nx * case.ny
+    out = {}
+    for name, kw in (("meg7_cons", {"cons": True}), ("order4", {"order": 4}), ("hllc_lm", {"riemann": 1})):
+        s = gbr.Solver.for_case(case, stream=st.cuda_stream, precision=64, **kw)
+        s.set_state(q_start)
+        for _ in range(warmup):
+            s.step_cfl(CFL)
+        s.sync()
+        ms = time_steps(torch, s, steps, flush)
+        rc = s.sync(allow=(gbr.GBR_ERR_NONPHYSICAL,))
+        s.close()
+        rate = 3.0 * cells * steps / (ms * 1e-3)
+        out[name] = {"value": rate, "unit": METRIC, "ms_per_step": ms / steps, "vs_plain_fp64": rate / plain_rate,
+                     "status": gbr.error_string(rc)}
+    return out
+
+
+def run_viscous(torch, gbr, cases, st, flush, prelude=50, warmup=3, steps=10):
+    """The viscous shock tube on 2048 x 1024 cells (Re 1000, Pr 0.73, no-slip
+    walls, symmetry top) at the paper's CFL 0.2 (the viscous bound decides dt
+    on this grid, and CFL 0.5 is beyond the stability limit of the viscous
+    operator there): FP64 and FP32 forms timed from a common state after
+    `prelude` FP64 steps, and the FP32 form's density L1 against FP64 after
+    20 steps of a common fixed dt."""
+    import numpy as np
+    c = cases.viscous_shock_tube(2048, 1024)
+    cells = c.nx * c.ny
+    pre = gbr.Solver.for_case(c, stream=st.cuda_stream, precision=64)
+    pre.set_state(torch.from_numpy(c.Q).cuda())
+    for _ in range(prelude):
+        pre.step_cfl(c.cfl)
+    q0 = torch.empty((4, c.ny, c.nx), dtype=torch.float64, device="cuda")
+    gbr.gbr_get_state(pre.ctx, q0, c.nx, c.ny)
+    t0 = pre.time()
+    dt = 0.8 * c.cfl / pre.max_wavespeed()
+    pre.close()
+    out = {"workload": "viscous_shock_tube_2048x1024", "unit": METRIC, "cfl": c.cfl, "t_start": t0,
+           "prelude_fp64_steps": prelude}
+    rho = {}
+    for prec in (64, 32):
+        s = gbr.Solver.for_case(c, stream=st.cuda_stream, precision=prec)
+        s.set_state(q0)
+        for _ in range(warmup):
+            s.step_cfl(c.cfl)
+        s.sync()
+        ms = time_steps(torch, s, steps, flush, cfl=c.cfl)
+        rc = s.sync(allow=(gbr.GBR_ERR_NONPHYSICAL,))
+        s.close()
+        out[f"fp{prec}"] = {"value": 3.0 * cells * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                            "status": gbr.error_string(rc)}
+        s = gbr.Solver.for_case(c, stream=st.cuda_stream, precision=prec)
+        s.set_state(q0)
+        for _ in range(20):
+            s.step(dt)
+        rho[prec] = s.get_state()[0]
+        s.close()
+    out["density_l1_fp32_vs_fp64_20_steps"] = float(np.abs(rho[32] - rho[64]).sum() / np.abs(rho[64]).sum())
+    return out
+
+
+def time_steps(torch, solver, steps, flush, profile=False, cfl=CFL):
     """Device time of `steps` RK3 steps, L2 flushed between steps (outside
     the events); per-step events on the library's stream."""
     st = torch.cuda.current_stream()
@@ -362,7 +428,7 @@ def time_steps(torch, solver, steps, flush, profile=False):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(st)
-        solver.step_cfl(CFL)
+        solver.step_cfl(cfl)
         b.record(st)
         b.synchronize()
         total += a.elapsed_time(b)
@@ -529,6 +595,9 @@ def main():
             "stage_ms_avg": rl["timing"]["stage"][0] / max(rl["timing"]["stage"][1], 1),
             "sensor": "MLP 50-32-32-1, BF16 mma.sync, fallback band [0.3, 0.7]",
             "density_l1_vs_fp64_20_steps": acc.get((32, True)), "clocks": rl["clocks"]}
+    if not args.no_variants:
+        line["variants_fp64"] = run_variants(torch, gbr, case, q_start, st, flush, value)
+        line["viscous"] = run_viscous(torch, gbr, cases, st, flush)
     if not args.no_4096 and sensor_w is not None:
         line["fp32_learned_4096"] = run_learned_4096(torch, gbr, cases, st, sensor_w)
     if not args.no_ensemble:

@@ -133,7 +133,13 @@ def riemann_2d(n, ny=None, t_end=0.3, cfl=0.5, split=(0.8, 0.8)):
 # Example 10: viscous shock tube (Daru-Tenaud), [0,1] x [0,0.5]
 # --------------------------------------------------------------------------
 
-def viscous_shock_tube(nx, ny=None, Re=1000.0, Pr=0.73, gamma=1.4, t_end=1.0, cfl=0.5):
+def viscous_shock_tube(nx, ny=None, Re=1000.0, Pr=0.73, gamma=1.4, t_end=1.0, cfl=0.2):
+    """Navier-Stokes shock tube on [0,1] x [0,0.5]: rho 120 / 1.2 split at
+    x = 0.5, p = rho/gamma, at rest; mu = 1/Re; no-slip adiabatic walls west,
+    east and south, a symmetry plane north. CFL 0.2 as in Sec. 2.5 (used for
+    all of the paper's runs): on fine grids the viscous bound of the time step
+    decides dt, and the alpha-damping heat-conduction operator is unstable
+    under TVD-RK3 above CFL ~0.33 there."""
     ny = nx // 2 if ny is None else ny
     xc, dx = centres(nx, 0.0, 1.0)
     yc, dy = centres(ny, 0.0, 0.5)

@@ -281,3 +281,33 @@ def test_meg7_cons(env, name, make):
         assert rc == 0
     assert_state_close(s.get_state(), Q, what=f"{name} cons steps")
     s.close()
+
+
+def test_viscous_shock_tube_time_step(env):
+    """Config 3 at full size (2048 x 1024), where the viscous bound of Sec.
+    2.5 decides dt: 100 steps at the paper's CFL 0.2 stay physical (t grows
+    by 100 viscous-limited steps); at CFL 0.5 the alpha-damping heat
+    conduction is beyond TVD-RK3's stability interval and the state turns
+    non-physical within 60 steps, which the positivity check reports
+    (GBR_ERR_NONPHYSICAL, no fault) rather than a silent blow-up."""
+    torch, O, gbr = env
+    c = C.viscous_shock_tube(2048, 1024)
+    assert c.cfl == 0.2
+    s = gbr.Solver.for_case(c)
+    s.set_state(c.Q)
+    lam0 = s.max_wavespeed()
+    assert lam0 > 3 * 2048 * 1.0              # viscous bound 4 nu/dx^2 dominates (|u| + c)/dx ~ 2048
+    for _ in range(100):
+        s.step_cfl(c.cfl)
+    assert s.sync() == gbr.GBR_OK
+    Q = s.get_state()
+    p = 0.4 * (Q[3] - 0.5 * (Q[1] ** 2 + Q[2] ** 2) / Q[0])
+    assert np.all(np.isfinite(Q)) and Q[0].min() > 0 and p.min() > 0
+    assert 0.5 * 100 * c.cfl / lam0 < s.time() < 1.5 * 100 * c.cfl / lam0
+    s.close()
+    s = gbr.Solver.for_case(c)
+    s.set_state(c.Q)
+    for _ in range(60):
+        s.step_cfl(0.5)
+    assert s.sync(allow=(gbr.GBR_ERR_NONPHYSICAL,)) == gbr.GBR_ERR_NONPHYSICAL
+    s.close()

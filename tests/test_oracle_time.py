@@ -106,3 +106,36 @@ def test_vortex_evolution_seventh_order(oracle_mod):
         errs.append(np.abs(Q[0] - C.vortex_prims(X, Y, 2.0)[0]).mean())
     orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert orders[0] > 7.0 and orders[1] >= 6.5, orders
+
+
+def test_viscous_time_step_limit(oracle_mod):
+    """Sec. 2.5's time step with CFL 0.2 (the paper's value for all runs) is
+    stable where the viscous bound decides dt; the configs' CFL 0.5 is not
+    there. Periodic 24^2 gas at rest with 1e-4 seeded density noise, mu = 0.05
+    (viscous bound 4 nu/dx^2 = 115 against (|u| + c)/dx = 28): the discrete
+    heat-conduction operator of the alpha-damping scheme (alpha_v = 4) has a
+    spectral radius near 8 (gamma/Pr) nu (1/dx^2 + 1/dy^2), so TVD-RK3 (real
+    stability interval 2.51) needs CFL below ~0.33."""
+    import numpy as np
+    from paper_2305_00762_gb300 import cases as C
+    O = oracle_mod
+    n, mu = 24, 0.05
+    rng = np.random.default_rng(5)
+    rho = 1 + 1e-4 * rng.standard_normal((n, n))
+    Q0 = np.ascontiguousarray(C.prim_to_cons(rho, 0 * rho, 0 * rho, np.ones((n, n)), 1.4))
+    cfg = O.Config(n, n, 1.0 / n, 1.0 / n, 1.4, mu, 0.73, (0, 0, 0, 0))
+    lam = O.max_wavespeed(cfg, Q0)
+    nu_max = mu / Q0[0].min()
+    assert abs(lam - 4 * nu_max * n * n) < 1e-9 * lam   # the viscous bound decides
+    assert lam > 3 * np.sqrt(1.4 * 1.0 / Q0[0].min()) * n
+    dev0 = np.abs(Q0[0] - Q0[0].mean()).max()
+
+    def run(cfl, steps):
+        q = Q0
+        for _ in range(steps):
+            q, rc = O.rk3_step(cfg, q, cfl / O.max_wavespeed(cfg, q))
+            if rc != 0 or not np.isfinite(q).all():
+                return np.inf
+        return np.abs(q[0] - q[0].mean()).max()
+    assert run(0.5, 60) > 1e3 * dev0        # grows without bound (or turns non-physical)
+    assert run(0.2, 60) < dev0              # decays
