@@ -57,16 +57,16 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) batch_stage_kernel
     }
 }
 
-// Persistent grid size: resident CTAs per SM x SMs (computed once; the first
-// call also raises the kernel's dynamic shared-memory limit, so it must
-// happen outside stream capture).
+// Persistent grid size: resident CTAs per SM x SMs (computed once per
+// device; the first call on a device also raises the kernel's dynamic
+// shared-memory limit there, so it must happen outside stream capture).
 template <typename T, int BX, int BY, int NT, bool LEARNED>
 cudaError_t batch_blocks(int* out)
 {
     using L = TileLayout<BX, BY, false>;
     constexpr size_t smem = L::template total_bytes<T, NT, LEARNED>();
-    static int blocks = 0;
-    if (blocks == 0) {
+    static PerDevice<int> blocks;
+    return blocks.get(out, [&](int* v) {
         auto kern = batch_stage_kernel<T, BX, BY, NT, LEARNED>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -74,10 +74,9 @@ cudaError_t batch_blocks(int* out)
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem)) != cudaSuccess) return e;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        blocks = (per_sm > 0 ? per_sm : 1) * sms;
-    }
-    *out = blocks;
-    return cudaSuccess;
+        *v = (per_sm > 0 ? per_sm : 1) * sms;
+        return cudaSuccess;
+    });
 }
 
 // total_tiles < 0: only prepare the kernel (batch_blocks), launch nothing.

@@ -6,7 +6,35 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace gbr {
+
+// Per-device launch set-up (kernel attributes and occupancy-derived grid
+// sizes are properties of a kernel on one device). PerDevice<V> holds one
+// value per device ordinal below kDeviceSlots; `get` computes it with `make`
+// on the current device the first time and returns the stored value after
+// (a race between threads computes the same value twice, harmlessly).
+constexpr int kDeviceSlots = 64;
+template <typename V>
+struct PerDevice {
+    std::atomic<V> val[kDeviceSlots];  // zero: not computed yet
+    template <typename F>
+    cudaError_t get(V* out, F make)
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= kDeviceSlots) return make(out);
+        V v = val[dev].load(std::memory_order_acquire);
+        if (v == V(0)) {
+            if ((e = make(&v)) != cudaSuccess) return e;
+            val[dev].store(v, std::memory_order_release);
+        }
+        *out = v;
+        return cudaSuccess;
+    }
+};
 
 constexpr int kGhost = 6;  // ghost layers per side (Sec. 2.3, LC bound reach)
 

@@ -278,15 +278,18 @@ __global__ void __launch_bounds__(256) batch_sensor_decide_kernel(const BatchCas
 cudaError_t launch_batch_sensor_decide(const BatchCase* cases, int ncases, int total_tiles, int buf,
                                        const SensorDev* w, cudaStream_t s)
 {
-    static int blocks = 0;
-    if (blocks == 0) {
+    static PerDevice<int> grid;  // resident CTAs per SM x SMs, per device
+    int blocks = 0;
+    cudaError_t e = grid.get(&blocks, [](int* v) {
         int per_sm = 0, dev = 0, sms = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sensor_decide_kernel, 256, 0);
-        if (e != cudaSuccess) return e;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        blocks = (per_sm > 0 ? per_sm : 1) * sms;
-    }
+        cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sensor_decide_kernel, 256, 0);
+        if (r != cudaSuccess) return r;
+        if ((r = cudaGetDevice(&dev)) != cudaSuccess) return r;
+        if ((r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return r;
+        *v = (per_sm > 0 ? per_sm : 1) * sms;
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
     if (total_tiles < 0) return cudaSuccess;  // prepare only
     batch_sensor_decide_kernel<<<blocks, 256, 0, s>>>(cases, ncases, total_tiles, buf, w);
     return cudaGetLastError();

@@ -1182,15 +1182,16 @@ cudaError_t launch_stage_t(const StageParams& p, cudaStream_t s)
 {
     using L = TileLayout<BX, BY, VISC, CONS>;
     constexpr size_t smem = L::template total_bytes<T, NT, LEARNED>();
-    static bool configured = false;
+    static PerDevice<int> configured;  // the shared-memory limit is raised once per device
     auto kern = stage_kernel<T, BX, BY, NT, VISC, LEARNED, ORDER, CONS>;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    int ok = 0;
+    cudaError_t e = configured.get(&ok, [&](int* v) {
+        *v = 1;
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (e != cudaSuccess) return e;
     CUtensorMap map;
-    const cudaError_t e = encode_state_map(p.g, p.q, L::RW, L::RH, &map);
+    e = encode_state_map(p.g, p.q, L::RW, L::RH, &map);
     if (e != cudaSuccess) return e;
     dim3 grid((p.g.nx + BX - 1) / BX, (p.g.ny + BY - 1) / BY);
     kern<<<grid, NT, smem, s>>>(p, map);
