@@ -55,6 +55,8 @@ def parse():
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--ensemble-cases", type=int, default=64)
     ap.add_argument("--no-4096", action="store_true", help="skip the 4096^2 FP32 + learned-sensor measurement")
+    ap.add_argument("--paper-table", action="store_true",
+                    help="instead of the benchmark: the runs of the paper's Table speed (whole runs, CFL 0.2)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the scheme variants and the viscous shock-tube workload")
     return ap.parse_args()
@@ -416,6 +418,66 @@ def run_viscous(torch, gbr, cases, st, flush, prelude=50, warmup=3, steps=10):
     return out
 
 
+def run_to(solver, t_end, cfl, chunk=50):
+    """Advance to t_end at the given CFL with dt formed on the device: chunks
+    of `chunk` unbounded steps while the time left exceeds three chunks at the
+    last mean dt, then single steps with dt_max = the time left (one host read
+    of the time per chunk or step). Returns the number of steps."""
+    steps, t, mean_dt = 0, solver.time(), None
+    while t < t_end * (1 - 1e-14):
+        left = t_end - t
+        if mean_dt is not None and left > 3.0 * chunk * mean_dt:
+            for _ in range(chunk):
+                solver.step_cfl(cfl)
+            n = chunk
+        else:
+            solver.step_cfl(cfl, left)
+            n = 1
+        t_new = solver.time()
+        steps += n
+        mean_dt = (t_new - t) / n
+        t = t_new
+    return steps
+
+
+def run_paper_table(torch, gbr, cases):
+    """The paper's Table speed runs (whole runs at the paper's CFL 0.2,
+    MEG7-prim and MEG7-cons in FP64, and MEG7-prim in the FP32 form):
+    wall-clock seconds on this GPU, host loop included, beside the paper's
+    serial CPU times (unnamed hardware, unstated precision: context only)."""
+    import numpy as np
+    runs = [("riemann_2d_400x400_t0.8", lambda: cases.riemann_2d(400, t_end=0.8), 0.8,
+             {"prim": 1025.0, "cons": 1031.0}),
+            ("double_mach_1024x256_t0.2", lambda: cases.double_mach(1024, 256), 0.2,
+             {"prim": 1806.0, "cons": 1946.0}),
+            ("viscous_shock_tube_1280x640_t1", lambda: cases.viscous_shock_tube(1280, 640), 1.0,
+             {"prim": 35455.0, "cons": 38062.0})]
+    out = {}
+    for name, make, t_end, paper in runs:
+        c = make()
+        row = {"paper_serial_cpu_s": paper}
+        for form, kw in (("fp64_prim", {}), ("fp64_cons", {"cons": True}), ("fp32_prim", {"precision": 32})):
+            s = gbr.Solver.for_case(c, **kw)
+            s.set_state(torch.from_numpy(c.Q).cuda())
+            s.step_cfl(0.2, 1e-12)   # warm-up launch (kernel set-up), then restart from t = 0
+            s.set_state(torch.from_numpy(c.Q).cuda())
+            s.set_time(0.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            steps = run_to(s, t_end, 0.2)
+            rc = s.sync(allow=(gbr.GBR_ERR_NONPHYSICAL,))
+            wall = time.perf_counter() - t0
+            t = s.time()
+            Q = s.get_state()
+            s.close()
+            row[form] = {"wall_s": wall, "steps": steps, "t": t, "t_end_overshoot": t > t_end * (1 + 1e-12),
+                         "status": gbr.error_string(rc),
+                         "rho_min": float(Q[0].min()), "rho_max": float(Q[0].max()),
+                         "cell_updates_per_s": 3.0 * c.nx * c.ny * steps / wall}
+        out[name] = row
+    return out
+
+
 def time_steps(torch, solver, steps, flush, profile=False, cfl=CFL):
     """Device time of `steps` RK3 steps, L2 flushed between steps (outside
     the events); per-step events on the library's stream."""
@@ -448,6 +510,14 @@ def main():
     from paper_2305_00762_gb300 import build, cases, costs, gbr
     build.build()
     gbr.load()
+    if args.paper_table:
+        if rank == 0:
+            print(json.dumps({"paper_table_speed": run_paper_table(torch, gbr, cases), "cfl": 0.2,
+                              "note": "whole runs, host loop included; the paper's times are serial CPU runs "
+                                      "on unnamed hardware (context only)"}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     case = cases.riemann_2d(args.n)
     st = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
