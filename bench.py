@@ -675,7 +675,7 @@ def main():
             "value": rl["rate"], "ms_per_step": rl["ms"] / args.steps,
             "speedup_vs_fp64": r64["ms"] / rl["ms"],
             "stage_ms_avg": rl["timing"]["stage"][0] / max(rl["timing"]["stage"][1], 1),
-            "sensor": "MLP 50-32-32-1, BF16 mma.sync, fallback band [0.3, 0.7]",
+            "sensor": "MLP 50-32-32-1, BF16 tcgen05.mma (FP32 accumulators in tensor memory), fallback band [0.3, 0.7]",
             "density_l1_vs_fp64_20_steps": acc.get((32, True)), "clocks": rl["clocks"]}
     if not args.no_variants:
         line["variants_fp64"] = run_variants(torch, gbr, case, q_start, st, flush, value)

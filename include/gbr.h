@@ -257,7 +257,11 @@ int gbr_get_timing(gbr_ctx *ctx, double *ms, int *launches, int *dropped);
 int gbr_set_sensor_weights(gbr_ctx *ctx, const float *w, int n);
 
 /* Network output p per interior cell of the current state ([ny][nx] float32),
- * computed from FP32 primitives exactly as the fused stage kernel does. */
+ * computed from FP32 primitives as the FP32 stage kernel stages them, by the
+ * same tcgen05 tensor-core pass that forms the stage's decisions. Errors:
+ * GBR_ERR_STATE without a state or weights; GBR_ERR_TIMEOUT if a bounded
+ * device wait gave up (reported here with host buffers, else by the next
+ * synchronising call). */
 int gbr_sensor_eval(gbr_ctx *ctx, float *prob, int on_device);
 
 /* Training data from the current state (device buffers): features[ny*nx][64]

@@ -194,7 +194,7 @@ int stage(gbr_ctx* c, const StageParams& p)
     if (c->precision == 32 && p.sensor) {
         StageParams q = p;
         q.dec = c->dec;
-        cudaError_t e = launch_sensor_decide(c->g, c->ph.gamma, p.q, p.sensor, c->dec, c->stream);
+        cudaError_t e = launch_sensor_decide(c->g, c->ph.gamma, p.q, p.sensor, c->dec, p.err, c->stream);
         if (e == cudaSuccess) e = launch_stage_f32(q, c->stream);
         return cuda_status(e);
     }
@@ -573,10 +573,13 @@ int gbr_sensor_eval(gbr_ctx* c, float* prob, int on_device)
         if (!c->prob) GBR_TRY(cudaMalloc(&c->prob, sizeof(float) * n));
         out = c->prob;
     }
-    GBR_TRY(launch_sensor_tile(c->g, c->ph.gamma, c->Qn, c->d_sensor, out, nullptr, nullptr, nullptr, c->stream));
+    GBR_TRY(launch_sensor_tile(c->g, c->ph.gamma, c->Qn, c->d_sensor, out, nullptr, nullptr, nullptr, &c->ds->err,
+                               c->stream));
     if (!on_device) {
         GBR_TRY(cudaMemcpyAsync(prob, c->prob, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
-        GBR_TRY(cudaStreamSynchronize(c->stream));
+        DevScalars h;
+        rc = read_back_errors(c, &h);  // synchronises
+        if (rc == GBR_ERR_TIMEOUT || rc == GBR_ERR_CUDA) return rc;
     }
     return GBR_OK;
 }
@@ -589,7 +592,7 @@ int gbr_sensor_dataset(gbr_ctx* c, void* features, unsigned char* labels, unsign
     int rc = ghosts(c, c->Qn, 0, 0, 0, 0);
     if (rc != GBR_OK) return rc;
     return cuda_status(
-        launch_sensor_tile(c->g, c->ph.gamma, c->Qn, nullptr, nullptr, features, labels, targets, c->stream));
+        launch_sensor_tile(c->g, c->ph.gamma, c->Qn, nullptr, nullptr, features, labels, targets, nullptr, c->stream));
 }
 
 int gbr_sensor_train(const void* features, const unsigned char* targets, long long n, int steps, int batch,

@@ -154,17 +154,23 @@ void pack_sensor(const float* w, SensorDev* out);
 // Host-only; encodings are cached per (state, grid, box).
 cudaError_t encode_state_map(const Grid& g, const double* q, int box_w, int box_h, CUtensorMap* out);
 
+// Network outputs (prob, on the tcgen05 tensor cores), dataset features,
+// labels and targets of one padded state (ghosts filled). A bounded wait of
+// the tensor-core pass that gives up sets kErrTimeout in *err.
 cudaError_t launch_sensor_tile(const Grid& g, double gamma, const double* q, const SensorDev* w, float* prob,
-                               void* feat_bf16, unsigned char* label, unsigned char* target, cudaStream_t s);
-// The learned sensor's decision pass of one padded state (ghosts filled):
-// dec[y * pitch + x] for padded cells x in [3, nx + 9), y in [3, ny + 9):
-// 1 = discontinuity (p > 0.7), 0 = smooth (p < 0.3), 2 = unsure.
+                               void* feat_bf16, unsigned char* label, unsigned char* target, unsigned* err,
+                               cudaStream_t s);
+// The learned sensor's decision pass of one padded state (ghosts filled), on
+// the tcgen05 tensor cores: dec[y * pitch + x] for padded cells x in
+// [3, nx + 9), y in [3, ny + 9): 1 = discontinuity (p > 0.7), 0 = smooth
+// (p < 0.3), 2 = unsure. A wait that gives up sets kErrTimeout in *err.
 cudaError_t launch_sensor_decide(const Grid& g, double gamma, const double* q, const SensorDev* w,
-                                 unsigned char* dec, cudaStream_t s);
+                                 unsigned char* dec, unsigned* err, cudaStream_t s);
 // Sensor-pass tiles of a grid (the tile grid over its decision region).
 void sensor_decide_tiles(const Grid& g, int* tiles_x, int* tiles);
-// The decision pass of buffer `buf` of every running case of a batch
-// (persistent; total_tiles = sum of the cases' sensor-pass tiles).
+// The decision pass of buffer `buf` of every running case of a batch (one
+// CTA per sensor tile; total_tiles = sum of the cases' sensor-pass tiles; a
+// negative count only prepares the kernel, outside stream capture).
 cudaError_t launch_batch_sensor_decide(const BatchCase* cases, int ncases, int total_tiles, int buf,
                                        const SensorDev* w, cudaStream_t s);
 cudaError_t launch_sensor_train(const void* X_bf16, const unsigned char* y, long long n, int steps, int batch,

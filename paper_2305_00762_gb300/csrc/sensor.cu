@@ -57,23 +57,22 @@ struct SensorTileParams {
     unsigned char* dec;     // decision-region mode: decisions (padded layout), else nullptr
 };
 
-struct SensorTileSmem {
+// The staged region of one tile and the per-cell normalisation scales.
+struct SensorRegion {
     float sr[kRH * kRW], sp[kRH * kRW];  // staged rho, p (tile + 2-cell halo)
     float hr[2 * kRH * kTX], hp[2 * kRH * kTX];  // max, then min, over 5 columns
     float scr[kTY * kTX], scp[kTY * kTX];  // per-cell normalisation scales
-    alignas(16) SensorDev w;                   // ldmatrix rows need 16-byte alignment
 };
 
-__device__ void sensor_tile(const SensorTileParams& P, const int tx0, const int ty0, SensorTileSmem& S)
+// Stage the tile's region as FP32 rho, p exactly as the FP32 stage kernel
+// stages its primitives (clamped to the padded extent; clamped cells feed no
+// output), and, if `scales`, each cell's normalisation scales. Every thread of
+// the block takes part (block-wide barriers inside).
+__device__ void sensor_stage(const SensorTileParams& P, const int tx0, const int ty0, const int org, bool scales,
+                             SensorRegion& S)
 {
-    const bool decide = P.dec != nullptr;
-    const int org = decide ? kDecOrigin : kGhost;  // padded index of the space's cell 0
-    const int ni = decide ? P.g.ny + 2 * kDecOrigin : P.g.ny;
-    const int nj = decide ? P.g.nx + 2 * kDecOrigin : P.g.nx;
     const int nx = P.g.nx, ny = P.g.ny;
     const float gm1 = (float)(P.gamma - 1.0);
-    // stage the region as FP32 primitives exactly as the FP32 stage kernel
-    // does (clamped to the padded extent; clamped cells feed no output)
     for (int idx = threadIdx.x; idx < kRH * kRW; idx += blockDim.x) {
         const int ry = idx / kRW, rx = idx - ry * kRW;
         const int gx = min(tx0 + rx + org - kH, nx + 2 * kGhost - 1);
@@ -85,90 +84,66 @@ __device__ void sensor_tile(const SensorTileParams& P, const int tx0, const int 
         S.sp[idx] = pr;
     }
     __syncthreads();
-    const bool features = P.prob || decide || P.feat;
-    if (features) {
-        // Normalisation scales 1/(max_k |q_k - q_c| + floor) over each cell's
-        // 5 x 5 window, from separable window maxima and minima: rounding is
-        // monotone, so max_k RN(q_k - q_c) = RN(max_k q_k - q_c) (likewise
-        // for the minimum) and the scales are those of the direct 25-term
-        // maximum, bit for bit.
-        for (int idx = threadIdx.x; idx < kRH * kTX; idx += blockDim.x) {
-            const int ry = idx / kTX, cx = idx - ry * kTX;
-            const float* r = S.sr + ry * kRW + cx;
-            const float* p = S.sp + ry * kRW + cx;
-            float rmx = r[0], rmn = r[0], pmx = p[0], pmn = p[0];
+    if (!scales) return;
+    // Normalisation scales 1/(max_k |q_k - q_c| + floor) over each cell's
+    // 5 x 5 window, from separable window maxima and minima: rounding is
+    // monotone, so max_k RN(q_k - q_c) = RN(max_k q_k - q_c) (likewise for the
+    // minimum) and the scales are those of the direct 25-term maximum, bit
+    // for bit.
+    for (int idx = threadIdx.x; idx < kRH * kTX; idx += blockDim.x) {
+        const int ry = idx / kTX, cx = idx - ry * kTX;
+        const float* r = S.sr + ry * kRW + cx;
+        const float* p = S.sp + ry * kRW + cx;
+        float rmx = r[0], rmn = r[0], pmx = p[0], pmn = p[0];
 #pragma unroll
-            for (int d = 1; d < 5; ++d) {
-                rmx = fmaxf(rmx, r[d]);
-                rmn = fminf(rmn, r[d]);
-                pmx = fmaxf(pmx, p[d]);
-                pmn = fminf(pmn, p[d]);
-            }
-            S.hr[idx] = rmx;
-            S.hr[kRH * kTX + idx] = rmn;
-            S.hp[idx] = pmx;
-            S.hp[kRH * kTX + idx] = pmn;
+        for (int d = 1; d < 5; ++d) {
+            rmx = fmaxf(rmx, r[d]);
+            rmn = fminf(rmn, r[d]);
+            pmx = fmaxf(pmx, p[d]);
+            pmn = fminf(pmn, p[d]);
         }
-        __syncthreads();
-        for (int c = threadIdx.x; c < kTY * kTX; c += blockDim.x) {
-            const int cy = c / kTX, cx = c - cy * kTX;
-            float rmx = S.hr[c], rmn = S.hr[kRH * kTX + c], pmx = S.hp[c], pmn = S.hp[kRH * kTX + c];
-#pragma unroll
-            for (int d = 1; d < 5; ++d) {
-                const int o = c + d * kTX;
-                rmx = fmaxf(rmx, S.hr[o]);
-                rmn = fminf(rmn, S.hr[kRH * kTX + o]);
-                pmx = fmaxf(pmx, S.hp[o]);
-                pmn = fminf(pmn, S.hp[kRH * kTX + o]);
-            }
-            const float rc = S.sr[(cy + kH) * kRW + cx + kH], pc = S.sp[(cy + kH) * kRW + cx + kH];
-            const float mr = fmaxf(0.f, fmaxf(rmx - rc, rc - rmn)), mp = fmaxf(0.f, fmaxf(pmx - pc, pc - pmn));
-            S.scr[c] = 1.f / (mr + kSensorFloor);
-            S.scp[c] = 1.f / (mp + kSensorFloor);
-        }
-        __syncthreads();
+        S.hr[idx] = rmx;
+        S.hr[kRH * kTX + idx] = rmn;
+        S.hp[idx] = pmx;
+        S.hp[kRH * kTX + idx] = pmn;
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    for (int chunk = warp; features && chunk < kTX * kTY / 16; chunk += blockDim.x >> 5) {
-        auto cells = [&](int i, const float*& r, const float*& p, float& sr, float& sp) {
-            const int c = chunk * 16 + i, cy = c / kTX, cx = c - cy * kTX;
-            r = S.sr + (cy + kH) * kRW + (cx + kH);
-            p = S.sp + (cy + kH) * kRW + (cx + kH);
-            sr = S.scr[c];
-            sp = S.scp[c];
-        };
-        if (P.prob || decide) {
-            float plo, phi;
-            sensor_warp16(S.w, cells, kRW, plo, phi);
-            if (t == 0) {
-                for (int h = 0; h < 2; ++h) {
-                    const int c = chunk * 16 + g + 8 * h, cy = c / kTX, cx = c - cy * kTX;
-                    const int i = ty0 + cy, j = tx0 + cx;
-                    if (i >= ni || j >= nj) continue;
-                    const float pv = h ? phi : plo;
-                    if (decide)
-                        P.dec[(long long)(i + org) * P.g.pitch + (j + org)] =
-                            pv > kSensorHi ? 1 : (pv < kSensorLo ? 0 : 2);
-                    else
-                        P.prob[(long long)i * nx + j] = pv;
-                }
-            }
+    __syncthreads();
+    for (int c = threadIdx.x; c < kTY * kTX; c += blockDim.x) {
+        const int cy = c / kTX, cx = c - cy * kTX;
+        float rmx = S.hr[c], rmn = S.hr[kRH * kTX + c], pmx = S.hp[c], pmn = S.hp[kRH * kTX + c];
+#pragma unroll
+        for (int d = 1; d < 5; ++d) {
+            const int o = c + d * kTX;
+            rmx = fmaxf(rmx, S.hr[o]);
+            rmn = fminf(rmn, S.hr[kRH * kTX + o]);
+            pmx = fmaxf(pmx, S.hp[o]);
+            pmn = fminf(pmn, S.hp[kRH * kTX + o]);
         }
-        if (P.feat) {  // one cell per lane: lanes 0..15 write 64 features each
-            if (lane < 16) {
-                const int c = chunk * 16 + lane, cy = c / kTX, cx = c - cy * kTX;
-                const int i = ty0 + cy, j = tx0 + cx;
-                if (i < ny && j < nx) {
-                    const float* r;
-                    const float* p;
-                    float s1, s2;
-                    cells(lane, r, p, s1, s2);
-                    uint32_t* out = reinterpret_cast<uint32_t*>(P.feat + ((long long)i * nx + j) * kSensorK);
-                    for (int k = 0; k < kSensorK; k += 2)
-                        out[k / 2] = pack_bf16(sensor_feature(r, p, kRW, s1, s2, k),
-                                               sensor_feature(r, p, kRW, s1, s2, k + 1));
-                }
-            }
+        const float rc = S.sr[(cy + kH) * kRW + cx + kH], pc = S.sp[(cy + kH) * kRW + cx + kH];
+        const float mr = fmaxf(0.f, fmaxf(rmx - rc, rc - rmn)), mp = fmaxf(0.f, fmaxf(pmx - pc, pc - pmn));
+        S.scr[c] = 1.f / (mr + kSensorFloor);
+        S.scp[c] = 1.f / (mp + kSensorFloor);
+    }
+    __syncthreads();
+}
+
+// Dataset extraction on one tile: BF16 features of each interior cell (for
+// training), the plain detector's label and its soft target (FP64, Eq.
+// detector).
+__device__ void sensor_dataset_tile(const SensorTileParams& P, const int tx0, const int ty0, SensorRegion& S)
+{
+    const int nx = P.g.nx, ny = P.g.ny;
+    sensor_stage(P, tx0, ty0, kGhost, P.feat != nullptr, S);
+    if (P.feat) {  // one cell per thread, 64 features each
+        for (int c = threadIdx.x; c < kTX * kTY; c += blockDim.x) {
+            const int cy = c / kTX, cx = c - cy * kTX, i = ty0 + cy, j = tx0 + cx;
+            if (i >= ny || j >= nx) continue;
+            const float* r = S.sr + (cy + kH) * kRW + (cx + kH);
+            const float* p = S.sp + (cy + kH) * kRW + (cx + kH);
+            const float s1 = S.scr[c], s2 = S.scp[c];
+            uint32_t* out = reinterpret_cast<uint32_t*>(P.feat + ((long long)i * nx + j) * kSensorK);
+            for (int k = 0; k < kSensorK; k += 2)
+                out[k / 2] = pack_bf16(sensor_feature(r, p, kRW, s1, s2, k), sensor_feature(r, p, kRW, s1, s2, k + 1));
         }
     }
     if (P.label || P.target) {  // plain detector in FP64 on the density (Eq. detector)
@@ -189,15 +164,358 @@ __device__ void sensor_tile(const SensorTileParams& P, const int tx0, const int 
     }
 }
 
-__global__ void __launch_bounds__(256) sensor_tile_kernel(const SensorTileParams P)
+__global__ void __launch_bounds__(256) sensor_dataset_kernel(const SensorTileParams P)
 {
-    __shared__ SensorTileSmem S;
-    if (P.w) load_sensor(&S.w, P.w);
-    sensor_tile(P, blockIdx.x * kTX, blockIdx.y * kTY, S);
+    __shared__ SensorRegion S;
+    sensor_dataset_tile(P, blockIdx.x * kTX, blockIdx.y * kTY, S);
+}
+
+// ---------------------------------------------------------------------------
+// The network on the fifth-generation tensor cores (tcgen05): one CTA of G
+// warpgroups (128 G threads) per 32 x 16 tile, one thread per cell, 4/G
+// rounds; warpgroup g's 128 cells of a round are the M = 128 rows of its own
+// MMAs, on its own 64 tensor-memory columns.
+// A thread writes its cell's 64 features (50 + zero padding, BF16 pairs) into
+// its own tensor-memory lane; one thread issues the layer-1 MMAs
+// (M = 128 cells, N = 32, K = 64: four K = 16 steps, A from tensor memory, B
+// = W1^T from shared memory through a matrix descriptor, FP32 accumulation in
+// tensor memory); each thread reads its cell's 32 accumulators back, adds the
+// bias, applies ReLU, rounds to BF16 and writes them as layer 2's A; layer 2
+// (K = 32) runs the same way; the 32 -> 1 output is a per-thread dot product.
+// Tensor memory per warpgroup: 64 columns, A at [0, 32) (layer 1's features,
+// then layer 2's inputs once layer 1's MMAs are done) and D at [32, 64)
+// (layer 1's accumulators, then layer 2's once every thread has read them).
+// The shared memory of a CTA is sized so that at most 8/G CTAs fit on an SM
+// (228 KB), so their allocations (64 G columns each, 512 per SM) never wait
+// on one another. Every mbarrier wait is bounded; on a timeout the CTA reports
+// kErrTimeout, skips its remaining rounds and still frees its columns.
+// ---------------------------------------------------------------------------
+constexpr int kTcGroups = 2;  // warpgroups per CTA (2: 0.205 ms learned stage at 1024^2; 4: 0.214; 1: 0.228)
+constexpr unsigned kColA = 0, kColD = 32, kColsPerGroup = 64;
+// shared memory per CTA for G warpgroups: more than 228 KB / (8/G + 1) with
+// the 1 KB the runtime reserves per CTA, so no more than 8/G CTAs fit
+template <int G>
+constexpr size_t tc_smem_bytes() { return G == 4 ? 80 * 1024 : (G == 2 ? 48 * 1024 : 28 * 1024); }
+
+struct TcSmem {
+    SensorRegion R;
+    // W1^T [32 n][64 k] and W2^T [32 n][32 k], BF16, K-major in 8 x 8 core
+    // matrices (8 rows of 16 bytes, 128 contiguous bytes each), core matrix
+    // (n/8, k/8) at ((n/8) * KG + k/8) * 128 bytes, KG = k-groups per row.
+    alignas(128) __nv_bfloat16 w1c[kSensorH * kSensorK];
+    alignas(128) __nv_bfloat16 w2c[kSensorH * kSensorH];
+    float b1[kSensorH], b2[kSensorH], w3[kSensorH], b3;
+    alignas(8) unsigned long long mbar;
+    unsigned taddr;
+};
+static_assert(sizeof(TcSmem) <= tc_smem_bytes<1>(), "tcgen05 sensor tile exceeds its shared memory");
+
+__host__ __device__ constexpr int core_index(int n, int k, int kgroups)
+{
+    return ((n >> 3) * kgroups + (k >> 3)) * 64 + (n & 7) * 8 + (k & 7);
+}
+
+// Shared-memory matrix descriptor (no swizzle, K-major core matrices):
+// start address, leading byte offset (between core matrices adjacent in K),
+// stride byte offset (between adjacent 8-row groups), descriptor version 1.
+__device__ __forceinline__ uint64_t tc_smem_desc(const void* p, unsigned lbo, unsigned sbo)
+{
+    const unsigned a = smem_addr(p);
+    return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulation, BF16 A and B, both
+// K-major, N = 32, M = 128.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kSensorH >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem d] (+)= A[tmem a] B[desc], issued by one thread.
+__device__ __forceinline__ void tc_mma(uint32_t d, uint32_t a, uint64_t bdesc, bool accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+        "r"(a), "l"(bdesc), "r"(kTcIdesc), "r"(accumulate ? 1 : 0)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(unsigned long long* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_st16(uint32_t taddr, const uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+// Wait for phase `parity` of the mbarrier: a tight spin first (an MMA round
+// trip takes a few hundred cycles), then polls spaced by sleeps, about a
+// second in all; false if it gave up.
+__device__ __forceinline__ bool mbar_wait_parity_bounded(unsigned long long* bar, unsigned parity)
+{
+    for (int it = 0; it < (1 << 12); ++it)
+        if (mbar_test(bar, parity)) return true;
+    for (int it = 0; it < (1 << 24); ++it) {
+        if (mbar_test(bar, parity)) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
+// Warp 0 waits for the MMAs' completion; the block barrier then releases the
+// other warps (which read the accumulators after their own fence). True on
+// every thread if the wait succeeded.
+__device__ __forceinline__ bool tc_wait_mmas(unsigned long long* bar, unsigned parity)
+{
+    bool done = true;
+    if ((threadIdx.x >> 5) == 0) done = mbar_wait_parity_bounded(bar, parity);
+    return __syncthreads_and(done) != 0;
+}
+
+// Set-up of a CTA: the weights in core-matrix order (read by the MMAs through
+// the async proxy), the mbarrier, and 64 G tensor-memory columns (warp 0).
+// Returns the columns' base address.
+template <int G>
+__device__ uint32_t tc_setup(const SensorDev* w, TcSmem& S)
+{
+    constexpr int kThreads = 128 * G;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kSensorH * kSensorK; i += kThreads) {
+        const int n = i / kSensorK, k = i - n * kSensorK;
+        S.w1c[core_index(n, k, kSensorK / 8)] = w->w1t[n * kW1Pitch + k];
+    }
+    for (int i = tid; i < kSensorH * kSensorH; i += kThreads) {
+        const int n = i / kSensorH, k = i - n * kSensorH;
+        S.w2c[core_index(n, k, kSensorH / 8)] = w->w2t[n * kW2Pitch + k];
+    }
+    if (tid < kSensorH) {
+        S.b1[tid] = w->b1[tid];
+        S.b2[tid] = w->b2[tid];
+        S.w3[tid] = w->w3[tid];
+    }
+    if (tid == 0) {
+        S.b3 = w->b3;
+        mbar_init(&S.mbar, 1);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if ((tid >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&S.taddr)),
+                     "r"(kColsPerGroup * G)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    return S.taddr;
+}
+
+// Release of the CTA's tensor-memory columns (after its last wait).
+template <int G>
+__device__ void tc_teardown(uint32_t tm)
+{
+    tc_fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kColsPerGroup * G)
+                     : "memory");
+    }
+}
+
+// One 32 x 16 tile: stage, then 4/G rounds of both layers. `phase` is the
+// mbarrier's next parity (two completions per round). False if a bounded wait
+// gave up (uniform over the CTA; the remaining rounds are skipped).
+template <int G>
+__device__ bool tc_tile(const SensorTileParams& P, const int tx0, const int ty0, TcSmem& S, const uint32_t tm,
+                        unsigned& phase)
+{
+    constexpr int kThreads = 128 * G;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const bool decide = P.dec != nullptr;
+    const int org = decide ? kDecOrigin : kGhost;
+    const int ni = decide ? P.g.ny + 2 * kDecOrigin : P.g.ny;
+    const int nj = decide ? P.g.nx + 2 * kDecOrigin : P.g.nx;
+    sensor_stage(P, tx0, ty0, org, true, S.R);  // ends with a block barrier
+    // this warp's quarter of the lanes, in its warpgroup's columns
+    const uint32_t lanes = ((uint32_t)((warp & 3) * 32) << 16) + kColsPerGroup * (uint32_t)(warp >> 2);
+    const uint64_t d1 = tc_smem_desc(S.w1c, 128, 128 * (kSensorK / 8));
+    const uint64_t d2 = tc_smem_desc(S.w2c, 128, 128 * (kSensorH / 8));
+    for (int round = 0; round < kTX * kTY / kThreads; ++round) {
+        const int c = round * kThreads + tid, cy = c / kTX, cx = c - cy * kTX;
+        const float* r = S.R.sr + (cy + kH) * kRW + (cx + kH);
+        const float* p = S.R.sp + (cy + kH) * kRW + (cx + kH);
+        const float sr = S.R.scr[c], sp = S.R.scp[c];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {  // features 32 half .. 32 half + 31
+            uint32_t a[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int k = 32 * half + 2 * j;
+                a[j] = pack_bf16(sensor_feature(r, p, kRW, sr, sp, k), sensor_feature(r, p, kRW, sr, sp, k + 1));
+            }
+            tc_st16(tm + lanes + kColA + 16 * half, a);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int ks = 0; ks < kSensorK / 16; ++ks)
+                    tc_mma(tm + kColsPerGroup * g + kColD, tm + kColsPerGroup * g + kColA + 8 * ks,
+                           d1 + (uint64_t)((256 * ks) >> 4), ks > 0);
+            tc_commit(&S.mbar);
+        }
+        if (!tc_wait_mmas(&S.mbar, phase)) return false;
+        phase ^= 1u;
+        tc_fence_after();
+        uint32_t h[16];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {  // hidden units 16 half .. 16 half + 15
+            uint32_t d[16];
+            tc_ld16(tm + lanes + kColD + 16 * half, d);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int n = 16 * half + 2 * j;
+                h[8 * half + j] = pack_bf16(fmaxf(__uint_as_float(d[2 * j]) + S.b1[n], 0.f),
+                                            fmaxf(__uint_as_float(d[2 * j + 1]) + S.b1[n + 1], 0.f));
+            }
+        }
+        tc_st16(tm + lanes + kColA, h);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int ks = 0; ks < kSensorH / 16; ++ks)
+                    tc_mma(tm + kColsPerGroup * g + kColD, tm + kColsPerGroup * g + kColA + 8 * ks,
+                           d2 + (uint64_t)((256 * ks) >> 4), ks > 0);
+            tc_commit(&S.mbar);
+        }
+        if (!tc_wait_mmas(&S.mbar, phase)) return false;
+        phase ^= 1u;
+        tc_fence_after();
+        float z = 0.f;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            uint32_t d[16];
+            tc_ld16(tm + lanes + kColD + 16 * half, d);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int n = 16 * half + j;
+                z += fmaxf(__uint_as_float(d[j]) + S.b2[n], 0.f) * S.w3[n];
+            }
+        }
+        const float pv = 1.f / (1.f + expf(-(z + S.b3)));
+        const int i = ty0 + cy, j = tx0 + cx;
+        if (i < ni && j < nj) {
+            if (decide)
+                P.dec[(long long)(i + org) * P.g.pitch + (j + org)] = pv > kSensorHi ? 1 : (pv < kSensorLo ? 0 : 2);
+            else
+                P.prob[(long long)i * P.g.nx + j] = pv;
+        }
+    }
+    return true;
+}
+
+// One CTA per tile of one grid.
+template <int G>
+__global__ void __launch_bounds__(128 * G, 8 / G) sensor_tc_kernel(const SensorTileParams P, unsigned* err)
+{
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    TcSmem& S = *reinterpret_cast<TcSmem*>(tc_raw);
+    const uint32_t tm = tc_setup<G>(P.w, S);
+    unsigned phase = 0;
+    const bool ok = tc_tile<G>(P, blockIdx.x * kTX, blockIdx.y * kTY, S, tm, phase);
+    tc_teardown<G>(tm);
+    if (!ok && threadIdx.x == 0 && err) atomicOr(err, kErrTimeout);
+}
+
+// Decision pass over every running case of a batch: one CTA per sensor tile
+// of the concatenated tile list (a persistent loop over tiles measured twice
+// as slow: its CTAs move through the staging and MMA phases in step). A CTA
+// of a stopped case returns before it allocates anything.
+template <int G>
+__global__ void __launch_bounds__(128 * G, 8 / G)
+    batch_sensor_tc_kernel(const BatchCase* __restrict__ cases, int ncases, int buf, const SensorDev* w)
+{
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    TcSmem& S = *reinterpret_cast<TcSmem*>(tc_raw);
+    const int tile = blockIdx.x;
+    int lo = 0, hi = ncases - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cases[mid].dtile_begin <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchCase& C = cases[lo];
+    if (C.ds->dt == 0.0) return;  // stopped case; uniform over the CTA
+    const int local = tile - C.dtile_begin;
+    const int ty = local / C.dtiles_x, tx = local - ty * C.dtiles_x;
+    SensorTileParams P;
+    P.g = C.g;
+    P.gamma = C.ph.gamma;
+    P.q = C.q[buf];
+    P.w = w;
+    P.prob = nullptr;
+    P.feat = nullptr;
+    P.label = nullptr;
+    P.target = nullptr;
+    P.dec = C.dec;
+    const uint32_t tm = tc_setup<G>(w, S);
+    unsigned phase = 0;
+    const bool ok = tc_tile<G>(P, tx * kTX, ty * kTY, S, tm, phase);
+    tc_teardown<G>(tm);
+    if (!ok && threadIdx.x == 0) atomicOr(&C.ds->err, kErrTimeout);
+}
+
+static cudaError_t launch_sensor_tc(const SensorTileParams& P, dim3 grid, unsigned* err, cudaStream_t s)
+{
+    constexpr size_t smem = tc_smem_bytes<kTcGroups>();
+    static PerDevice<int> configured;  // the shared-memory limit is raised once per device
+    int ok = 0;
+    cudaError_t e = configured.get(&ok, [](int* v) {
+        *v = 1;
+        return cudaFuncSetAttribute(sensor_tc_kernel<kTcGroups>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    });
+    if (e != cudaSuccess) return e;
+    sensor_tc_kernel<kTcGroups><<<grid, 128 * kTcGroups, smem, s>>>(P, err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sensor_tile(const Grid& g, double gamma, const double* q, const SensorDev* w, float* prob,
-                               void* feat_bf16, unsigned char* label, unsigned char* target, cudaStream_t s)
+                               void* feat_bf16, unsigned char* label, unsigned char* target, unsigned* err,
+                               cudaStream_t s)
 {
     SensorTileParams P;
     P.g = g;
@@ -210,7 +528,11 @@ cudaError_t launch_sensor_tile(const Grid& g, double gamma, const double* q, con
     P.target = target;
     P.dec = nullptr;
     dim3 grid((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY);
-    sensor_tile_kernel<<<grid, 256, 0, s>>>(P);
+    if (prob) {
+        if (!w || feat_bf16 || label || target) return cudaErrorInvalidValue;
+        return launch_sensor_tc(P, grid, err, s);
+    }
+    sensor_dataset_kernel<<<grid, 256, 0, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -222,7 +544,7 @@ void sensor_decide_tiles(const Grid& g, int* tiles_x, int* tiles)
 }
 
 cudaError_t launch_sensor_decide(const Grid& g, double gamma, const double* q, const SensorDev* w,
-                                 unsigned char* dec, cudaStream_t s)
+                                 unsigned char* dec, unsigned* err, cudaStream_t s)
 {
     if (!w || !dec) return cudaErrorInvalidValue;
     SensorTileParams P;
@@ -237,61 +559,23 @@ cudaError_t launch_sensor_decide(const Grid& g, double gamma, const double* q, c
     P.dec = dec;
     int tx, tiles;
     sensor_decide_tiles(g, &tx, &tiles);
-    dim3 grid(tx, tiles / tx);
-    sensor_tile_kernel<<<grid, 256, 0, s>>>(P);
-    return cudaGetLastError();
-}
-
-// Persistent decision pass over every running case of a batch: CTA k takes
-// sensor-pass tiles k, k + gridDim.x, ... of the concatenated tile list.
-__global__ void __launch_bounds__(256) batch_sensor_decide_kernel(const BatchCase* __restrict__ cases, int ncases,
-                                                                  int total_tiles, int buf, const SensorDev* w)
-{
-    __shared__ SensorTileSmem S;
-    load_sensor(&S.w, w);
-    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
-        int lo = 0, hi = ncases - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (cases[mid].dtile_begin <= tile) lo = mid;
-            else hi = mid - 1;
-        }
-        const BatchCase& C = cases[lo];
-        if (C.ds->dt == 0.0) continue;  // stopped case; uniform over the CTA
-        const int local = tile - C.dtile_begin;
-        const int ty = local / C.dtiles_x, tx = local - ty * C.dtiles_x;
-        SensorTileParams P;
-        P.g = C.g;
-        P.gamma = C.ph.gamma;
-        P.q = C.q[buf];
-        P.w = w;
-        P.prob = nullptr;
-        P.feat = nullptr;
-        P.label = nullptr;
-        P.target = nullptr;
-        P.dec = C.dec;
-        __syncthreads();  // the previous tile's readers of S are done
-        sensor_tile(P, tx * kTX, ty * kTY, S);
-    }
+    return launch_sensor_tc(P, dim3(tx, tiles / tx), err, s);
 }
 
 cudaError_t launch_batch_sensor_decide(const BatchCase* cases, int ncases, int total_tiles, int buf,
                                        const SensorDev* w, cudaStream_t s)
 {
-    static PerDevice<int> grid;  // resident CTAs per SM x SMs, per device
-    int blocks = 0;
-    cudaError_t e = grid.get(&blocks, [](int* v) {
-        int per_sm = 0, dev = 0, sms = 0;
-        cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sensor_decide_kernel, 256, 0);
-        if (r != cudaSuccess) return r;
-        if ((r = cudaGetDevice(&dev)) != cudaSuccess) return r;
-        if ((r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return r;
-        *v = (per_sm > 0 ? per_sm : 1) * sms;
-        return cudaSuccess;
+    constexpr size_t smem = tc_smem_bytes<kTcGroups>();
+    auto kern = batch_sensor_tc_kernel<kTcGroups>;
+    static PerDevice<int> configured;  // the shared-memory limit is raised once per device
+    int ok = 0;
+    cudaError_t e = configured.get(&ok, [&](int* v) {
+        *v = 1;
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     });
     if (e != cudaSuccess) return e;
-    if (total_tiles < 0) return cudaSuccess;  // prepare only
-    batch_sensor_decide_kernel<<<blocks, 256, 0, s>>>(cases, ncases, total_tiles, buf, w);
+    if (total_tiles <= 0) return cudaSuccess;  // prepare only (or nothing to do)
+    kern<<<total_tiles, 128 * kTcGroups, smem, s>>>(cases, ncases, buf, w);
     return cudaGetLastError();
 }
 
