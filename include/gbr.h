@@ -244,8 +244,9 @@ int gbr_get_timing(gbr_ctx *ctx, double *ms, int *launches, int *dropped);
  * [0.3, 0.7] the plain detector decides (per direction), and > 0.7 marks a
  * discontinuity whose direction the plain per-direction tests assign (both
  * directions if neither test marks the cell). The buffer of Eq. buffer is
- * unchanged. The network runs on the tensor cores with BF16
- * operands and FP32 accumulation, fused into the stage kernel.
+ * unchanged. The network runs on the tcgen05 tensor cores (BF16 operands,
+ * FP32 accumulation in tensor memory) in a decision pass launched before each
+ * FP32 stage; the stage kernel applies its per-cell decisions.
  * Weight vector (GBR_SENSOR_PARAMS floats): W1[50][32], b1[32], W2[32][32],
  * b2[32], w3[32], b3, with h1 = relu(x W1 + b1) rounded to BF16,
  * h2 = relu(h1 W2 + b2), p = 1/(1 + exp(-(h2 . w3 + b3))).
