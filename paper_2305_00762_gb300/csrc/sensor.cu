@@ -68,6 +68,8 @@ struct SensorRegion {
 // stages its primitives (clamped to the padded extent; clamped cells feed no
 // output), and, if `scales`, each cell's normalisation scales. Every thread of
 // the block takes part (block-wide barriers inside).
+__device__ void sensor_scales(SensorRegion& S);
+
 __device__ void sensor_stage(const SensorTileParams& P, const int tx0, const int ty0, const int org, bool scales,
                              SensorRegion& S)
 {
@@ -84,7 +86,11 @@ __device__ void sensor_stage(const SensorTileParams& P, const int tx0, const int
         S.sp[idx] = pr;
     }
     __syncthreads();
-    if (!scales) return;
+    if (scales) sensor_scales(S);
+}
+
+__device__ void sensor_scales(SensorRegion& S)
+{
     // Normalisation scales 1/(max_k |q_k - q_c| + floor) over each cell's
     // 5 x 5 window, from separable window maxima and minima: rounding is
     // monotone, so max_k RN(q_k - q_c) = RN(max_k q_k - q_c) (likewise for the
@@ -197,18 +203,29 @@ constexpr unsigned kColA = 0, kColD = 32, kColsPerGroup = 64;
 template <int G>
 constexpr size_t tc_smem_bytes() { return G == 4 ? 80 * 1024 : (G == 2 ? 48 * 1024 : 28 * 1024); }
 
+// Tensor copy of a tile's FP64 region: x from the region's first column
+// rounded down to even (16-byte aligned), 2 columns wider than the region.
+constexpr int kRawW = kRW + 2;
+constexpr size_t kRawBytes = sizeof(double) * 4 * kRawW * kRH;
+constexpr size_t kRegionScratch = sizeof(SensorRegion) - sizeof(float) * 2 * kRH * kRW;  // hr .. scp
+
 struct TcSmem {
-    SensorRegion R;
     // W1^T [32 n][64 k] and W2^T [32 n][32 k], BF16, K-major in 8 x 8 core
     // matrices (8 rows of 16 bytes, 128 contiguous bytes each), core matrix
     // (n/8, k/8) at ((n/8) * KG + k/8) * 128 bytes, KG = k-groups per row.
     alignas(128) __nv_bfloat16 w1c[kSensorH * kSensorK];
     alignas(128) __nv_bfloat16 w2c[kSensorH * kSensorH];
     float b1[kSensorH], b2[kSensorH], w3[kSensorH], b3;
-    alignas(8) unsigned long long mbar;
+    alignas(8) unsigned long long mbar, tma_bar;
     unsigned taddr;
+    // the tensor copy lands on R.hr .. R.scp and the tail after them (free
+    // until the window maxima are formed, after the conversion)
+    alignas(128) SensorRegion R;
+    unsigned char raw_tail[kRawBytes > kRegionScratch ? kRawBytes - kRegionScratch : 1];
 };
-static_assert(sizeof(TcSmem) <= tc_smem_bytes<1>(), "tcgen05 sensor tile exceeds its shared memory");
+static_assert(sizeof(TcSmem) <= tc_smem_bytes<kTcGroups>(), "tcgen05 sensor tile exceeds its shared memory");
+static_assert((sizeof(float) * 2 * kRH * kRW) % 128 == 0, "the copy's landing area must stay 128-byte aligned");
+static_assert(kRawW % 2 == 0 && kRawW <= 256 && kRH <= 256, "tensor copy box: 16-byte rows, at most 256 wide");
 
 __host__ __device__ constexpr int core_index(int n, int k, int kgroups)
 {
@@ -294,8 +311,8 @@ __device__ __forceinline__ bool tc_wait_mmas(unsigned long long* bar, unsigned p
 }
 
 // Set-up of a CTA: the weights in core-matrix order (read by the MMAs through
-// the async proxy), the mbarrier, and 64 G tensor-memory columns (warp 0).
-// Returns the columns' base address.
+// the async proxy) and 64 G tensor-memory columns (warp 0). The MMA mbarrier
+// is initialised by the kernel before. Returns the columns' base address.
 template <int G>
 __device__ uint32_t tc_setup(const SensorDev* w, TcSmem& S)
 {
@@ -314,10 +331,7 @@ __device__ uint32_t tc_setup(const SensorDev* w, TcSmem& S)
         S.b2[tid] = w->b2[tid];
         S.w3[tid] = w->w3[tid];
     }
-    if (tid == 0) {
-        S.b3 = w->b3;
-        mbar_init(&S.mbar, 1);
-    }
+    if (tid == 0) S.b3 = w->b3;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if ((tid >> 5) == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&S.taddr)),
@@ -344,9 +358,10 @@ __device__ void tc_teardown(uint32_t tm)
     }
 }
 
-// One 32 x 16 tile: stage, then 4/G rounds of both layers. `phase` is the
-// mbarrier's next parity (two completions per round). False if a bounded wait
-// gave up (uniform over the CTA; the remaining rounds are skipped).
+// One 32 x 16 tile whose region and scales are staged: 4/G rounds of both
+// layers. `phase` is the mbarrier's next parity (two completions per round).
+// False if a bounded wait gave up (uniform over the CTA; the remaining rounds
+// are skipped).
 template <int G>
 __device__ bool tc_tile(const SensorTileParams& P, const int tx0, const int ty0, TcSmem& S, const uint32_t tm,
                         unsigned& phase)
@@ -357,7 +372,6 @@ __device__ bool tc_tile(const SensorTileParams& P, const int tx0, const int ty0,
     const int org = decide ? kDecOrigin : kGhost;
     const int ni = decide ? P.g.ny + 2 * kDecOrigin : P.g.ny;
     const int nj = decide ? P.g.nx + 2 * kDecOrigin : P.g.nx;
-    sensor_stage(P, tx0, ty0, org, true, S.R);  // ends with a block barrier
     // this warp's quarter of the lanes, in its warpgroup's columns
     const uint32_t lanes = ((uint32_t)((warp & 3) * 32) << 16) + kColsPerGroup * (uint32_t)(warp >> 2);
     const uint64_t d1 = tc_smem_desc(S.w1c, 128, 128 * (kSensorK / 8));
@@ -447,17 +461,61 @@ __device__ bool tc_tile(const SensorTileParams& P, const int tx0, const int ty0,
     return true;
 }
 
-// One CTA per tile of one grid.
+// One CTA per tile of one grid. The region arrives by one tensor copy (tmap:
+// box kRawW x kRH x 4 of the padded state), issued before the weights are
+// staged and the tensor memory is allocated, so the three overlap.
 template <int G>
-__global__ void __launch_bounds__(128 * G, 8 / G) sensor_tc_kernel(const SensorTileParams P, unsigned* err)
+__global__ void __launch_bounds__(128 * G, 8 / G)
+    sensor_tc_kernel(const SensorTileParams P, unsigned* err, const __grid_constant__ CUtensorMap tmap)
 {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>(tc_raw);
+    const int tid = threadIdx.x;
+    const int tx0 = blockIdx.x * kTX, ty0 = blockIdx.y * kTY;
+    const int org = P.dec ? kDecOrigin : kGhost;
+    const int gx0 = tx0 + org - kH, gy0 = ty0 + org - kH;  // padded coordinates of region cell (0, 0)
+    const int xa = gx0 & ~1, ox = gx0 - xa;                // 16-byte aligned copy origin
+    double* raw = reinterpret_cast<double*>(S.R.hr);
+    const bool tma = (smem_addr(raw) & 127u) == 0;         // uniform: the copy needs 128-byte alignment
+    if (tid == 0) {
+        mbar_init(&S.mbar, 1);
+        mbar_init(&S.tma_bar, 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (tma && tid == 0) {
+        mbar_arrive_expect_tx(&S.tma_bar, (unsigned)kRawBytes);
+        tma_load_3d(raw, &tmap, xa, gy0, 0, &S.tma_bar);
+    }
     const uint32_t tm = tc_setup<G>(P.w, S);
+    bool ok = true;
+    if (tma) {
+        ok = __syncthreads_and(mbar_wait_bounded(&S.tma_bar)) != 0;
+        if (!ok) {
+            mbar_wait_bounded(&S.tma_bar);  // one more bounded wait for the copy before the CTA leaves
+        } else {
+            // cells beyond the padded extent read as zero and only feed
+            // outputs that are never stored
+            const float gm1 = (float)(P.gamma - 1.0);
+            constexpr int plane = kRawW * kRH;
+            for (int idx = tid; idx < kRH * kRW; idx += blockDim.x) {
+                const int ry = idx / kRW, rx = idx - ry * kRW;
+                const int o = ry * kRawW + rx + ox;
+                float r, u, v, pr;
+                prims_of(raw[o], raw[plane + o], raw[2 * plane + o], raw[3 * plane + o], gm1, r, u, v, pr);
+                S.R.sr[idx] = r;
+                S.R.sp[idx] = pr;
+            }
+            __syncthreads();
+            sensor_scales(S.R);
+        }
+    } else {
+        sensor_stage(P, tx0, ty0, org, true, S.R);
+    }
     unsigned phase = 0;
-    const bool ok = tc_tile<G>(P, blockIdx.x * kTX, blockIdx.y * kTY, S, tm, phase);
+    if (ok) ok = tc_tile<G>(P, tx0, ty0, S, tm, phase);
     tc_teardown<G>(tm);
-    if (!ok && threadIdx.x == 0 && err) atomicOr(err, kErrTimeout);
+    if (!ok && tid == 0 && err) atomicOr(err, kErrTimeout);
 }
 
 // Decision pass over every running case of a batch: one CTA per sensor tile
@@ -491,7 +549,9 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
     P.label = nullptr;
     P.target = nullptr;
     P.dec = C.dec;
-    const uint32_t tm = tc_setup<G>(w, S);
+    if (threadIdx.x == 0) mbar_init(&S.mbar, 1);
+    const uint32_t tm = tc_setup<G>(w, S);  // its barriers order the initialisation
+    sensor_stage(P, tx * kTX, ty * kTY, kDecOrigin, true, S.R);
     unsigned phase = 0;
     const bool ok = tc_tile<G>(P, tx * kTX, ty * kTY, S, tm, phase);
     tc_teardown<G>(tm);
@@ -509,7 +569,9 @@ static cudaError_t launch_sensor_tc(const SensorTileParams& P, dim3 grid, unsign
                                     (int)smem);
     });
     if (e != cudaSuccess) return e;
-    sensor_tc_kernel<kTcGroups><<<grid, 128 * kTcGroups, smem, s>>>(P, err);
+    CUtensorMap map;
+    if ((e = encode_state_map(P.g, P.q, kRawW, kRH, &map)) != cudaSuccess) return e;
+    sensor_tc_kernel<kTcGroups><<<grid, 128 * kTcGroups, smem, s>>>(P, err, map);
     return cudaGetLastError();
 }
 
