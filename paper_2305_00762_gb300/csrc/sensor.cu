@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(256) sensor_dataset_kernel(const SensorTilePar
 // on one another. Every mbarrier wait is bounded; on a timeout the CTA reports
 // kErrTimeout, skips its remaining rounds and still frees its columns.
 // ---------------------------------------------------------------------------
-constexpr int kTcGroups = 2;  // warpgroups per CTA (2: 0.205 ms learned stage at 1024^2; 4: 0.214; 1: 0.228)
+constexpr int kTcGroups = 2;  // warpgroups per CTA (measured fastest of 1, 2 and 4)
 constexpr unsigned kColA = 0, kColD = 32, kColsPerGroup = 64;
 // shared memory per CTA for G warpgroups: more than 228 KB / (8/G + 1) with
 // the 1 KB the runtime reserves per CTA, so no more than 8/G CTAs fit
