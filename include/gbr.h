@@ -131,7 +131,12 @@ typedef enum {
      * wait for 16 bytes more than its tile copy delivers, so each CTA's
      * bounded staging wait gives up (after a few seconds) and the next
      * synchronising call reports GBR_ERR_TIMEOUT; the copy itself completes,
-     * nothing faults, and gbr_set_state clears the error. 0: off (default). */
+     * nothing faults, and gbr_set_state clears the error. 2: the learned
+     * sensor's decision pass (FP32 with the sensor on) withholds its first
+     * batch of tensor-core MMAs, so each CTA's bounded wait for their
+     * completion gives up (no MMA is in flight; its tensor memory is freed)
+     * and the next synchronising call reports GBR_ERR_TIMEOUT in the same
+     * way. 0: off (default). */
     GBR_OPT_STALL_TEST = 6,
     /* Riemann solver of Eq. Riemann_revisit: 0 = HLLC (default); 1 = the
      * shock-stable HLLC of Fleischmann, Adami and Adams (2020), which

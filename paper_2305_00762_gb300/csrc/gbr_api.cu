@@ -183,7 +183,7 @@ StageParams stage_params(gbr_ctx* c, const double* q)
     p.sigx = c->record_flags ? c->sigx : nullptr;
     p.sigy = c->record_flags ? c->sigy : nullptr;
     p.sensor = (c->sensor && c->precision == 32) ? c->d_sensor : nullptr;
-    p.stall_bytes = c->stall_test ? 16u : 0u;
+    p.stall_bytes = c->stall_test == 1 ? 16u : 0u;
     return p;
 }
 
@@ -194,7 +194,8 @@ int stage(gbr_ctx* c, const StageParams& p)
     if (c->precision == 32 && p.sensor) {
         StageParams q = p;
         q.dec = c->dec;
-        cudaError_t e = launch_sensor_decide(c->g, c->ph.gamma, p.q, p.sensor, c->dec, p.err, c->stream);
+        cudaError_t e =
+            launch_sensor_decide(c->g, c->ph.gamma, p.q, p.sensor, c->dec, p.err, c->stall_test == 2, c->stream);
         if (e == cudaSuccess) e = launch_stage_f32(q, c->stream);
         return cuda_status(e);
     }
@@ -491,7 +492,7 @@ int gbr_set_option(gbr_ctx* c, int key, double val)
         c->ph.cons = (int)val;
         return GBR_OK;
     case GBR_OPT_STALL_TEST:
-        if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;
+        if (val != 0.0 && val != 1.0 && val != 2.0) return GBR_ERR_ARG;
         c->stall_test = (int)val;
         return GBR_OK;
     case GBR_OPT_RIEMANN:

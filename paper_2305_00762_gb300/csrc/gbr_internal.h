@@ -163,9 +163,11 @@ cudaError_t launch_sensor_tile(const Grid& g, double gamma, const double* q, con
 // The learned sensor's decision pass of one padded state (ghosts filled), on
 // the tcgen05 tensor cores: dec[y * pitch + x] for padded cells x in
 // [3, nx + 9), y in [3, ny + 9): 1 = discontinuity (p > 0.7), 0 = smooth
-// (p < 0.3), 2 = unsure. A wait that gives up sets kErrTimeout in *err.
+// (p < 0.3), 2 = unsure. A wait that gives up sets kErrTimeout in *err;
+// stall != 0 (failure-detection test) withholds the first MMA batch so that
+// its bounded wait gives up.
 cudaError_t launch_sensor_decide(const Grid& g, double gamma, const double* q, const SensorDev* w,
-                                 unsigned char* dec, unsigned* err, cudaStream_t s);
+                                 unsigned char* dec, unsigned* err, int stall, cudaStream_t s);
 // Sensor-pass tiles of a grid (the tile grid over its decision region).
 void sensor_decide_tiles(const Grid& g, int* tiles_x, int* tiles);
 // The decision pass of buffer `buf` of every running case of a batch (one

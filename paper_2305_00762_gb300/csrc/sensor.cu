@@ -55,6 +55,7 @@ struct SensorTileParams {
     unsigned char* label;   // [ny*nx] plain-detector label, or nullptr
     unsigned char* target;  // [ny*nx] soft target in units of 1/255, or nullptr
     unsigned char* dec;     // decision-region mode: decisions (padded layout), else nullptr
+    int stall;              // failure-detection test: withhold the first MMA batch (its wait gives up)
 };
 
 // The staged region of one tile and the per-cell normalisation scales.
@@ -394,7 +395,7 @@ __device__ bool tc_tile(const SensorTileParams& P, const int tx0, const int ty0,
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && !(P.stall && round == 0)) {
             tc_fence_after();
 #pragma unroll
             for (int g = 0; g < G; ++g)
@@ -549,6 +550,7 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
     P.label = nullptr;
     P.target = nullptr;
     P.dec = C.dec;
+    P.stall = 0;
     if (threadIdx.x == 0) mbar_init(&S.mbar, 1);
     const uint32_t tm = tc_setup<G>(w, S);  // its barriers order the initialisation
     sensor_stage(P, tx * kTX, ty * kTY, kDecOrigin, true, S.R);
@@ -589,6 +591,7 @@ cudaError_t launch_sensor_tile(const Grid& g, double gamma, const double* q, con
     P.label = label;
     P.target = target;
     P.dec = nullptr;
+    P.stall = 0;
     dim3 grid((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY);
     if (prob) {
         if (!w || feat_bf16 || label || target) return cudaErrorInvalidValue;
@@ -606,7 +609,7 @@ void sensor_decide_tiles(const Grid& g, int* tiles_x, int* tiles)
 }
 
 cudaError_t launch_sensor_decide(const Grid& g, double gamma, const double* q, const SensorDev* w,
-                                 unsigned char* dec, unsigned* err, cudaStream_t s)
+                                 unsigned char* dec, unsigned* err, int stall, cudaStream_t s)
 {
     if (!w || !dec) return cudaErrorInvalidValue;
     SensorTileParams P;
@@ -619,6 +622,7 @@ cudaError_t launch_sensor_decide(const Grid& g, double gamma, const double* q, c
     P.label = nullptr;
     P.target = nullptr;
     P.dec = dec;
+    P.stall = stall;
     int tx, tiles;
     sensor_decide_tiles(g, &tx, &tiles);
     return launch_sensor_tc(P, dim3(tx, tiles / tx), err, s);

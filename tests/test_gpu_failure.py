@@ -48,3 +48,27 @@ def test_staging_wait_gives_up_and_context_recovers(env, precision):
     else:
         assert np.abs(R - Ro).max() < 1e-4 * np.abs(Ro).max()
     s.close()
+
+
+def test_tensor_core_wait_gives_up_and_context_recovers(env):
+    """The learned sensor's decision pass waits, bounded, for its tcgen05
+    MMAs; with GBR_OPT_STALL_TEST = 2 the first MMA batch is withheld, the
+    wait gives up, the CTA frees its tensor memory and the call reports
+    GBR_ERR_TIMEOUT; nothing faults and the context keeps working."""
+    torch, O, gbr = env
+    from paper_2305_00762_gb300 import sensor_train
+    w = sensor_train.load_weights()
+    c = C.isentropic_vortex(32)
+    s = gbr.Solver.for_case(c, precision=32)
+    s.set_state(c.Q)
+    s.set_sensor(w)
+    R0 = s.residual()
+    gbr.gbr_set_option(s.ctx, gbr.GBR_OPT_STALL_TEST, 2)
+    with pytest.raises(gbr.GbrError) as e:
+        s.residual()
+    assert e.value.status == gbr.GBR_ERR_TIMEOUT
+    gbr.gbr_set_option(s.ctx, gbr.GBR_OPT_STALL_TEST, 0)
+    s.set_state(c.Q)
+    assert s.sync() == gbr.GBR_OK
+    assert np.array_equal(s.residual(), R0)   # the same decisions as before the stall
+    s.close()
