@@ -83,3 +83,13 @@ def test_degenerate_sizes_and_options_rejected(lib):
     assert lib.gbr_step_static(ctypes.c_void_p(16), ctypes.c_void_p(16), 4096, 4096, ctypes.c_double(1.4),
                                ctypes.c_double(0.0), ctypes.c_double(0.72), ctypes.byref(big),
                                ctypes.c_double(1e-3), None) == gbr.GBR_ERR_ARG
+
+
+def test_fma_probe_library_exports_its_entry():
+    """The benchmark's FMA-throughput probe is its own library; it builds and
+    exports gbr_probe_fma_gflops (no compute without a GPU)."""
+    import ctypes
+    from paper_2305_00762_gb300 import build as B
+    B.build()
+    L = ctypes.CDLL(B.PROBE_LIB)
+    assert hasattr(L, "gbr_probe_fma_gflops")

@@ -163,3 +163,23 @@ def test_riemann_flag_is_checked(oracle_mod):
     c = C.free_stream(16, 16)
     with pytest.raises(RuntimeError):
         O.residual(_cfg(O, c, 2), c.Q)
+
+
+def test_odd_even_shock_is_a_rankine_hugoniot_shock():
+    """The generator's states: in the frame moving at the shock speed, mass,
+    momentum and energy fluxes agree across the jump (to roundoff), and the
+    pre-shock Mach number relative to the shock is the requested one."""
+    c = C.odd_even_shock(64, 4, mach=6.0, noise=0.0)
+    Q = c.Q
+    us = c.meta["shock_speed"]
+
+    def fluxes(j):
+        r, mu, E = Q[0, 0, j], Q[1, 0, j], Q[3, 0, j]
+        u = mu / r
+        p = (G - 1) * (E - 0.5 * r * u * u)
+        w = u - us
+        return np.array([r * w, r * w * w + p, w * (E - r * u * us + 0.5 * r * us * us + p)]), r, p, w
+    f2, r2, p2, _ = fluxes(0)       # behind the shock
+    f1, r1, p1, w1 = fluxes(63)     # gas at rest ahead of it
+    assert np.allclose(f1, f2, rtol=1e-13, atol=1e-12 * np.abs(f1).max())
+    assert abs(-w1 / np.sqrt(G * p1 / r1) - 6.0) < 1e-12
