@@ -311,3 +311,46 @@ def test_viscous_shock_tube_time_step(env):
         s.step_cfl(0.5)
     assert s.sync(allow=(gbr.GBR_ERR_NONPHYSICAL,)) == gbr.GBR_ERR_NONPHYSICAL
     s.close()
+
+
+def _rough_low_mach(n, seed):
+    """Seeded cell-to-cell random rho, p in [0.5, 1.5] and u, v ~ N(0, 0.02)
+    on the periodic unit square: low-Mach jumps on every face (the
+    shock-stable flux's phi < 1 everywhere, the detector flagging many
+    faces)."""
+    rng = np.random.default_rng(seed)
+    r, p = rng.uniform(0.5, 1.5, (n, n)), rng.uniform(0.5, 1.5, (n, n))
+    u, v = rng.normal(0, 0.02, (n, n)), rng.normal(0, 0.02, (n, n))
+    Q = np.ascontiguousarray(C.prim_to_cons(r, u, v, p, 1.4))
+    return C.Case("rough_low_mach", Q, 1.0 / n, 1.0 / n, 1.4, 0.0, 0.72, (C.BC_PERIODIC,) * 4)
+
+
+VARIANTS = {"cons_riemann1024": (lambda: C.riemann_2d(1024), {"cons": True}, {"cons": 1}),
+            "order4_riemann1024": (lambda: C.riemann_2d(1024), {"order": 4}, {"order": 4}),
+            "hllc_lm_rough1024": (lambda: _rough_low_mach(1024, 21), {"riemann": 1}, {"riemann": 1})}
+
+
+@pytest.mark.parametrize("which", list(VARIANTS))
+def test_full_size_variants_sampled(env, which):
+    """The scheme variants the benchmark times on 1024^2 grids (MEG7-cons,
+    the fourth-order member, the shock-stable HLLC-LM), in its launch
+    configuration: the residual at sampled cells (every boundary cell plus
+    random interior ones near the jumps) against the oracle's, computed one
+    by one from the same state."""
+    torch, O, gbr = env
+    make, kw, okw = VARIANTS[which]
+    c = make()
+    cfg = O.Config(c.nx, c.ny, c.dx, c.dy, c.gamma, c.mu, c.Pr, c.bc, okw.get("order", 7), okw.get("cons", 0),
+                   riemann=okw.get("riemann", 0))
+    s = gbr.Solver.for_case(c, **kw)
+    s.set_state(c.Q)
+    R = s.residual()
+    mask = _sample_mask(c.Q, np.random.default_rng(8))
+    Ro = O.residual(cfg, c.Q, mask=mask)
+    sel = mask.astype(bool)
+    sc = residual_scales(c.Q, c.dx, c.dy, c.gamma)
+    sc = [max(sc[m], np.abs(Ro[m][sel]).max()) for m in range(4)]
+    errs = [np.abs(R[m][sel] - Ro[m][sel]).max() / sc[m] for m in range(4)]
+    assert max(np.abs(Ro[m][sel]).max() for m in range(4)) > 0
+    assert max(errs) <= TOL64, errs
+    s.close()
