@@ -10,9 +10,11 @@ The arithmetic lives in ``meg7_oracle.c`` (plain loops, FP64,
 numpy arrays through ctypes.
 
 Parity status of each function (see the pins in ``tests/test_oracle_*.py``):
-the scalar building blocks, the detector, HLLC, the residual and the RK3 step
-are pinned; the choices the paper leaves open (characteristic projection
-state, HLLC wave-speed bounds, 2D viscous cross terms, ghost-layer count) are
+the scalar building blocks (each MP bound of Eq. mp-procedure on its own, the
+characteristic eigenvector matrices), the detector, HLLC, the residual and
+the RK3 step are pinned; the choices the paper leaves open (the state the
+characteristic projection is frozen at, HLLC wave-speed bounds, 2D viscous
+cross terms, ghost-layer count) are
 "parity unpinned" with respect to the paper's intent, because the paper prints
 no number that depends on them alone.
 """
@@ -108,6 +110,8 @@ def lib():
             L.or_fill_ghosts_padded.argtypes = [cp, dp]
             L.or_cons_eigenvectors.restype = None
             L.or_cons_eigenvectors.argtypes = [ctypes.c_double, dp, dp, dp]
+            L.or_prim_eigenvectors.restype = None
+            L.or_prim_eigenvectors.argtypes = [ctypes.c_double, dp, dp, dp]
             L.or_trouble_labels.restype = ctypes.c_int
             L.or_trouble_labels.argtypes = [cp, dp, u8]
             L.or_psi_min.restype = ctypes.c_int
@@ -269,10 +273,21 @@ def fill_ghosts_padded(cfg: Config, Qp) -> np.ndarray:
 
 def cons_eigenvectors(gamma, w):
     """(L, R) eigenvector matrices of the conservative x-flux Jacobian at
-    primitive state w = (rho, u, v, p)."""
+    primitive state w = (rho, u, v, p), as the MEG7-cons face projection
+    uses them (rows of L, columns of R)."""
     L = np.zeros(16)
     R = np.zeros(16)
     lib().or_cons_eigenvectors(float(gamma), _dp(_vec(w, 4)), _dp(L), _dp(R))
+    return L.reshape(4, 4), R.reshape(4, 4)
+
+
+def prim_eigenvectors(gamma, w):
+    """(L, R) eigenvector matrices of the primitive-variable x-Jacobian at
+    primitive state w = (rho, u, v, p), as the MEG7-prim face projection
+    uses them (reading R2; rows of L, columns of R)."""
+    L = np.zeros(16)
+    R = np.zeros(16)
+    lib().or_prim_eigenvectors(float(gamma), _dp(_vec(w, 4)), _dp(L), _dp(R))
     return L.reshape(4, 4), R.reshape(4, 4)
 
 

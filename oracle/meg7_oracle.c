@@ -484,6 +484,53 @@ static void prim_gradient_from_cons(double gamma, const double *q, const double 
     dw[3] = (gamma - 1.0) * (dq[3] - u * dq[1] - v * dq[2] + 0.5 * (u * u + v * v) * dq[0]);
 }
 
+/* Left (rows of L) and right (columns of R) eigenvector matrices of the
+ * x-direction flux Jacobian at the mean primitive state wb = (rho, u, v, p)
+ * of a face, with c = sqrt(gamma p / rho).
+ * cons = 0, reading R2 (end of Sec. 2.3, characteristic projection of the
+ * primitive variables): the Jacobian of the primitive form U_t + A U_x = 0,
+ * A = [[u, rho, 0, 0], [0, u, 0, 1/rho], [0, 0, u, 0], [0, rho c^2, 0, u]].
+ * cons = 1, reading R20: the Jacobian dF/dQ of the conservative x-flux, with
+ * H = c^2/(gamma-1) + (u^2+v^2)/2. Both diagonalise to (u-c, u, u, u+c). */
+static void char_eigenvectors(int cons, double g, const double *wb, double Lm[4][4], double Rm[4][4])
+{
+    double rb = wb[0], pb = wb[3];
+    double cb = sqrt(g * pb / rb);
+    if (!cons) {
+        const double L0[4][4] = {
+            {0.0, -rb / (2.0 * cb), 0.0, 1.0 / (2.0 * cb * cb)},
+            {1.0, 0.0, 0.0, -1.0 / (cb * cb)},
+            {0.0, 0.0, 1.0, 0.0},
+            {0.0, rb / (2.0 * cb), 0.0, 1.0 / (2.0 * cb * cb)},
+        };
+        const double R0[4][4] = {/* columns are the right eigenvectors */
+                                 {1.0, 1.0, 0.0, 1.0},
+                                 {-cb / rb, 0.0, 0.0, cb / rb},
+                                 {0.0, 0.0, 1.0, 0.0},
+                                 {cb * cb, 0.0, 0.0, cb * cb}};
+        memcpy(Lm, L0, sizeof(L0));
+        memcpy(Rm, R0, sizeof(R0));
+    } else {
+        double ub = wb[1], vb = wb[2];
+        double q2 = ub * ub + vb * vb;
+        double Hb = cb * cb / (g - 1.0) + 0.5 * q2;
+        double b1 = (g - 1.0) / (cb * cb), b2 = 0.5 * q2 * b1;
+        const double L1[4][4] = {
+            {0.5 * (b2 + ub / cb), -0.5 * (b1 * ub + 1.0 / cb), -0.5 * b1 * vb, 0.5 * b1},
+            {1.0 - b2, b1 * ub, b1 * vb, -b1},
+            {-vb, 0.0, 1.0, 0.0},
+            {0.5 * (b2 - ub / cb), -0.5 * (b1 * ub - 1.0 / cb), -0.5 * b1 * vb, 0.5 * b1},
+        };
+        const double R1[4][4] = {/* columns r1..r4 */
+                                 {1.0, 1.0, 0.0, 1.0},
+                                 {ub - cb, ub, 0.0, ub + cb},
+                                 {vb, vb, 1.0, vb},
+                                 {Hb - ub * cb, 0.5 * q2, vb, Hb + ub * cb}};
+        memcpy(Lm, L1, sizeof(L1));
+        memcpy(Rm, R1, sizeof(R1));
+    }
+}
+
 static void face_flux(const or_cfg *c, const double *const P[4], const double *const Cq[4], ptrdiff_t at,
                       ptrdiff_t s, ptrdiff_t st, double dn, double dtn, double *Fh, int *sigma_out)
 {
@@ -527,43 +574,10 @@ static void face_flux(const or_cfg *c, const double *const P[4], const double *c
 
     /* Reading R2: eigenvectors of the primitive Jacobian at the mean state
      * (R20: of the conservative Jacobian for MEG7-cons). */
-    double rb = 0.5 * (U[5][0] + U[6][0]);
-    double pb = 0.5 * (U[5][3] + U[6][3]);
-    double cb = sqrt(g * pb / rb);
+    double wb[4] = {0.5 * (U[5][0] + U[6][0]), 0.5 * (U[5][1] + U[6][1]), 0.5 * (U[5][2] + U[6][2]),
+                    0.5 * (U[5][3] + U[6][3])};
     double Lm[4][4], Rm[4][4];
-    if (!c->cons) {
-        const double L0[4][4] = {
-            {0.0, -rb / (2.0 * cb), 0.0, 1.0 / (2.0 * cb * cb)},
-            {1.0, 0.0, 0.0, -1.0 / (cb * cb)},
-            {0.0, 0.0, 1.0, 0.0},
-            {0.0, rb / (2.0 * cb), 0.0, 1.0 / (2.0 * cb * cb)},
-        };
-        const double R0[4][4] = {/* columns are the right eigenvectors */
-                                 {1.0, 1.0, 0.0, 1.0},
-                                 {-cb / rb, 0.0, 0.0, cb / rb},
-                                 {0.0, 0.0, 1.0, 0.0},
-                                 {cb * cb, 0.0, 0.0, cb * cb}};
-        memcpy(Lm, L0, sizeof(Lm));
-        memcpy(Rm, R0, sizeof(Rm));
-    } else {
-        double ub = 0.5 * (U[5][1] + U[6][1]), vb = 0.5 * (U[5][2] + U[6][2]);
-        double q2 = ub * ub + vb * vb;
-        double Hb = cb * cb / (g - 1.0) + 0.5 * q2;
-        double b1 = (g - 1.0) / (cb * cb), b2 = 0.5 * q2 * b1;
-        const double L1[4][4] = {
-            {0.5 * (b2 + ub / cb), -0.5 * (b1 * ub + 1.0 / cb), -0.5 * b1 * vb, 0.5 * b1},
-            {1.0 - b2, b1 * ub, b1 * vb, -b1},
-            {-vb, 0.0, 1.0, 0.0},
-            {0.5 * (b2 - ub / cb), -0.5 * (b1 * ub - 1.0 / cb), -0.5 * b1 * vb, 0.5 * b1},
-        };
-        const double R1[4][4] = {/* columns r1..r4 */
-                                 {1.0, 1.0, 0.0, 1.0},
-                                 {ub - cb, ub, 0.0, ub + cb},
-                                 {vb, vb, 1.0, vb},
-                                 {Hb - ub * cb, 0.5 * q2, vb, Hb + ub * cb}};
-        memcpy(Lm, L1, sizeof(Lm));
-        memcpy(Rm, R1, sizeof(Rm));
-    }
+    char_eigenvectors(c->cons, g, wb, Lm, Rm);
     /* characteristic values and gradients of cells j-2..j+3 */
     double Wc[6][4], Wd[6][4];
     for (int k = 0; k < 6; ++k) {
@@ -966,23 +980,23 @@ int or_psi_min(const or_cfg *c, const double *Q, double *psi)
     return OR_OK;
 }
 
-/* Pin helper: the left (rows) and right (columns) eigenvector matrices of
- * the x-direction conservative flux Jacobian at primitive state w (R20). */
+/* Pin helpers: the eigenvector matrices face_flux uses (char_eigenvectors),
+ * L row-major (rows = left eigenvectors), R row-major (columns = right
+ * eigenvectors), at primitive state w. */
+void or_prim_eigenvectors(double g, const double *w, double *L, double *R)
+{
+    double Lm[4][4], Rm[4][4];
+    char_eigenvectors(0, g, w, Lm, Rm);
+    memcpy(L, Lm, sizeof(Lm));
+    memcpy(R, Rm, sizeof(Rm));
+}
+
 void or_cons_eigenvectors(double g, const double *w, double *L, double *R)
 {
-    double ub = w[1], vb = w[2], cb = sqrt(g * w[3] / w[0]);
-    double q2 = ub * ub + vb * vb, Hb = cb * cb / (g - 1.0) + 0.5 * q2;
-    double b1 = (g - 1.0) / (cb * cb), b2 = 0.5 * q2 * b1;
-    const double L1[16] = {0.5 * (b2 + ub / cb), -0.5 * (b1 * ub + 1.0 / cb), -0.5 * b1 * vb, 0.5 * b1,
-                           1.0 - b2, b1 * ub, b1 * vb, -b1,
-                           -vb, 0.0, 1.0, 0.0,
-                           0.5 * (b2 - ub / cb), -0.5 * (b1 * ub - 1.0 / cb), -0.5 * b1 * vb, 0.5 * b1};
-    const double R1[16] = {1.0, 1.0, 0.0, 1.0,
-                           ub - cb, ub, 0.0, ub + cb,
-                           vb, vb, 1.0, vb,
-                           Hb - ub * cb, 0.5 * q2, vb, Hb + ub * cb};
-    memcpy(L, L1, sizeof(L1));
-    memcpy(R, R1, sizeof(R1));
+    double Lm[4][4], Rm[4][4];
+    char_eigenvectors(1, g, w, Lm, Rm);
+    memcpy(L, Lm, sizeof(Lm));
+    memcpy(R, Rm, sizeof(Rm));
 }
 
 /* Pin helper: fill ghosts of a padded state given as 4 planes of

@@ -264,3 +264,116 @@ def test_hllc_stationary_contact_and_consistency(oracle_mod):
     W = np.array([1.3, 0.4, -0.2, 0.9])
     F, _ = _euler_flux(g, W)
     assert np.abs(oracle_mod.hllc(g, W, W, F, F) - F).max() < 1e-15
+
+
+# ------------------------------------- MP bounds: closed forms (Sec. 2.3) ----
+# Each case makes one bound of Eq. mp-procedure the binding one, so that the
+# limited left value at j+1/2 equals a value fixed by that bound alone.
+# phi, dphi: Phi_{j-2..j+2} and the dx-scaled Phi'_{j-2..j+2}. The curvatures
+# d_k of Eq. mp-procedure are noted beside each case; the gradients are chosen
+# so that the minmod in MD (of d_j, d_{j+1}) or in LC (of d_j, d_{j-1}) is
+# decided by one named curvature, while the other pairing would give 0. In
+# every case the GRB value lies beyond the binding bound, so the MP test
+# (Eq. mp5Condition) fails and the limiter returns that bound.
+MP_BOUND_CASES = {
+    # Gentle rise Phi_j - Phi_{j-1} = 0.01 then a steep one: the upper limit
+    # UL = Phi_j + xi (Phi_j - Phi_{j-1}), xi = 7 (Eq. alpha), binds.
+    # d_{j-1} = -0.48, d_j = 17.96: LC = Phi_j + 0.005 stays below UL.
+    "UL": ([1.0, 1.0, 1.01, 10.0, 19.0], [0.0, 0.0, 1.0, 0.0, 0.0], 1.01 + 7 * 0.01),
+    # Steep rise onto a flat top (Phi_j = Phi_{j+1} = 4): the median bound
+    # MD = (Phi_j + Phi_{j+1})/2 - minmod(d_j, d_{j+1})/2 binds.
+    # d_{j-1} = 7, d_j = -1, d_{j+1} = -2: MD = 4 + 1/2.
+    "MD_dj": ([0.0, 0.0, 4.0, 4.0, 4.0], [0.0, 14.0, 2.0, 0.0, 6.0], 4.5),
+    # d_{j-1} = 7, d_j = -2, d_{j+1} = -1: MD = 4 + 1/2 again, now set by d_{j+1}.
+    "MD_djp1": ([0.0, 0.0, 4.0, 4.0, 4.0], [0.0, 12.0, 2.0, 0.0, 4.0], 4.5),
+    # Fall of 1 into a steep drop: the large-curvature bound
+    # LC = Phi_j + (Phi_j - Phi_{j-1})/2 + 4/3 minmod(d_j, d_{j-1}) binds.
+    # d_{j-1} = -6, d_j = -7, d_{j+1} = 13: LC = 1 - 1/2 - 8.
+    "LC_djm1": ([-4.0, 2.0, 1.0, -10.0, -10.0], [-2.0, 0.0, -18.0, -26.0, 0.0], -7.5),
+    # d_{j-1} = -7, d_j = -6, d_{j+1} = 13: LC = -7.5 again, set by d_j.
+    "LC_dj": ([-4.0, 2.0, 1.0, -10.0, -10.0], [-4.0, 0.0, -18.0, -28.0, 0.0], -7.5),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MP_BOUND_CASES))
+@pytest.mark.parametrize("sign", [1.0, -1.0], ids=["upper", "lower"])
+def test_mp_bounds_closed_forms(oracle_mod, name, sign):
+    """The MD, UL and LC bounds of Eq. mp-procedure, one at a time. The
+    procedure is odd (minmod is odd; min and max swap under negation), so the
+    negated data test the other side (Phi^min instead of Phi^max) with the
+    negated expected value. Also checks that the MP test fails (the limiter
+    runs) and that the right value of the mirrored stencil is the same."""
+    phi, dphi, expect = MP_BOUND_CASES[name]
+    phi, dphi, expect = sign * np.array(phi), sign * np.array(dphi), sign * expect
+    grb = oracle_mod.grb_left(phi, dphi)
+    pj, pjm1, pjp1 = phi[2], phi[1], phi[3]
+    a, b = pjp1 - pj, 7.0 * (pj - pjm1)
+    pmp = pj + (0.0 if a * b <= 0 else (min(a, b) if a > 0 else max(a, b)))
+    assert (grb - pj) * (grb - pmp) > 1e-40          # the limiter runs
+    got = oracle_mod.meg7_left(phi, dphi)
+    assert abs(got - expect) <= 1e-14 * (1 + abs(expect)), (got, expect, grb)
+    assert oracle_mod.meg7_right(phi[::-1], -dphi[::-1]) == got
+
+
+@pytest.mark.parametrize("offset", np.linspace(-0.45, 0.45, 19))
+def test_mp_smooth_extremum_keeps_grb(oracle_mod, offset):
+    """Sec. 2.3 adopts the MP bounds of Suresh and Huynh so that smooth
+    extrema are not clipped. A cosine sampled at 24 cells per wavelength
+    with its maximum near the face j+1/2: where the maximum lies between
+    cells j and j+1, the GRB value lies above both of them, so Eq.
+    mp5Condition fails and the limiter runs, yet
+    the curvature-aware bounds MD and LC admit the GRB value and MEG7
+    returns it unchanged. A monotonicity bound [min, max](Phi_j, Phi_{j+1})
+    would have clipped it."""
+    h = 2 * np.pi / 24
+    x = (np.arange(-5, 6) - 0.5 - offset) * h   # cells j-5..j+5; peak at j+1/2+offset
+    f = np.cos(x)
+    d = np.array([oracle_mod.grad6(f[i - 3:i + 4]) for i in range(3, 8)])
+    ph = f[3:8]
+    grb = oracle_mod.grb_left(ph, d)
+    pj = ph[2]
+    a, b = ph[3] - pj, 7.0 * (pj - ph[1])
+    pmp = pj + (0.0 if a * b <= 0 else (min(a, b) if a > 0 else max(a, b)))
+    assert oracle_mod.meg7_left(ph, d) == grb
+    if abs(offset) < 0.3:   # the maximum lies between cells j and j+1
+        assert (grb - pj) * (grb - pmp) > 1e-40      # the limiter runs
+        assert grb > max(ph[2], ph[3])               # a plain monotone bound would clip
+
+
+# ----------------------- characteristic projection (reading R2, Sec. 2.3) ----
+def _prim_jacobian(w, g=1.4):
+    """A = (dQ/dU)^-1 dF/dU of the Euler x-flux F(Q(U)) in primitive variables
+    U = (rho, u, v, p), both factors by complex-step differentiation."""
+    def Q_of(U):
+        r, u, v, p = U
+        return np.array([r, r * u, r * v, p / (g - 1) + 0.5 * r * (u * u + v * v)])
+
+    def F_of(U):
+        r, u, v, p = U
+        E = p / (g - 1) + 0.5 * r * (u * u + v * v)
+        return np.array([r * u, r * u * u + p, r * u * v, u * (E + p)])
+    dQ = np.zeros((4, 4))
+    dF = np.zeros((4, 4))
+    for k in range(4):
+        U = np.array(w, complex)
+        U[k] += 1e-30j
+        dQ[:, k] = np.imag(Q_of(U)) / 1e-30
+        dF[:, k] = np.imag(F_of(U)) / 1e-30
+    return np.linalg.solve(dQ, dF)
+
+
+def test_prim_eigenvectors_diagonalise_the_primitive_jacobian(oracle_mod):
+    """The matrices the MEG7-prim face projection uses (reading R2): L R = I
+    and L A R = diag(u - c, u, u, u + c), in that field order, with A the
+    primitive-variable Jacobian of the Euler x-flux. A sign slip in l1/l4 or
+    r1/r4 swapped consistently with L keeps L R = I but breaks this."""
+    rng = _rng(11)
+    for _ in range(20):
+        w = np.array([rng.uniform(0.2, 3), rng.normal(), rng.normal(), rng.uniform(0.1, 3)])
+        L, R = oracle_mod.prim_eigenvectors(1.4, w)
+        assert np.abs(L @ R - np.eye(4)).max() < 1e-13
+        A = _prim_jacobian(w)
+        c = np.sqrt(1.4 * w[3] / w[0])
+        D = L @ A @ R
+        lam = np.array([w[1] - c, w[1], w[1], w[1] + c])
+        assert np.abs(D - np.diag(lam)).max() < 1e-12 * (1 + np.abs(lam).max())
