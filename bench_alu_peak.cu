@@ -6,7 +6,8 @@
 // `iters` iterations (a, b runtime values, so nothing folds); the grid holds
 // eight 256-thread blocks per SM. The sum of the chains is stored only if it
 // is negative, which it never is, so the work cannot be removed. Built as its
-// own library (libgbr_probe.so): it is measurement, not part of the solver.
+// own library (libgbr_probe.so) from beside the benchmark: it is
+// measurement, not part of the solver.
 #include <cuda_runtime.h>
 
 namespace {

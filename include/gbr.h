@@ -344,6 +344,17 @@ int gbr_batch_set_end_times(gbr_batch *b, const double *t_end);
  * tile shape) and replayed. Asynchronous. */
 int gbr_batch_step_cfl(gbr_batch *b, double cfl, int nsteps);
 
+/* One TVD-RK3 step (Sec. 2.5, Eq. rk) of every grid at the caller's step
+ * size: grid k advances by dt_per_case[k] >= 0 (host array of n finite
+ * values, read during the call only); a grid at dt 0 is skipped (state, time
+ * and wavespeed unchanged). For callers that run their own time control, e.g.
+ * a common dt = CFL / max_k lambda_k, or fixed steps compared with a
+ * reference. End times (gbr_batch_set_end_times) are not applied here. The
+ * launches are issued directly (no graph) on the batch's stream;
+ * asynchronous. GBR_ERR_ARG for a NULL pointer or a negative or non-finite
+ * dt (nothing runs). */
+int gbr_batch_step(gbr_batch *b, const double *dt_per_case);
+
 /* Per-grid time t[k] and last step size dt[k] (host arrays of n entries, either
  * may be NULL). Synchronises; returns GBR_ERR_NONPHYSICAL if any grid's stage
  * produced rho <= 0, p <= 0 or a non-finite value. */
@@ -385,13 +396,23 @@ int gbr_batch_sync(gbr_batch *b);
  * doubles, held by every GPU that loads the library until the process exits.
  * A grid needs 32 + 12 * roundup16(roundup16(nx + 12) * (ny + 12)) doubles of
  * it, which admits up to about 270 x 270 cells (256 x 256 fits); a larger
- * grid returns GBR_ERR_ARG and nothing runs. The first call on a device looks
- * up the array's device address for that device (cudaGetSymbolAddress, with
- * that device current); make that first call before any stream capture. All
- * calls share the one array and each clears what must start at zero; calls
- * that overlap on the GPU (several host threads or streams at once) race on
- * it, so serialise them. Allocates nothing: no cudaMalloc, cudaFree or
- * allocating library routine is called. */
+ * grid returns GBR_ERR_ARG and nothing runs. Devices with ordinal 64 or more
+ * return GBR_ERR_UNSUPPORTED.
+ *
+ * First call on a device. It looks up the array's device address for that
+ * device (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture. With CUDA's default lazy module loading,
+ * the code and the array are also loaded onto the device at that first call
+ * (or at the first call of any other entry point there): the driver then
+ * reserves device memory for the 8 MiB array and the kernels' code, which
+ * takes time and can fail near the memory limit (GBR_ERR_CUDA). Callers that
+ * must not see that should make one warm-up call at start-up, or run with
+ * CUDA_MODULE_LOADING=EAGER. After that, calls allocate nothing: no
+ * cudaMalloc, cudaFree or allocating library routine is called.
+ *
+ * All calls share the one array and each clears what must start at zero;
+ * calls that overlap on the GPU (several host threads or streams at once)
+ * race on it, so serialise them. */
 int gbr_step_static(const double *Q_in, double *Q_out, int nx, int ny, double gamma, double mu, double Pr,
                     const gbr_bc *bc, double dt, void *stream);
 

@@ -12,8 +12,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgbr.so")
-# the benchmark's FMA-throughput probe, a library of its own
-PROBE_SRC = os.path.join(HERE, "probe", "alu_peak.cu")
+# the benchmark's FMA-throughput probe (a source beside bench.py, not part of
+# the solver), built here as a library of its own
+PROBE_SRC = os.path.join(os.path.dirname(HERE), "bench_alu_peak.cu")
 PROBE_LIB = os.path.join(OUT, "libgbr_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -59,9 +59,11 @@ cudaError_t launch_ghosts(const GhostParams& p, cudaStream_t s)
 
 // Ghost cells of buffer `buf` of every grid of a batch (one thread per ghost
 // cell of the whole batch); with mode 2 the first ncases threads also form
-// each grid's dt, advance its time and clear its wavespeed slot.
+// each grid's dt, advance its time and clear its wavespeed slot; with mode 3
+// they take each grid's dt from dts[] instead (a grid at dt = 0 keeps its
+// time and its wavespeed, and its stages are skipped).
 __global__ void batch_ghost_kernel(const BatchCase* __restrict__ cases, int ncases, long long total, int buf,
-                                   int mode, double cfl)
+                                   int mode, double cfl, const double* __restrict__ dts)
 {
     const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (mode == 2 && id < ncases) {
@@ -72,6 +74,15 @@ __global__ void batch_ghost_kernel(const BatchCase* __restrict__ cases, int ncas
         d->dt = dt;
         d->t += dt;
         d->lam[0] = 0ull;
+    }
+    if (mode == 3 && id < ncases) {
+        DevScalars* d = cases[id].ds;
+        const double dt = dts[id];
+        d->dt = dt;
+        if (dt > 0.0) {
+            d->t += dt;
+            d->lam[0] = 0ull;
+        }
     }
     if (id >= total) return;
     int lo = 0, hi = ncases - 1;
@@ -85,11 +96,12 @@ __global__ void batch_ghost_kernel(const BatchCase* __restrict__ cases, int ncas
 }
 
 cudaError_t launch_batch_ghosts(const BatchCase* cases, int ncases, long long total_ghosts, int buf, int mode,
-                                double cfl, cudaStream_t s)
+                                double cfl, cudaStream_t s, const double* dts)
 {
     long long n = total_ghosts > ncases ? total_ghosts : ncases;
     const int nt = 256;
-    batch_ghost_kernel<<<(unsigned)((n + nt - 1) / nt), nt, 0, s>>>(cases, ncases, total_ghosts, buf, mode, cfl);
+    batch_ghost_kernel<<<(unsigned)((n + nt - 1) / nt), nt, 0, s>>>(cases, ncases, total_ghosts, buf, mode, cfl,
+                                                                     dts);
     return cudaGetLastError();
 }
 

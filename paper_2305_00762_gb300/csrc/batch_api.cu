@@ -38,6 +38,7 @@ struct gbr_batch {
     int sensor;               // 1: use them (FP32 only)
     unsigned char* dec_pool;  // the cases' learned-sensor decisions (padded layouts)
     int total_dtiles;         // sensor-pass tiles of all cases
+    double* d_dt;             // caller-supplied per-case dt of gbr_batch_step (n doubles)
 };
 
 namespace {
@@ -113,12 +114,13 @@ int stage(gbr_batch* b, int k, cudaStream_t s)
 }
 
 // One RK3 step of every case (Eq. rk): ghost fill + persistent stage kernel,
-// three times; the first ghost fill forms each case's dt on the device.
-int enqueue_step(gbr_batch* b, double cfl, cudaStream_t s)
+// three times; the first ghost fill forms each case's dt on the device
+// (mode 2: CFL) or takes it from b->d_dt (mode 3: the caller's dt).
+int enqueue_step(gbr_batch* b, double cfl, cudaStream_t s, int mode = 2)
 {
     int rc;
     for (int k = 0; k < 3; ++k) {
-        TRY(launch_batch_ghosts(b->d_cases, b->n, b->total_ghosts, k, k == 0 ? 2 : 0, cfl, s));
+        TRY(launch_batch_ghosts(b->d_cases, b->n, b->total_ghosts, k, k == 0 ? mode : 0, cfl, s, b->d_dt));
         if ((rc = stage(b, k, s)) != GBR_OK) return rc;
     }
     return GBR_OK;
@@ -239,6 +241,7 @@ int gbr_batch_create(int n, const int* nx, const int* ny, const double* dx, cons
     if (rc == GBR_OK) rc = st(cudaMalloc(&b->d_scal, sizeof(DevScalars) * n));
     if (rc == GBR_OK) rc = st(cudaMemset(b->d_scal, 0, sizeof(DevScalars) * n));
     if (rc == GBR_OK) rc = st(cudaMalloc(&b->d_cases, sizeof(BatchCase) * n));
+    if (rc == GBR_OK) rc = st(cudaMalloc(&b->d_dt, sizeof(double) * n));
     if (rc == GBR_OK) rc = st(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
     if (rc != GBR_OK) {
         gbr_batch_destroy(b);
@@ -271,6 +274,7 @@ int gbr_batch_destroy(gbr_batch* b)
     cudaFree(b->pool);
     cudaFree(b->d_scal);
     cudaFree(b->d_cases);
+    cudaFree(b->d_dt);
     cudaFree(b->d_sensor);
     cudaFree(b->dec_pool);
     cudaGetLastError();
@@ -366,6 +370,21 @@ int gbr_batch_step_cfl(gbr_batch* b, double cfl, int nsteps)
     return rc;
 }
 
+int gbr_batch_step(gbr_batch* b, const double* dt_per_case)
+{
+    if (!b || !dt_per_case) return GBR_ERR_ARG;
+    for (int k = 0; k < b->n; ++k)
+        if (!(dt_per_case[k] >= 0.0) || !(dt_per_case[k] < 1e300)) return GBR_ERR_ARG;
+    nvtxRangePushA("gbr batch step");
+    DeviceGuard dg(b->device);
+    int rc = upload(b);
+    // the host array is staged by the copy before the call returns
+    if (rc == GBR_OK)
+        rc = st(cudaMemcpyAsync(b->d_dt, dt_per_case, sizeof(double) * b->n, cudaMemcpyHostToDevice, b->stream));
+    if (rc == GBR_OK) rc = enqueue_step(b, 0.0, b->stream, 3);
+    nvtxRangePop();
+    return rc;
+}
 
 int gbr_batch_get_times(gbr_batch* b, double* t, double* dt)
 {

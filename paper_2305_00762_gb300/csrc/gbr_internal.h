@@ -134,9 +134,10 @@ cudaError_t launch_ghosts(const GhostParams& p, cudaStream_t s);
 cudaError_t launch_set_time(DevScalars* d, int cur, double t, cudaStream_t s);
 // Ghost cells of buffer `buf` (0, 1, 2) of every case; with mode 2 the first
 // ncases threads also form each case's dt = min(cfl / lam, t_end - t), advance
-// its time and clear its wavespeed slot.
+// its time and clear its wavespeed slot; with mode 3 each case's dt is
+// dts[k] (device array; a case at dt = 0 is left as it is).
 cudaError_t launch_batch_ghosts(const BatchCase* cases, int ncases, long long total_ghosts, int buf, int mode,
-                                double cfl, cudaStream_t s);
+                                double cfl, cudaStream_t s, const double* dts = nullptr);
 // Candidate tile shapes of the persistent batch kernel (returns the count).
 int batch_tile_shapes_f64(const TileShape** shapes);
 int batch_tile_shapes_f32(const TileShape** shapes);

@@ -39,14 +39,16 @@ double* g_scratch_addr[kMaxDevices];  // device address of the array, per device
 
 // Once per device, with that device current: the device address of the
 // array. In host code the name g_static_scratch is only a host-side stand-in
-// and must never be passed to a kernel.
+// and must never be passed to a kernel. Devices with an ordinal of
+// kMaxDevices or more are not served (GBR_ERR_UNSUPPORTED).
 int scratch_address(double** out)
 {
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
         cudaGetLastError();
         return GBR_ERR_CUDA;
     }
+    if (dev >= kMaxDevices) return GBR_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_addr[dev]) {
         double* p = nullptr;

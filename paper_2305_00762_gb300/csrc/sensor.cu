@@ -493,7 +493,12 @@ __global__ void __launch_bounds__(128 * G, 8 / G)
     if (tma) {
         ok = __syncthreads_and(mbar_wait_bounded(&S.tma_bar)) != 0;
         if (!ok) {
-            mbar_wait_bounded(&S.tma_bar);  // one more bounded wait for the copy before the CTA leaves
+            // One more bounded wait for the copy before the CTA leaves; leaving
+            // is safe only once its bytes have landed (a copy still in flight
+            // would write into shared memory another CTA may own). The timeout
+            // bit the CTA sets keeps every later result of the context
+            // untrusted until gbr_set_state.
+            mbar_wait_bounded(&S.tma_bar);
         } else {
             // cells beyond the padded extent read as zero and only feed
             // outputs that are never stored

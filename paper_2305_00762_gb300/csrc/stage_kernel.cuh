@@ -865,6 +865,12 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
             const bool ok = mbar_wait_bounded(bar);
             if (__syncthreads_or(!ok)) {
                 // Give the copy one more bounded wait before the CTA leaves.
+                // Leaving is safe only once the copy's bytes have landed: a
+                // copy still in flight after this second wait would write
+                // into shared memory the SM may have handed to another CTA.
+                // The timeout bit set here makes the next synchronising call
+                // fail and stays set until gbr_set_state, so no result
+                // computed after such an event is reported as valid.
                 mbar_wait_bounded(bar);
                 if (tid == 0) atomicOr(P.err, kErrTimeout);
                 return;

@@ -87,6 +87,7 @@ def load():
         "gbr_batch_get_state": (ip, [vp, ip, vp, ip]),
         "gbr_batch_set_end_times": (ip, [vp, ctypes.POINTER(dp)]),
         "gbr_batch_step_cfl": (ip, [vp, dp, ip]),
+        "gbr_batch_step": (ip, [vp, ctypes.POINTER(ctypes.c_double)]),
         "gbr_batch_get_times": (ip, [vp, ctypes.POINTER(dp), ctypes.POINTER(dp)]),
         "gbr_batch_autotune": (ip, [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip)]),
         "gbr_batch_sync": (ip, [vp]),
@@ -468,6 +469,11 @@ class Batch:
 
     def step_cfl(self, cfl, nsteps=1):
         _check(load().gbr_batch_step_cfl(self.b, float(cfl), int(nsteps)), "gbr_batch_step_cfl")
+
+    def step(self, dts):
+        """One RK3 step of every grid at its own caller-supplied dt (0 skips)."""
+        a = (ctypes.c_double * self.n)(*[float(x) for x in dts])
+        _check(load().gbr_batch_step(self.b, a), "gbr_batch_step")
 
     def times(self, allow=()):
         t = (ctypes.c_double * self.n)()

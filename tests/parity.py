@@ -100,5 +100,12 @@ def assert_state_close(a, b, tol=TOL64, what=""):
 
 
 def assert_residual_close(R, Ro, Q, case, tol=TOL64, exclude=None, what=""):
+    """Residual parity against the flux scale (the pass criterion); the error
+    against max|Res_m| itself is printed beside it, so the margin is visible
+    (pytest -s or -rP shows it)."""
     sc = residual_scales(Q, case.dx, case.dy, case.gamma, Ro)
-    return assert_close(R, Ro, tol, exclude, what, sc)
+    errs = assert_close(R, Ro, tol, exclude, what, sc)
+    own = field_errors(R, Ro, exclude)
+    print(f"[residual parity] {what}: max err / flux scale {max(errs):.2e}, "
+          f"/ max|Res_m| {max(own):.2e} (per field {', '.join(f'{e:.1e}' for e in own)})")
+    return errs

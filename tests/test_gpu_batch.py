@@ -70,6 +70,61 @@ def test_batch_fp64_equals_single_grids_and_oracle(env):
     b.close()
 
 
+def test_batch_step_at_caller_dt_matches_oracle(env):
+    """gbr_batch_step: one RK3 step of every grid at a dt the caller supplies
+    (Eq. rk with the time step of Sec. 2.5 chosen outside the library), each
+    case against the oracle's step at the same dt to 1e-12; a grid given dt 0
+    is left bitwise unchanged (state, time and wavespeed); three steps in a
+    row, the dt-0 grid resuming in the last one."""
+    torch, O, gbr = env
+    ens = small_ensemble()
+    b = gbr.Batch(ens)
+    for k, c in enumerate(ens):
+        b.set_state(k, c.Q)
+    Qo = [c.Q.copy() for c in ens]
+    t_ref = np.zeros(len(ens))
+    lam0 = [O.max_wavespeed(cfg_of(O, c), c.Q) for c in ens]
+    for step in range(3):
+        dts = [0.4 / l * (1.0 - 0.1 * k) for k, l in enumerate(lam0)]
+        if step < 2:
+            dts[2] = 0.0                                        # the Riemann grid waits
+        before = b.get_state(2)
+        b.step(dts)
+        t, dt = b.times()
+        for k, c in enumerate(ens):
+            if dts[k] > 0:
+                Qo[k], rc = O.rk3_step(cfg_of(O, c), Qo[k], dts[k])
+                assert rc == 0
+                t_ref[k] += dts[k]
+        assert np.array_equal(dt, np.array(dts))
+        assert np.allclose(t, t_ref, rtol=1e-15, atol=0)
+        if step < 2:
+            assert np.array_equal(b.get_state(2), before)
+    for k, c in enumerate(ens):
+        assert_state_close(b.get_state(k), Qo[k], TOL64 * 3, what=f"batch case {k} at caller dt")
+    # the skipped grid's wavespeed survived its dt-0 steps: a CFL step after
+    # them forms its dt from the state it holds, as the oracle does
+    b.step_cfl(0.5, 1)
+    _, dt = b.times()
+    for k, c in enumerate(ens):
+        lam = O.max_wavespeed(cfg_of(O, c), Qo[k])
+        assert abs(dt[k] - 0.5 / lam) <= 1e-13 * dt[k], k
+    b.close()
+
+
+def test_batch_step_rejects_bad_dt(env):
+    torch, O, gbr = env
+    ens = small_ensemble()[:2]
+    b = gbr.Batch(ens)
+    for k, c in enumerate(ens):
+        b.set_state(k, c.Q)
+    for bad in ([-1e-3, 1e-3], [float("nan"), 1e-3], [float("inf"), 1e-3]):
+        with pytest.raises(gbr.GbrError):
+            b.step(bad)
+    assert np.array_equal(b.get_state(0), ens[0].Q)
+    b.close()
+
+
 def test_graph_replay_and_autotune_are_bitwise_neutral(env):
     torch, O, gbr = env
     ens = small_ensemble()
