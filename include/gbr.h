@@ -72,7 +72,14 @@ typedef enum {
      * reflection of Woodward and Colella needs (Example 8). */
     GBR_BC_CUSTOM = 4,
     /* Only inside gbr_side: ghost cells hold a fixed primitive state. */
-    GBR_BC_FIXED = 5
+    GBR_BC_FIXED = 5,
+    /* South or north side of one slab of a grid split along y into slabs
+     * (single-grid solvers only; not with GBR_BC_CUSTOM sides): its six ghost
+     * rows are interior rows of the neighbouring slab, written by the caller
+     * with gbr_halo_copy before every stage (gbr_step_stage). The library
+     * fills only the west / east ghost cells of those rows, by the west /
+     * east rule, as it does for interior rows. */
+    GBR_BC_HALO = 6
 } gbr_bc_kind;
 
 /* Boundary kinds per side and the uniform cell sizes (the grid is
@@ -221,6 +228,50 @@ int gbr_get_time(gbr_ctx *ctx, double *t);
  * 4 nu/dy^2), c = sqrt(gamma p / rho), nu = mu / rho (Sec. 2.5: dt =
  * CFL / lambda). Synchronises; returns pending device errors. */
 int gbr_max_wavespeed(gbr_ctx *ctx, double *lambda);
+
+/* ----------------------------------------------------------------------
+ * One grid split along y into slabs (one context per slab, e.g. one per GPU).
+ * Eq. deriv's residual reaches six cells in each direction (reading of the
+ * LC bound, see GBR_GHOST), so before each Runge-Kutta stage every slab needs
+ * the six boundary rows of each neighbour at that stage. A step of a slab is
+ * then: for k = 0, 1, 2: copy the six rows next to each GBR_BC_HALO side out
+ * of every neighbour (gbr_halo_copy, dir 0) and into this slab's ghost rows
+ * (dir 1), then gbr_step_stage(k); after stage 2, the wavespeeds of all slabs
+ * are reduced to their maximum (gbr_lambda_word / gbr_lambda_max) so that
+ * the next CFL step takes one dt everywhere (Sec. 2.5). With identical
+ * inputs the slabs reproduce the single-grid step bit for bit.
+ * ---------------------------------------------------------------------- */
+
+/* Stage k (0, 1, 2) of a TVD-RK3 step (Eq. rk): the ghost fill of the
+ * stage's input state and the fused residual + stage-update pass, as gbr_step
+ * runs them. k = 0 starts a step: dt > 0 gives a fixed step; dt = 0 forms
+ * dt = min(cfl / lambda, dt_max) on the device (cfl, dt_max > 0), lambda the
+ * current wavespeed word. k = 1, 2 continue the step (dt, cfl, dt_max
+ * ignored). Stages must come in the order 0, 1, 2 (else GBR_ERR_STATE).
+ * Asynchronous. */
+int gbr_step_stage(gbr_ctx *ctx, int k, double dt, double cfl, double dt_max);
+
+/* Halo rows of the state the next gbr_step_stage reads. side: 2 south, 3
+ * north. dir 0 (pack): copy the six interior rows next to that side (rows
+ * 0..5 for south, ny-6..ny-1 for north, interior columns only) into buf;
+ * dir 1 (unpack): copy buf into the six ghost rows beyond that side (rows
+ * -6..-1 for south, ny..ny+5 for north; the side must be GBR_BC_HALO). buf:
+ * [4][6][nx] float64, x fastest, rows in increasing y, on the device
+ * (on_device = 1) or host. Device copies are asynchronous on the context's
+ * stream; host copies synchronise it. */
+int gbr_halo_copy(gbr_ctx *ctx, int side, int dir, double *buf, int on_device);
+
+/* Device address of the context's current wavespeed word (the bits of a
+ * double >= 0, so the largest word is the largest value): a max all-reduce
+ * of these words across slabs after each step (e.g. NCCL, unsigned 64-bit
+ * max) makes every slab's next CFL step use the global wavespeed. */
+int gbr_lambda_word(gbr_ctx *ctx, unsigned long long **word);
+
+/* The same reduction for 1 <= n <= 256 contexts on one device, between
+ * steps: after it, each context's wavespeed word holds the maximum over the
+ * n. Issued on ctx[0]'s stream (order the other contexts' streams before
+ * it); GBR_ERR_ARG for contexts on different devices or in mid-step. */
+int gbr_lambda_max(gbr_ctx *const *ctx, int n);
 
 /* Set an option (gbr_option). Returns GBR_ERR_ARG for an unknown key or a
  * bad value, GBR_ERR_UNSUPPORTED for a mode that cannot run. */

@@ -35,6 +35,9 @@ struct gbr_ctx {
     int sensor;
     int have_state;
     int lam_cur;
+    int stage_next;  // next stage of a step run stage by stage (gbr_step_stage): 0 = no step in progress
+    int step_mode;   // that step's dt: 1 = host value step_dt, 2 = CFL on the device
+    double step_dt;
     // launch timing (GBR_OPT_TIMING)
     int timing;
     std::vector<cudaEvent_t> ev;   // pairs: start, stop
@@ -88,8 +91,14 @@ int cuda_status(cudaError_t e)
 bool bc_ok(const gbr_bc* bc)
 {
     const int k[4] = {bc->west, bc->east, bc->south, bc->north};
-    for (int i = 0; i < 4; ++i)
-        if (k[i] < GBR_BC_PERIODIC || k[i] > GBR_BC_CUSTOM) return false;
+    bool halo = false, custom = false;
+    for (int i = 0; i < 4; ++i) {
+        if (k[i] < GBR_BC_PERIODIC || k[i] > GBR_BC_HALO || k[i] == GBR_BC_FIXED) return false;
+        if (k[i] == GBR_BC_HALO && i < 2) return false;  // slabs split along y only
+        halo |= k[i] == GBR_BC_HALO;
+        custom |= k[i] == GBR_BC_CUSTOM;
+    }
+    if (halo && custom) return false;
     if ((bc->west == GBR_BC_PERIODIC) != (bc->east == GBR_BC_PERIODIC)) return false;
     if ((bc->south == GBR_BC_PERIODIC) != (bc->north == GBR_BC_PERIODIC)) return false;
     return bc->dx > 0.0 && bc->dy > 0.0;
@@ -203,44 +212,59 @@ int stage(gbr_ctx* c, const StageParams& p)
     return cuda_status(e);
 }
 
-// Eq. rk: Q1 = Qn + dt R(Qn); Q2 = 3/4 Qn + 1/4 Q1 + 1/4 dt R(Q1);
-// Qn+1 = 1/3 Qn + 2/3 Q2 + 2/3 dt R(Q2). dt is a host value (dt_dev null) or
-// the device word formed by the first ghost fill.
+// Input state of RK stage k (0, 1, 2).
+double* stage_input(gbr_ctx* c, int k) { return k == 0 ? c->Qn : (k == 1 ? c->Qa : c->Qb); }
+
+// Stage k of Eq. rk: Q1 = Qn + dt R(Qn); Q2 = 3/4 Qn + 1/4 Q1 + 1/4 dt R(Q1);
+// Qn+1 = 1/3 Qn + 2/3 Q2 + 2/3 dt R(Q2): the ghost fill of the stage's input
+// (the first one forms the step's scalars: mode 1 with the host dt, mode 2
+// with dt from the CFL condition on the device; the stage times of the
+// boundaries are t, t + dt, t + dt/2) and the fused stage pass. dt is a host
+// value (mode 1) or the device word formed by the first ghost fill (mode 2).
+int rk3_stage(gbr_ctx* c, int k, int mode, double dt, double cfl, double dt_max)
+{
+    static const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    static const double c_stage[3] = {0.0, 1.0, 0.5};
+    int rc;
+    double* in = stage_input(c, k);
+    if ((rc = ghosts(c, in, k == 0 ? mode : 0, dt, cfl, dt_max, c_stage[k])) != GBR_OK) return rc;
+    StageParams p = stage_params(c, in);
+    p.qout = k == 2 ? c->Qn : stage_input(c, k + 1);  // stage 3: each cell reads its own Q^n before writing it
+    p.dt = dt;
+    p.dt_ptr = (mode == 2) ? &c->ds->dt : nullptr;
+    p.ca = ca[k];
+    p.cb = cb[k];
+    p.cc = cb[k];
+    if (k == 2) p.lam_out = &c->ds->lam[1 - c->lam_cur];
+    if ((rc = stage(c, p)) != GBR_OK) return rc;
+    if (k == 2) c->lam_cur = 1 - c->lam_cur;
+    return GBR_OK;
+}
+
 int rk3_step(gbr_ctx* c, int mode, double dt, double cfl, double dt_max)
 {
     Range r("gbr step");
     int rc;
-    const double* dt_dev = (mode == 2) ? &c->ds->dt : nullptr;
-    if ((rc = ghosts(c, c->Qn, mode, dt, cfl, dt_max)) != GBR_OK) return rc;
-    StageParams p = stage_params(c, c->Qn);
-    p.qout = c->Qa;
-    p.dt = dt;
-    p.dt_ptr = dt_dev;
-    p.ca = 0.0;
-    p.cb = 1.0;
-    p.cc = 1.0;
-    if ((rc = stage(c, p)) != GBR_OK) return rc;
-    if ((rc = ghosts(c, c->Qa, 0, 0, 0, 0, 1.0)) != GBR_OK) return rc;  // stage 2 at t + dt
-    p = stage_params(c, c->Qa);
-    p.qout = c->Qb;
-    p.dt = dt;
-    p.dt_ptr = dt_dev;
-    p.ca = 0.75;
-    p.cb = 0.25;
-    p.cc = 0.25;
-    if ((rc = stage(c, p)) != GBR_OK) return rc;
-    if ((rc = ghosts(c, c->Qb, 0, 0, 0, 0, 0.5)) != GBR_OK) return rc;  // stage 3 at t + dt/2
-    p = stage_params(c, c->Qb);
-    p.qout = c->Qn;  // each cell reads its own Q^n before writing it
-    p.dt = dt;
-    p.dt_ptr = dt_dev;
-    p.ca = 1.0 / 3.0;
-    p.cb = 2.0 / 3.0;
-    p.cc = 2.0 / 3.0;
-    p.lam_out = &c->ds->lam[1 - c->lam_cur];
-    if ((rc = stage(c, p)) != GBR_OK) return rc;
-    c->lam_cur = 1 - c->lam_cur;
+    for (int k = 0; k < 3; ++k)
+        if ((rc = rk3_stage(c, k, mode, dt, cfl, dt_max)) != GBR_OK) return rc;
     return GBR_OK;
+}
+
+// The wavespeed words of up to kLambdaMax contexts on one device, passed by
+// value to the reduction kernel.
+constexpr int kLambdaMax = 256;
+struct LambdaWords {
+    unsigned long long* w[kLambdaMax];
+    int n;
+};
+
+// One thread: the largest word (the largest non-negative double) written back
+// to every context.
+__global__ void lambda_max_kernel(const LambdaWords W)
+{
+    unsigned long long m = 0ull;
+    for (int i = 0; i < W.n; ++i) m = *W.w[i] > m ? *W.w[i] : m;
+    for (int i = 0; i < W.n; ++i) *W.w[i] = m;
 }
 
 }  // namespace
@@ -333,6 +357,7 @@ int gbr_set_state(gbr_ctx* c, const double* Q, int on_device)
     if (rc != GBR_OK) return rc;
     GBR_TRY(cudaMemsetAsync(c->ds, 0, sizeof(DevScalars), c->stream));
     c->lam_cur = 0;
+    c->stage_next = 0;
     {
         Timed tm(c, GBR_KERNEL_WAVESPEED);
         GBR_TRY(launch_wavespeed(c->g, c->ph, c->Qn, &c->ds->lam[0], c->precision, c->stream));
@@ -381,7 +406,7 @@ int gbr_residual(gbr_ctx* c, double* res, int on_device)
 int gbr_step(gbr_ctx* c, double dt)
 {
     if (!c || !(dt > 0.0)) return GBR_ERR_ARG;
-    if (!c->have_state) return GBR_ERR_STATE;
+    if (!c->have_state || c->stage_next != 0) return GBR_ERR_STATE;
     DeviceGuard dg(c->device);
     return rk3_step(c, 1, dt, 0.0, 0.0);
 }
@@ -389,9 +414,70 @@ int gbr_step(gbr_ctx* c, double dt)
 int gbr_step_cfl(gbr_ctx* c, double cfl, double dt_max)
 {
     if (!c || !(cfl > 0.0) || !(dt_max > 0.0)) return GBR_ERR_ARG;
-    if (!c->have_state) return GBR_ERR_STATE;
+    if (!c->have_state || c->stage_next != 0) return GBR_ERR_STATE;
     DeviceGuard dg(c->device);
     return rk3_step(c, 2, 0.0, cfl, dt_max);
+}
+
+int gbr_step_stage(gbr_ctx* c, int k, double dt, double cfl, double dt_max)
+{
+    if (!c || k < 0 || k > 2) return GBR_ERR_ARG;
+    if (k == 0 && !(dt > 0.0) && !(dt == 0.0 && cfl > 0.0 && dt_max > 0.0)) return GBR_ERR_ARG;
+    if (!c->have_state || c->stage_next != k) return GBR_ERR_STATE;
+    DeviceGuard dg(c->device);
+    Range r("gbr step stage");
+    if (k == 0) {
+        c->step_mode = dt > 0.0 ? 1 : 2;
+        c->step_dt = dt;
+    }
+    const int rc = rk3_stage(c, k, c->step_mode, c->step_dt, cfl, dt_max);
+    if (rc != GBR_OK) return rc;
+    c->stage_next = (k + 1) % 3;
+    return GBR_OK;
+}
+
+int gbr_halo_copy(gbr_ctx* c, int side, int dir, double* buf, int on_device)
+{
+    if (!c || !buf || (side != 2 && side != 3) || (dir != 0 && dir != 1)) return GBR_ERR_ARG;
+    if (dir == 1 && c->bc[side] != GBR_BC_HALO) return GBR_ERR_ARG;
+    if (!c->have_state) return GBR_ERR_STATE;
+    DeviceGuard dg(c->device);
+    const int nx = c->g.nx, ny = c->g.ny;
+    // padded row of the first of the six rows
+    const int row = dir == 0 ? (side == 2 ? kGhost : ny) : (side == 2 ? 0 : ny + kGhost);
+    double* q = stage_input(c, c->stage_next) + (long long)row * c->g.pitch + kGhost;
+    const size_t spitch = sizeof(double) * c->g.pitch, bpitch = sizeof(double) * nx;
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : (dir == 0 ? cudaMemcpyDeviceToHost
+                                                                           : cudaMemcpyHostToDevice);
+    for (int m = 0; m < 4; ++m) {
+        double* b = buf + (size_t)m * kGhost * nx;
+        double* s = q + m * c->g.plane;
+        if (dir == 0) GBR_TRY(cudaMemcpy2DAsync(b, bpitch, s, spitch, bpitch, kGhost, kind, c->stream));
+        else GBR_TRY(cudaMemcpy2DAsync(s, spitch, b, bpitch, bpitch, kGhost, kind, c->stream));
+    }
+    if (!on_device) GBR_TRY(cudaStreamSynchronize(c->stream));
+    return GBR_OK;
+}
+
+int gbr_lambda_word(gbr_ctx* c, unsigned long long** word)
+{
+    if (!c || !word) return GBR_ERR_ARG;
+    *word = &c->ds->lam[c->lam_cur];
+    return GBR_OK;
+}
+
+int gbr_lambda_max(gbr_ctx* const* ctx, int n)
+{
+    if (!ctx || n < 1 || n > kLambdaMax) return GBR_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!ctx[i] || ctx[i]->device != ctx[0]->device || ctx[i]->stage_next != 0) return GBR_ERR_ARG;
+    DeviceGuard dg(ctx[0]->device);
+    LambdaWords W;
+    memset(&W, 0, sizeof(W));
+    W.n = n;
+    for (int i = 0; i < n; ++i) W.w[i] = &ctx[i]->ds->lam[ctx[i]->lam_cur];
+    lambda_max_kernel<<<1, 1, 0, ctx[0]->stream>>>(W);
+    return cuda_status(cudaGetLastError());
 }
 
 int gbr_get_time(gbr_ctx* c, double* t)

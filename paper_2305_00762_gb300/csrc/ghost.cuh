@@ -33,7 +33,7 @@ __host__ __device__ __forceinline__ long long ghost_count(const Grid& g)
     return 2LL * kGhost * (g.nx + 2 * kGhost) + 2LL * kGhost * g.ny;
 }
 
-constexpr int kBcCustom = 4, kBcFixed = 5;
+constexpr int kBcCustom = 4, kBcFixed = 5, kBcHalo = 6;
 
 // Kind of a custom side beside the cell with tangential index k (centre at
 // (k + 1/2) h along the side) at time t; for kBcFixed also its state.
@@ -46,7 +46,11 @@ __device__ __forceinline__ int side_kind(const SideBC& S, int k, double h, doubl
 
 // Fill ghost cell number id (0 <= id < ghost_count) of the padded state q. A
 // corner ghost takes the y image of the x image of an interior cell, so the
-// velocity sign flips of both axes compose. With custom sides (sides != null,
+// velocity sign flips of both axes compose. The ghost rows of a halo side
+// (south / north of one slab of a grid split along y) hold the neighbouring
+// slab's interior rows, written before the fill: their interior columns are
+// left alone and their west / east ghosts follow the x rule of their own row,
+// as for an interior row. With custom sides (sides != null,
 // boundary time t), a south / north ghost whose side is fixed there takes the
 // fixed state; otherwise the source row is found first and a west / east
 // side is resolved at that row (a fixed state is then mirrored across the
@@ -72,6 +76,8 @@ __device__ __forceinline__ void fill_ghost(const Grid& g, double* q, const int b
         gx = c < kGhost ? c : nx + c;
     }
     const int j = gx - kGhost, i = gy - kGhost;
+    const bool halo_row = (i < 0 && bc[2] == kBcHalo) || (i >= ny && bc[3] == kBcHalo);
+    if (halo_row && j >= 0 && j < nx) return;
     const long long d = (long long)gy * g.pitch + gx;
     const long long pl = g.plane;
     int ky[2] = {bc[2], bc[3]}, kx[2] = {bc[0], bc[1]};
@@ -84,8 +90,8 @@ __device__ __forceinline__ void fill_ghost(const Grid& g, double* q, const int b
         }
         ky[i < 0 ? 0 : 1] = k;
     }
-    bool fnx, ftx, fny, fty;
-    const int is = ghost_src(i, ny, ky[0], ky[1], fny, fty);
+    bool fnx, ftx, fny = false, fty = false;
+    const int is = halo_row ? i : ghost_src(i, ny, ky[0], ky[1], fny, fty);
     if (sides && (j < 0 || j >= nx) && bc[j < 0 ? 0 : 1] == kBcCustom) {
         const double* st;
         const int k = side_kind(sides[j < 0 ? 0 : 1], is, dy, t, st);

@@ -19,7 +19,7 @@ from . import build as _build
 GBR_OK, GBR_ERR_ARG, GBR_ERR_CUDA, GBR_ERR_NONPHYSICAL = 0, -1, -2, -3
 GBR_ERR_TIMEOUT, GBR_ERR_STATE, GBR_ERR_NOMEM, GBR_ERR_UNSUPPORTED = -4, -5, -6, -7
 GBR_BC_PERIODIC, GBR_BC_TRANSMISSIVE, GBR_BC_NOSLIP_WALL, GBR_BC_SYMMETRY = 0, 1, 2, 3
-GBR_BC_CUSTOM, GBR_BC_FIXED = 4, 5
+GBR_BC_CUSTOM, GBR_BC_FIXED, GBR_BC_HALO = 4, 5, 6
 GBR_OPT_PRECISION, GBR_OPT_RECORD_FLAGS, GBR_OPT_SENSOR, GBR_OPT_TIMING, GBR_OPT_ORDER = 0, 1, 2, 3, 4
 GBR_OPT_VARIABLES, GBR_OPT_STALL_TEST, GBR_OPT_RIEMANN = 5, 6, 7
 GBR_KERNEL_STAGE, GBR_KERNEL_GHOST, GBR_KERNEL_WAVESPEED, GBR_KERNEL_CLASSES = 0, 1, 2, 3
@@ -78,6 +78,10 @@ def load():
         "gbr_get_timing": (ip, [vp, ctypes.POINTER(dp), ctypes.POINTER(ip), ctypes.POINTER(ip)]),
         "gbr_sync": (ip, [vp]),
         "gbr_step_static": (ip, [vp, vp, ip, ip, dp, dp, dp, ctypes.POINTER(gbr_bc), dp, vp]),
+        "gbr_step_stage": (ip, [vp, ip, dp, dp, dp]),
+        "gbr_halo_copy": (ip, [vp, ip, ip, vp, ip]),
+        "gbr_lambda_word": (ip, [vp, ctypes.POINTER(vp)]),
+        "gbr_lambda_max": (ip, [ctypes.POINTER(vp), ip]),
         "gbr_batch_create": (ip, [ip, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(dp),
                                   ctypes.POINTER(dp), ctypes.POINTER(ip), dp, ctypes.POINTER(vp)]),
         "gbr_batch_destroy": (ip, [vp]),
@@ -408,6 +412,30 @@ class Solver:
 
     def sync(self, allow=()):
         return gbr_sync(self.ctx, allow)
+
+    # -- one slab of a grid split along y (see slab.py) --
+    def step_stage(self, k, dt=0.0, cfl=0.0, dt_max=1e300):
+        _check(load().gbr_step_stage(self.ctx, int(k), float(dt), float(cfl), float(dt_max)), "gbr_step_stage")
+
+    def halo_copy(self, side, direction, buf):
+        """direction 0: the six rows next to `side` into buf [4][6][nx];
+        1: buf into the six ghost rows beyond `side` (a halo side)."""
+        _expect(buf, "float64", (4, 6, self.nx))
+        p, dev = _ptr(buf)
+        _check(load().gbr_halo_copy(self.ctx, int(side), int(direction), ctypes.c_void_p(p), dev), "gbr_halo_copy")
+
+    def lambda_word(self):
+        """Device address of the current wavespeed word (uint64 bits of a double >= 0)."""
+        w = ctypes.c_void_p()
+        _check(load().gbr_lambda_word(self.ctx, ctypes.byref(w)), "gbr_lambda_word")
+        return w.value
+
+
+def lambda_max(solvers):
+    """Reduce the wavespeed words of solvers on one device to their maximum."""
+    arr = (ctypes.c_void_p * len(solvers))(*[s.ctx.value if isinstance(s.ctx, ctypes.c_void_p) else s.ctx
+                                             for s in solvers])
+    _check(load().gbr_lambda_max(arr, len(solvers)), "gbr_lambda_max")
 
 
 class Batch:
