@@ -17,9 +17,11 @@ workload and window and reported beside it; the 1024^2 grid of the same
 problem is reported as an extra key.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbr|reference]
-Under torchrun (N > 1) every rank runs an independent replica of the
-workload (weak scaling, no collective on the data path); the wall time is the
-max over ranks and the value the total over ranks.
+Under torchrun (N > 1) the grid is split along y into N slabs, one per rank
+and GPU (strong scaling): before every RK stage each slab receives six rows
+from each neighbour, and after every step the CFL wavespeed is max-reduced
+over the ranks (NCCL). The wall time is the max over ranks; the value is the
+whole grid's cell-updates over it.
 """
 from __future__ import annotations
 
@@ -60,6 +62,11 @@ def parse():
                     help="only the FP64 steps of the headline workload, bracketed by cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off); prints a short JSON line")
     ap.add_argument("--profile-precision", type=int, default=64, choices=[32, 64])
+    ap.add_argument("--profile-timed", action="store_true",
+                    help="bracket the headline forms' timed steps with cudaProfilerStart/Stop "
+                         "(for ncu --profile-from-start off)")
+    ap.add_argument("--prelude-precision", type=int, default=None, choices=[32, 64],
+                    help="precision of the untimed prelude (default: 32 above 2048 cells per side, else 64)")
     ap.add_argument("--ensemble-cases", type=int, default=64)
     ap.add_argument("--ensemble-steps", type=int, default=50)
     ap.add_argument("--paper-table", action="store_true",
@@ -86,7 +93,7 @@ FP32_PEAK_NOMINAL = 80550.0   # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 G
 # (dram__bytes_read.sum + dram__bytes_write.sum) of
 # `bench.py --profile-only --n N --steps 2 --warmup 1 --state-cache ...`.
 # Re-measure when the kernel changes (None: not measured for this kernel).
-F64_STAGE_DRAM_BYTES = {1024: None, 4096: None}
+F64_STAGE_DRAM_BYTES = {1024: 59.77e6, 4096: None}
 
 
 def fma_peaks():
@@ -539,7 +546,7 @@ def time_forms(args, torch, gbr, case, q_start, forms, st, flush, dist, ws, loca
         s.timing(True)
         barrier(dist, torch)
         with ClockSampler(local) as clk:
-            ms = time_steps(torch, s, args.steps, flush)
+            ms = time_steps(torch, s, args.steps, flush, profile=args.profile_timed)
         barrier(dist, torch)
         tm, dropped = s.get_timing()
         s.timing(False)
@@ -612,6 +619,80 @@ def fp32_entry(r, r64, costs, cells, fma, hbm_peak, acc):
             "clocks": r["clocks"], "density_l1_vs_fp64_20_steps": acc}
 
 
+def run_slabs(args, torch, gbr, cases, dist, rank, ws, local):
+    """N > 1: the workload's grid split along y into ws slabs, one per rank
+    (paper_2305_00762_gb300.slab.DistSlab). Every rank prepares the same
+    window state (the untimed prelude on the whole grid), keeps its rows and
+    steps them with halo exchanges before each stage and a max all-reduce of
+    the wavespeed after each step; the timed steps are bracketed by a barrier
+    and a synchronize on both sides, and the time is the max over ranks."""
+    from paper_2305_00762_gb300 import slab as S
+    case = cases.riemann_2d(args.n)
+    st = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    pre_precision = args.prelude_precision or (32 if args.n > 2048 else 64)
+    q_start, t_start, pre_steps = window_state(torch, gbr, case, st, args.t_window, pre_precision,
+                                               args.state_cache)
+    sl = S.DistSlab(case, rank, ws, precision=64)
+    q_local = q_start[:, sl.i0:sl.i1, :].contiguous()
+    del q_start
+    sl.set_state(q_local)
+    for _ in range(args.warmup):
+        sl.step_cfl(CFL)
+    sl.solver.timing(True)
+    barrier(dist, torch)
+    with ClockSampler(local) as clk:
+        total = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            sl.step_cfl(CFL)
+            b.record(st)
+            b.synchronize()
+            total += a.elapsed_time(b)
+    barrier(dist, torch)
+    tm, _ = sl.solver.get_timing()
+    sl.solver.timing(False)
+    ms = allmax(dist, torch, total)
+    cells = case.nx * case.ny
+    rc = sl.solver.sync(allow=(gbr.GBR_ERR_NONPHYSICAL,))
+    # end to end: each rank's slab in from pinned host memory and out again
+    hq = q_local.cpu().pin_memory()
+    hout = torch.empty_like(hq).pin_memory()
+    barrier(dist, torch)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        gbr.gbr_set_state(sl.solver.ctx, hq.numpy(), sl.solver.nx, sl.solver.ny)
+        sl._reduce_lambda()
+        sl.step_cfl(CFL)
+        gbr.gbr_get_state(sl.solver.ctx, hout.numpy(), sl.solver.nx, sl.solver.ny)
+    barrier(dist, torch)
+    e2e = 3.0 * cells * args.steps / allmax(dist, torch, time.perf_counter() - t0)
+    slab_bytes = 32 * sl.solver.nx * sl.solver.ny
+    sl.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": 3.0 * cells * args.steps / (ms * 1e-3), "unit": METRIC, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"riemann_2d_{args.n}x{args.n}_fp64", "nx": args.n, "ny": args.n,
+                       "cfl": CFL, "bc": "transmissive", "l2": "flushed between steps (256 MB write)",
+                       "window_t_start": round(t_start, 6), "prelude_steps": pre_steps,
+                       "prelude_precision": f"fp{pre_precision}", "parallelism": f"y-slabs x{ws}",
+                       "halo": "6 rows x 4 fields per neighbour per stage (NCCL send/recv)",
+                       "wavespeed": "max all-reduce per step (NCCL)"},
+            "e2e": {"value": e2e, "unit": METRIC, "h2d_bytes_per_step": slab_bytes * ws,
+                    "d2h_bytes_per_step": slab_bytes * ws},
+            "gpu_launches": int(sum(n for _, n in tm.values())),
+            "clocks": clk.summary(), "status": gbr.error_string(rc),
+        }
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -622,6 +703,8 @@ def main():
     from paper_2305_00762_gb300 import build, cases, costs, gbr
     build.build()
     gbr.load()
+    if ws > 1 and not args.paper_table:
+        return run_slabs(args, torch, gbr, cases, dist, rank, ws, local)
     if args.paper_table:
         if rank == 0:
             print(json.dumps({"paper_table_speed": run_paper_table(torch, gbr, cases), "cfl": 0.2,
@@ -634,7 +717,7 @@ def main():
     st = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
     cells = case.nx * case.ny
-    pre_precision = 32 if args.n > 2048 else 64
+    pre_precision = args.prelude_precision or (32 if args.n > 2048 else 64)
     q_start, t_start, pre_steps = window_state(torch, gbr, case, st, args.t_window, pre_precision,
                                                args.state_cache)
     torch.cuda.synchronize()
