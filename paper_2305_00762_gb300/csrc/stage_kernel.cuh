@@ -28,6 +28,29 @@ struct TileLayout {
     static constexpr int V = VISC ? 1 : 0;
     static constexpr int RW = BX + 12, RH = BY + 12;  // staged region (tile + halo)
     static constexpr int NU = RW * RH;
+    // The cells any later phase reads: the staged region without its four
+    // C x C corners (face stencils run along rows or columns of the tile).
+    // C = 6 - V: the viscous tangential gradients reach one row / column
+    // further. The learned sensor's direction assignment runs each
+    // direction's plain test on the whole detector box [3, B + 9), which
+    // reaches the cells [3, 6) of the corners: C = 3 there.
+    template <bool LEARNED>
+    struct Cross {
+        static constexpr int C = LEARNED ? 3 : 6 - V;
+        static constexpr int NMID = RW * (RH - 2 * C), NCOL = RW - 2 * C;
+        static constexpr int N = NMID + 2 * C * NCOL;
+        // Cross cell e < N is region cell cell(e): first the full-width rows
+        // [C, RH - C), then the columns [C, RW - C) of the bottom and top
+        // bands of C rows.
+        __device__ static __forceinline__ int cell(int e)
+        {
+            if (e < NMID) return C * RW + e;
+            const int f = e - NMID;
+            const int band = f / (C * NCOL), g = f - band * (C * NCOL);
+            const int r = g / NCOL;
+            return (band ? RH - C + r : r) * RW + C + (g - r * NCOL);
+        }
+    };
     // x-gradients: rows [6-V, 6+BY+V), region columns [3, BX+9)
     static constexpr int GXW = BX + 6, GXH = BY + 2 * V, NGX = GXW * GXH;
     // y-gradients: region rows [3, BY+9), columns [6-V, 6+BX+V)
@@ -287,27 +310,40 @@ __device__ __forceinline__ GrbCoef<T> grb_coef(int order)
     return c;
 }
 
+// In terms of the differences to the centre cell, Dm1 = Phi_{j-1} - Phi_j,
+// Dp1 = Phi_{j+1} - Phi_j, S2 = D_{-2} + D_{+2}, and dd = Phi'_{j-1} -
+// Phi'_{j+1}: Phi^L = Phi_j + delta with delta the weighted sum above, and
+// Phi^MP = Phi_j + m with m = minmod(Dp1, -7 Dm1). The MP test of Eq.
+// mp5Condition, (Phi^L - Phi_j)(Phi^L - Phi^MP) <= 1e-40, is taken as
+// delta (delta - m) <= 1e-40 (the same quantity, rounded differently; the
+// limited value is continuous across the test's boundary, where Phi^L lies
+// within the MP bounds).
 template <typename T>
-__device__ __forceinline__ T grb_check(const T* p, const T* d, bool& need, const GrbCoef<T>& C)
+__device__ __forceinline__ T grb_mp(T pj, T Dm1, T Dp1, T s1, T S2, T dj, T dd, bool& need, const GrbCoef<T>& C)
 {
-    const T pl = p[2] + (T(420) * d[2] + C.w1 * (d[1] - d[3]) + C.w2 * ((p[1] - p[2]) + (p[3] - p[2])) +
-                         C.w3 * ((p[0] - p[2]) + (p[4] - p[2]))) *
-                            T(1.0 / 840.0);
-    const T pmp = p[2] + minmod(p[3] - p[2], T(7) * (p[2] - p[1]));
-    need = !mp_accept((pl - p[2]) * (pl - pmp));
-    return pl;
+    const T delta = (T(420) * dj + C.w1 * dd + C.w2 * s1 + C.w3 * S2) * T(1.0 / 840.0);
+    const T m = minmod(Dp1, T(-7) * Dm1);
+    need = !mp_accept(delta * (delta - m));
+    return pj + delta;
 }
 
-// Eq. mp-procedure: the MP-limited value given the GRB value pl.
+// Eq. mp-procedure: the MP-limited value given the GRB value pl. The
+// curvature d_j = 2 (Phi_{j-1} - 2 Phi_j + Phi_{j+1}) - (Phi'_{j+1} -
+// Phi'_{j-1})/2 can come from the sums the GRB value was formed with: s1 =
+// Dm1 + Dp1 and dd = Phi'_{j-1} - Phi'_{j+1}.
 // Its products are explicitly rounded: it is inlined at two sites (packed
 // and per lane, see meg7_pair) that must round alike.
 template <typename T>
-__device__ __forceinline__ T mp_limit(const T* p, const T* d, T pl)
+__device__ __forceinline__ T mp_limit(const T* p, const T* d, T pl, T s1, T dd)
 {
     const T dm1 = rfma(T(2), rfma(T(-2), p[1], p[2]) + p[0], rmul(T(-0.5), d[2] - d[0]));
-    const T dj = rfma(T(2), rfma(T(-2), p[2], p[3]) + p[1], rmul(T(-0.5), d[3] - d[1]));
+    // (FP64 takes d_j from s1 and dd, which saves FP64 operations; FP32,
+    // bound by its instruction count rather than by one pipe, recomputes it
+    // and keeps fewer values live)
+    const T dj = sizeof(T) == 8 ? rfma(T(2), s1, rmul(T(0.5), dd))
+                                : rfma(T(2), rfma(T(-2), p[2], p[3]) + p[1], rmul(T(-0.5), d[3] - d[1]));
     const T dp1 = rfma(T(2), rfma(T(-2), p[3], p[4]) + p[2], rmul(T(-0.5), d[4] - d[2]));
-    const T md = rmul(T(0.5), p[2] + p[3]) - rmul(T(0.5), minmod(dj, dp1));
+    const T md = rmul(T(0.5), (p[2] + p[3]) - minmod(dj, dp1));
     const T ul = rfma(T(7), p[2] - p[1], p[2]);
     const T lc = rfma(T(4.0 / 3.0), minmod(dj, dm1), rmul(T(0.5), rfma(T(3), p[2], -p[1])));
     T pmin, pmax;
@@ -350,8 +386,14 @@ __device__ __forceinline__ void meg7_pair(const GrbCoef<T>& C, const T (&w)[6], 
     const T pL[5] = {w[0], w[1], w[2], w[3], w[4]}, dL[5] = {e[0], e[1], e[2], e[3], e[4]};
     const T pR[5] = {w[5], w[4], w[3], w[2], w[1]}, dR[5] = {-e[5], -e[4], -e[3], -e[2], -e[1]};
     bool needL, needR;
-    vl = grb_check(pL, dL, needL, C);
-    vr = grb_check(pR, dR, needR, C);
+    // The two sides share the difference w3 - w2 (the left side's D_{+1} is
+    // minus the right side's).
+    const T b = w[3] - w[2];
+    const T aL = w[1] - w[2], aR = w[4] - w[3];
+    const T s1L = aL + b, s1R = aR - b;          // second differences at j, j+1
+    const T ddL = e[1] - e[3], ddR = e[2] - e[4];  // (mirrored for the right side)
+    vl = grb_mp(w[2], aL, b, s1L, (w[0] - w[2]) + (w[4] - w[2]), e[2], ddL, needL, C);
+    vr = grb_mp(w[3], aR, -b, s1R, (w[5] - w[3]) + (w[1] - w[3]), -e[3], ddR, needR, C);
     if constexpr (sizeof(T) == 8) {
         const unsigned mL = __ballot_sync(0xffffffffu, needL), mR = __ballot_sync(0xffffffffu, needR);
         const int nL = __popc(mL), nR = __popc(mR);
@@ -366,14 +408,19 @@ __device__ __forceinline__ void meg7_pair(const GrbCoef<T>& C, const T (&w)[6], 
                 W[k] = __shfl_sync(0xffffffffu, w[k], src);
                 E[k] = __shfl_sync(0xffffffffu, e[k], src);
             }
+            // (the source lane's left and right values both travel; the
+            // receiving lane picks the side it limits)
             const T gl = __shfl_sync(0xffffffffu, vl, src), gr = __shfl_sync(0xffffffffu, vr, src);
+            const T sl = __shfl_sync(0xffffffffu, s1L, src), sr = __shfl_sync(0xffffffffu, s1R, src);
+            const T dl = __shfl_sync(0xffffffffu, ddL, src), dr = __shfl_sync(0xffffffffu, ddR, src);
+            const T g = isR ? gr : gl, s1 = isR ? sr : sl, dd = isR ? dr : dl;
             T p[5], d[5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
                 p[k] = isR ? W[5 - k] : W[k];
                 d[k] = isR ? -E[5 - k] : E[k];
             }
-            const T lim = mp_limit(p, d, isR ? gr : gl);
+            const T lim = mp_limit(p, d, g, s1, dd);
             const unsigned below = (1u << lane) - 1u;
             const T rl = __shfl_sync(0xffffffffu, lim, __popc(mL & below));
             const T rr = __shfl_sync(0xffffffffu, lim, (nL + __popc(mR & below)) & 31);
@@ -382,8 +429,8 @@ __device__ __forceinline__ void meg7_pair(const GrbCoef<T>& C, const T (&w)[6], 
             return;
         }
     }
-    if (needL) vl = mp_limit(pL, dL, vl);
-    if (needR) vr = mp_limit(pR, dR, vr);
+    if (needL) vl = mp_limit(pL, dL, vl, s1L, ddL);
+    if (needR) vr = mp_limit(pR, dR, vr, s1R, ddR);
 }
 
 // 1/2 (F(f_L) + F(f_R)) at the face after cell f[0]: the sum of Eq.
@@ -455,12 +502,16 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
 
     const int su = in.su, sg = in.sg;
     // Characteristic projection at the arithmetic-mean state.
+    // Every factor from one reciprocal square root y = 1/sqrt(gamma p rho):
+    // 1/c = rho y, c = gamma p y, 1/rho = gamma p y^2.
     const T rb = T(0.5) * (in.u[0][0] + in.u[0][su]);
     const T pb = T(0.5) * (in.u[3][0] + in.u[3][su]);
-    const T irb = T(1) / rb;
-    const T c2 = P.gamma * pb * irb;  // c^2
-    const T icb = trsqrt(c2);         // 1 / c
-    const T cb = c2 * icb;
+    const T gp = P.gamma * pb;
+    const T y = trsqrt(gp * rb);
+    const T icb = rb * y;            // 1 / c
+    const T cb = gp * y;             // c
+    const T c2 = cb * cb;            // c^2
+    const T irb = cb * y;            // 1 / rho
     const T al = T(0.5) * rb * icb;  // rho / (2 c)
     const T ic2 = icb * icb;         // 1 / c^2
     const T be = T(0.5) * ic2;       // 1 / (2 c^2)
@@ -472,12 +523,12 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
     #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 const int o = (k - 2);
-                const T tu = al * in.u[1][o * su], tp = be * in.u[3][o * su];
-                w0[k] = tp - tu;
-                w3[k] = tp + tu;
-                const T gu = al * in.g[1][o * sg], gp = be * in.g[3][o * sg];
-                e0[k] = gp - gu;
-                e3[k] = gp + gu;
+                const T tu = al * in.u[1][o * su], p = in.u[3][o * su];
+                w0[k] = rfma(be, p, -tu);
+                w3[k] = rfma(be, p, tu);
+                const T gu = al * in.g[1][o * sg], gp = in.g[3][o * sg];
+                e0[k] = rfma(be, gp, -gu);
+                e3[k] = rfma(be, gp, gu);
             }
             meg7_pair(coef, w0, e0, wL[0], wR[0]);
             meg7_pair(coef, w3, e3, wL[3], wR[3]);
@@ -487,8 +538,8 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
     #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 const int o = (k - 2);
-                w[k] = in.u[0][o * su] - ic2 * in.u[3][o * su];
-                e[k] = in.g[0][o * sg] - ic2 * in.g[3][o * sg];
+                w[k] = rfma(-ic2, in.u[3][o * su], in.u[0][o * su]);
+                e[k] = rfma(-ic2, in.g[3][o * sg], in.g[0][o * sg]);
             }
             meg7_pair(coef, w, e, wL[1], wR[1]);
         }
@@ -798,6 +849,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
                                            unsigned char* smem_raw, const CUtensorMap* tmap = nullptr)
 {
     using L = TileLayout<BX, BY, VISC, CONS>;
+    using X = typename L::template Cross<LEARNED>;  // the staged cells
     T* const sm = reinterpret_cast<T*>(smem_raw);
     T* const sU = sm + L::oU;
     T* const sGX = sm + L::oGX;
@@ -875,15 +927,18 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
                 if (tid == 0) atomicOr(P.err, kErrTimeout);
                 return;
             }
-            for (int idx = tid; idx < NU; idx += NT)
+            for (int e = tid; e < X::N; e += NT) {
+                const int idx = X::cell(e);
                 stage_cell(idx, raw[idx], raw[NU + idx], raw[2 * NU + idx], raw[3 * NU + idx]);
+            }
             staged = true;
         }
     }
     if (!staged) {
         // Plain loads, clamped to the padded extent (the clamped cells only
         // feed results that are never stored).
-        for (int idx = tid; idx < NU; idx += NT) {
+        for (int e = tid; e < X::N; e += NT) {
+            const int idx = X::cell(e);
             const int ry = idx / RW, rx = idx - ry * RW;
             const int gx = min(tx0 + rx, nx + 2 * kGhost - 1);
             const int gy = min(ty0 + ry, ny + 2 * kGhost - 1);
