@@ -333,16 +333,20 @@ __device__ __forceinline__ T grb_mp(T pj, T Dm1, T Dp1, T s1, T S2, T dj, T dd, 
 // Dm1 + Dp1 and dd = Phi'_{j-1} - Phi'_{j+1}.
 // Its products are explicitly rounded: it is inlined at two sites (packed
 // and per lane, see meg7_pair) that must round alike.
+// The curvature d_{j+1} is the other side's d_j (the right value at the same
+// face is centred on cell j+1, mirrored, and the curvature is unchanged by
+// the mirror): it comes from that side's sums s1o, ddo.
 template <typename T>
-__device__ __forceinline__ T mp_limit(const T* p, const T* d, T pl, T s1, T dd)
+__device__ __forceinline__ T mp_limit(const T* p, const T* d, T pl, T s1, T dd, T s1o, T ddo)
 {
     const T dm1 = rfma(T(2), rfma(T(-2), p[1], p[2]) + p[0], rmul(T(-0.5), d[2] - d[0]));
-    // (FP64 takes d_j from s1 and dd, which saves FP64 operations; FP32,
-    // bound by its instruction count rather than by one pipe, recomputes it
-    // and keeps fewer values live)
+    // (FP64 takes d_j and d_{j+1} from the sums, which saves FP64
+    // operations; FP32, bound by its instruction count rather than by one
+    // pipe, recomputes them and keeps fewer values live)
     const T dj = sizeof(T) == 8 ? rfma(T(2), s1, rmul(T(0.5), dd))
                                 : rfma(T(2), rfma(T(-2), p[2], p[3]) + p[1], rmul(T(-0.5), d[3] - d[1]));
-    const T dp1 = rfma(T(2), rfma(T(-2), p[3], p[4]) + p[2], rmul(T(-0.5), d[4] - d[2]));
+    const T dp1 = sizeof(T) == 8 ? rfma(T(2), s1o, rmul(T(0.5), ddo))
+                                 : rfma(T(2), rfma(T(-2), p[3], p[4]) + p[2], rmul(T(-0.5), d[4] - d[2]));
     const T md = rmul(T(0.5), (p[2] + p[3]) - minmod(dj, dp1));
     const T ul = rfma(T(7), p[2] - p[1], p[2]);
     const T lc = rfma(T(4.0 / 3.0), minmod(dj, dm1), rmul(T(0.5), rfma(T(3), p[2], -p[1])));
@@ -414,13 +418,14 @@ __device__ __forceinline__ void meg7_pair(const GrbCoef<T>& C, const T (&w)[6], 
             const T sl = __shfl_sync(0xffffffffu, s1L, src), sr = __shfl_sync(0xffffffffu, s1R, src);
             const T dl = __shfl_sync(0xffffffffu, ddL, src), dr = __shfl_sync(0xffffffffu, ddR, src);
             const T g = isR ? gr : gl, s1 = isR ? sr : sl, dd = isR ? dr : dl;
+            const T s1o = isR ? sl : sr, ddo = isR ? dl : dr;
             T p[5], d[5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
                 p[k] = isR ? W[5 - k] : W[k];
                 d[k] = isR ? -E[5 - k] : E[k];
             }
-            const T lim = mp_limit(p, d, g, s1, dd);
+            const T lim = mp_limit(p, d, g, s1, dd, s1o, ddo);
             const unsigned below = (1u << lane) - 1u;
             const T rl = __shfl_sync(0xffffffffu, lim, __popc(mL & below));
             const T rr = __shfl_sync(0xffffffffu, lim, (nL + __popc(mR & below)) & 31);
@@ -429,8 +434,8 @@ __device__ __forceinline__ void meg7_pair(const GrbCoef<T>& C, const T (&w)[6], 
             return;
         }
     }
-    if (needL) vl = mp_limit(pL, dL, vl, s1L, ddL);
-    if (needR) vr = mp_limit(pR, dR, vr, s1R, ddR);
+    if (needL) vl = mp_limit(pL, dL, vl, s1L, ddL, s1R, ddR);
+    if (needR) vr = mp_limit(pR, dR, vr, s1R, ddR, s1L, ddL);
 }
 
 // 1/2 (F(f_L) + F(f_R)) at the face after cell f[0]: the sum of Eq.
@@ -699,10 +704,16 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
         const T SL = tmin(unL - cL, ut - ct);
         const T SR = tmax(unR + cR, ut + ct);
         const T mL = rL * (SL - unL), mR = rR * (SR - unR);
-        const T Ss = (pR - pL + mL * unL - mR * unR) / (mL - mR);
-        // 1/(S_L - S*) and 1/(S_R - S*) from one division
-        const T dL = SL - Ss, dR = SR - Ss, iLR = T(1) / (dL * dR);
-        const T iL = dR * iLR, iR = dL * iLR;
+        // S* = num / den and 1/(S_L - S*), 1/(S_R - S*) from one division:
+        // with nL = S_L den - num, nR = S_R den - num and z = 1/(den nL nR),
+        // S* = num nL nR z, 1/(S_L - S*) = den^2 nR z, 1/(S_R - S*) = den^2 nL z
+        const T num = pR - pL + mL * unL - mR * unR, den = mL - mR;
+        const T nL = SL * den - num, nR = SR * den - num;
+        const T nLR = nL * nR;
+        const T z = T(1) / (den * nLR);
+        const T Ss = num * nLR * z;
+        const T d2z = den * den * z;
+        const T iL = nR * d2z, iR = nL * d2z;
         const T kL = mL * iL, kR = mR * iR;
         const T QsL[4] = {kL, kL * Ss, kL * utL, kL * (EL * irL + (Ss - unL) * Ss) + (Ss - unL) * pL * iL};
         const T QsR[4] = {kR, kR * Ss, kR * utR, kR * (ER * irR + (Ss - unR) * Ss) + (Ss - unR) * pR * iR};
@@ -720,11 +731,11 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
                 aR *= phi;
             }
         }
+        // 1/2 |A| dQ = 1/2 (aL (QsL - QL) + aS (QsR - QsL) + aR (QR - QsR)),
+        // regrouped by state: four fused terms per component
+        const T hL = T(0.5) * (aL - aS), hS = T(0.5) * (aS - aR), hQL = T(0.5) * aL, hQR = T(0.5) * aR;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const T adq = aL * (QsL[m] - QL[m]) + aS * (QsR[m] - QsL[m]) + aR * (QR[m] - QsR[m]);
-            out[m] = Fc[m] - T(0.5) * adq;
-        }
+        for (int m = 0; m < 4; ++m) out[m] = Fc[m] - hL * QsL[m] - hS * QsR[m] + hQL * QL[m] - hQR * QR[m];
     }
 
     if constexpr (VISC) {
