@@ -114,9 +114,12 @@ typedef enum {
      * or stage evaluation (read back with gbr_get_flags); 0: off (default). */
     GBR_OPT_RECORD_FLAGS = 1,
     /* Discontinuity sensor: 0 = the density detector of Sec. 2.4 (default);
-     * 1 = the learned sensor (needs gbr_set_sensor_weights first, else
-     * GBR_ERR_STATE; used in precision 32 only), with the density detector as
-     * fallback. */
+     * 1 = the learned sensor evaluated by a separate decision pass before
+     * each stage (the form batches use; the faster one); 2 = the learned
+     * sensor's network evaluated inside the FP32 stage kernel on the tile it
+     * has staged. Both take the same decisions; they need
+     * gbr_set_sensor_weights first (else GBR_ERR_STATE), act in precision 32
+     * only, and keep the density detector as fallback. */
     GBR_OPT_SENSOR = 2,
     /* 1: bracket every kernel launch with CUDA events on the context's
      * stream (read back with gbr_get_timing); 0: off (default). */
@@ -301,8 +304,9 @@ int gbr_get_timing(gbr_ctx *ctx, double *ms, int *launches, int *dropped);
  * discontinuity whose direction the plain per-direction tests assign (both
  * directions if neither test marks the cell). The buffer of Eq. buffer is
  * unchanged. The network runs on the tcgen05 tensor cores (BF16 operands,
- * FP32 accumulation in tensor memory) in a decision pass launched before each
- * FP32 stage; the stage kernel applies its per-cell decisions.
+ * FP32 accumulation in tensor memory), in a decision pass launched before
+ * each FP32 stage (GBR_OPT_SENSOR = 1), or inside the FP32 stage kernel on
+ * the cells the stage has staged (GBR_OPT_SENSOR = 2).
  * Weight vector (GBR_SENSOR_PARAMS floats): W1[50][32], b1[32], W2[32][32],
  * b2[32], w3[32], b3, with h1 = relu(x W1 + b1) rounded to BF16,
  * h2 = relu(h1 W2 + b2), p = 1/(1 + exp(-(h2 . w3 + b3))).

@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) batch_stage_kernel
         P.sensor = sensor;
         P.dec = C.dec;
         P.stall_bytes = 0;
+        P.stall_mma = 0;
         stage_tile<T, BX, BY, NT, false, LEARNED>(P, tx * BX, ty * BY, smem_raw);
     }
 }

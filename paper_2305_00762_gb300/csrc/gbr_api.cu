@@ -202,7 +202,12 @@ int stage(gbr_ctx* c, const StageParams& p)
     Timed tm(c, GBR_KERNEL_STAGE);  // includes the learned sensor's decision pass
     if (c->precision == 32 && p.sensor) {
         StageParams q = p;
-        q.dec = c->dec;
+        if (c->sensor == 2) {  // the network fused into the stage kernel
+            q.dec = nullptr;
+            q.stall_mma = c->stall_test == 2 ? 1u : 0u;
+            return cuda_status(launch_stage_f32(q, c->stream));
+        }
+        q.dec = c->dec;  // a separate decision pass, then the stage
         cudaError_t e =
             launch_sensor_decide(c->g, c->ph.gamma, p.q, p.sensor, c->dec, p.err, c->stall_test == 2, c->stream);
         if (e == cudaSuccess) e = launch_stage_f32(q, c->stream);
@@ -563,8 +568,8 @@ int gbr_set_option(gbr_ctx* c, int key, double val)
         c->record_flags = (int)val;
         return GBR_OK;
     case GBR_OPT_SENSOR:
-        if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;
-        if (val == 1.0 && !c->d_sensor) return GBR_ERR_STATE;
+        if (val != 0.0 && val != 1.0 && val != 2.0) return GBR_ERR_ARG;
+        if (val != 0.0 && !c->d_sensor) return GBR_ERR_STATE;
         c->sensor = (int)val;
         return GBR_OK;
     case GBR_OPT_ORDER:

@@ -91,6 +91,7 @@ struct StageParams {
     const SensorDev* sensor; // learned-sensor weights (FP32 form) or nullptr
     const unsigned char* dec;  // learned-sensor decisions of padded cells [3, n+9) (pitch g.pitch), with sensor
     unsigned stall_bytes;    // failure-detection test hook: extra bytes the tile staging waits for (0)
+    unsigned stall_mma;      // failure-detection test hook: the fused sensor withholds its first MMA batch (0)
 };
 
 // Ghost fill of one padded state, plus the per-step scalar bookkeeping done

@@ -198,7 +198,6 @@ __global__ void __launch_bounds__(256) sensor_dataset_kernel(const SensorTilePar
 // kErrTimeout, skips its remaining rounds and still frees its columns.
 // ---------------------------------------------------------------------------
 constexpr int kTcGroups = 2;  // warpgroups per CTA (measured fastest of 1, 2 and 4)
-constexpr unsigned kColA = 0, kColD = 32, kColsPerGroup = 64;
 // shared memory per CTA for G warpgroups: more than 228 KB / (8/G + 1) with
 // the 1 KB the runtime reserves per CTA, so no more than 8/G CTAs fit
 template <int G>
@@ -227,79 +226,6 @@ struct TcSmem {
 static_assert(sizeof(TcSmem) <= tc_smem_bytes<kTcGroups>(), "tcgen05 sensor tile exceeds its shared memory");
 static_assert((sizeof(float) * 2 * kRH * kRW) % 128 == 0, "the copy's landing area must stay 128-byte aligned");
 static_assert(kRawW % 2 == 0 && kRawW <= 256 && kRH <= 256, "tensor copy box: 16-byte rows, at most 256 wide");
-
-__host__ __device__ constexpr int core_index(int n, int k, int kgroups)
-{
-    return ((n >> 3) * kgroups + (k >> 3)) * 64 + (n & 7) * 8 + (k & 7);
-}
-
-// Shared-memory matrix descriptor (no swizzle, K-major core matrices):
-// start address, leading byte offset (between core matrices adjacent in K),
-// stride byte offset (between adjacent 8-row groups), descriptor version 1.
-__device__ __forceinline__ uint64_t tc_smem_desc(const void* p, unsigned lbo, unsigned sbo)
-{
-    const unsigned a = smem_addr(p);
-    return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// Instruction descriptor of kind::f16: FP32 accumulation, BF16 A and B, both
-// K-major, N = 32, M = 128.
-constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kSensorH >> 3) << 17) |
-                              ((uint32_t)(128 >> 4) << 24);
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// D[tmem d] (+)= A[tmem a] B[desc], issued by one thread.
-__device__ __forceinline__ void tc_mma(uint32_t d, uint32_t a, uint64_t bdesc, bool accumulate)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
-        "r"(a), "l"(bdesc), "r"(kTcIdesc), "r"(accumulate ? 1 : 0)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_commit(unsigned long long* bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_st16(uint32_t taddr, const uint32_t (&v)[16])
-{
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-            taddr),
-        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr)
-        : "memory");
-}
-
-// Wait for phase `parity` of the mbarrier: a tight spin first (an MMA round
-// trip takes a few hundred cycles), then polls spaced by sleeps, about a
-// second in all; false if it gave up.
-__device__ __forceinline__ bool mbar_wait_parity_bounded(unsigned long long* bar, unsigned parity)
-{
-    for (int it = 0; it < (1 << 12); ++it)
-        if (mbar_test(bar, parity)) return true;
-    for (int it = 0; it < (1 << 24); ++it) {
-        if (mbar_test(bar, parity)) return true;
-        __nanosleep(64);
-    }
-    return false;
-}
 
 // Warp 0 waits for the MMAs' completion; the block barrier then releases the
 // other warps (which read the accumulators after their own fence). True on

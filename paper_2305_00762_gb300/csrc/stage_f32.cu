@@ -11,9 +11,13 @@ cudaError_t launch_stage_f32(const StageParams& p, cudaStream_t s)
         if (p.ph.mu > 0.0) return launch_stage_t<float, 28, 16, 256, true, false, 4>(p, s);
         return launch_stage_t<float, 28, 16, 256, false, false, 4>(p, s);
     }
-    if (p.sensor) {
-        if (p.ph.mu > 0.0) return launch_stage_t<float, 28, 16, 256, true, true>(p, s);
-        return launch_stage_t<float, 28, 16, 256, false, true>(p, s);
+    if (p.sensor && p.dec) {  // decisions from the separate decision pass
+        if (p.ph.mu > 0.0) return launch_stage_t<float, 28, 16, 256, true, 1>(p, s);
+        return launch_stage_t<float, 28, 16, 256, false, 1>(p, s);
+    }
+    if (p.sensor) {  // the network fused into the stage
+        if (p.ph.mu > 0.0) return launch_stage_t<float, 28, 16, 256, true, 2>(p, s);
+        return launch_stage_t<float, 28, 16, 256, false, 2>(p, s);
     }
     if (p.ph.mu > 0.0) return launch_stage_t<float, 28, 16, 256, true>(p, s);
     return launch_stage_t<float, 28, 16, 256, false>(p, s);

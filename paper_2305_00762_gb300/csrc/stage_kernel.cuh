@@ -33,10 +33,11 @@ struct TileLayout {
     // C = 6 - V: the viscous tangential gradients reach one row / column
     // further. The learned sensor's direction assignment runs each
     // direction's plain test on the whole detector box [3, B + 9), which
-    // reaches the cells [3, 6) of the corners: C = 3 there.
-    template <bool LEARNED>
+    // reaches the cells [3, 6) of the corners: C = 3 there; its fused
+    // inference reads the 5 x 5 windows of the box, [1, B + 11): C = 1.
+    template <int LEARNED>
     struct Cross {
-        static constexpr int C = LEARNED ? 3 : 6 - V;
+        static constexpr int C = LEARNED == 2 ? 1 : (LEARNED ? 3 : 6 - V);
         static constexpr int NMID = RW * (RH - 2 * C), NCOL = RW - 2 * C;
         static constexpr int N = NMID + 2 * C * NCOL;
         // Cross cell e < N is region cell cell(e): first the full-width rows
@@ -232,6 +233,13 @@ __device__ __forceinline__ bool positive_bits(double x)
     const long long b = __double_as_longlong(x);
     return b > 0 && b <= 0x7ff0000000000000LL;
 }
+// 0 < x in T: the comparison itself in FP32, the bit test in FP64 (off the
+// FP64 pipe; the same answer for every value, NaN included).
+__device__ __forceinline__ bool tpositive(float x) { return x > 0.0f; }
+__device__ __forceinline__ bool tpositive(double x) { return positive_bits(x); }
+// a < b for values that are not NaN, in T (FP64 on the integer pipe).
+__device__ __forceinline__ bool tless(float a, float b) { return a < b; }
+__device__ __forceinline__ bool tless(double a, double b) { return ordkey(a) < ordkey(b); }
 
 // Eq. six: dx-scaled sixth-order gradient at s[0] along stride st.
 template <typename T>
@@ -250,7 +258,7 @@ __device__ __forceinline__ bool trouble_cell(const T* r, int st)
     const T eps = T(0.9 * 0.5 / (1.0 - 0.9 * 0.5) * 1e-6);
     const T a = tabs(r[0] - r[-st]) + tabs(rfma(T(-2), r[-st], r[0]) + r[-2 * st]);
     const T b = tabs(r[0] - r[st]) + tabs(rfma(T(-2), r[st], r[0]) + r[2 * st]);
-    return T(2) * rfma(T(2) * a, b, eps) < rfma(a, a, rfma(b, b, eps));
+    return tless(T(2) * rfma(T(2) * a, b, eps), rfma(a, a, rfma(b, b, eps)));
 }
 
 // The value of psi itself (Eq. detector), same a, b and eps as trouble_cell.
@@ -348,8 +356,9 @@ __device__ __forceinline__ T mp_limit(const T* p, const T* d, T pl, T s1, T dd, 
     const T dp1 = sizeof(T) == 8 ? rfma(T(2), s1o, rmul(T(0.5), ddo))
                                  : rfma(T(2), rfma(T(-2), p[3], p[4]) + p[2], rmul(T(-0.5), d[4] - d[2]));
     const T md = rmul(T(0.5), (p[2] + p[3]) - minmod(dj, dp1));
-    const T ul = rfma(T(7), p[2] - p[1], p[2]);
-    const T lc = rfma(T(4.0 / 3.0), minmod(dj, dm1), rmul(T(0.5), rfma(T(3), p[2], -p[1])));
+    const T Dm1 = p[1] - p[2];
+    const T ul = rfma(T(-7), Dm1, p[2]);
+    const T lc = rfma(T(4.0 / 3.0), minmod(dj, dm1), rfma(T(-0.5), Dm1, p[2]));
     T pmin, pmax;
     mp_bounds(p[2], p[3], md, ul, lc, pmin, pmax);
     return pl + minmod(pmin - pl, pmax - pl);
@@ -592,13 +601,13 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
         // positivity fallback: a face state with rho <= 0 or p <= 0 takes the
         // adjacent cell's state (characteristic reconstruction across a
         // strong shock, e.g. the foot of the double Mach reflection)
-        if (!(rL > T(0) && pL > T(0))) {
+        if (!(tpositive(rL) && tpositive(pL))) {
             rL = in.u[0][0];
             unL = in.u[1][0];
             utL = in.u[2][0];
             pL = in.u[3][0];
         }
-        if (!(rR > T(0) && pR > T(0))) {
+        if (!(tpositive(rR) && tpositive(pR))) {
             rR = in.u[0][su];
             unR = in.u[1][su];
             utR = in.u[2][su];
@@ -645,7 +654,7 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
             pR = P.gm1 * (ER - T(0.5) * rR * (unR * unR + utR * utR));
         }
         // positivity fallback (as for MEG7-prim): the adjacent cell's state
-        if (!(rL > T(0) && pL > T(0))) {
+        if (!(tpositive(rL) && tpositive(pL))) {
             rL = in.u[0][0];
             unL = in.u[1][0];
             utL = in.u[2][0];
@@ -656,7 +665,7 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
             QL[2] = rL * utL;
             QL[3] = EL;
         }
-        if (!(rR > T(0) && pR > T(0))) {
+        if (!(tpositive(rR) && tpositive(pR))) {
             rR = in.u[0][su];
             unR = in.u[1][su];
             utR = in.u[2][su];
@@ -851,10 +860,306 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Fifth-generation tensor cores (tcgen05), shared by the learned sensor's
+// decision pass (sensor.cu) and the stage kernel's fused inference: matrix
+// and instruction descriptors, MMA issue and commit, tensor-memory loads and
+// stores of 32 lanes x 16 columns, and a bounded mbarrier wait.
+// ---------------------------------------------------------------------------
+// Tensor memory of one warpgroup's network rounds: 64 columns, A at [0, 32)
+// (layer 1's features, then layer 2's inputs) and D at [32, 64) (the
+// accumulators of both layers in turn).
+constexpr unsigned kColA = 0, kColD = 32, kColsPerGroup = 64;
+
+__host__ __device__ constexpr int core_index(int n, int k, int kgroups)
+{
+    return ((n >> 3) * kgroups + (k >> 3)) * 64 + (n & 7) * 8 + (k & 7);
+}
+
+// Shared-memory matrix descriptor (no swizzle, K-major core matrices):
+// start address, leading byte offset (between core matrices adjacent in K),
+// stride byte offset (between adjacent 8-row groups), descriptor version 1.
+__device__ __forceinline__ uint64_t tc_smem_desc(const void* p, unsigned lbo, unsigned sbo)
+{
+    const unsigned a = smem_addr(p);
+    return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulation, BF16 A and B, both
+// K-major, N = 32, M = 128.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kSensorH >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem d] (+)= A[tmem a] B[desc], issued by one thread.
+__device__ __forceinline__ void tc_mma(uint32_t d, uint32_t a, uint64_t bdesc, bool accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+        "r"(a), "l"(bdesc), "r"(kTcIdesc), "r"(accumulate ? 1 : 0)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(unsigned long long* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_st16(uint32_t taddr, const uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+// Wait for phase `parity` of the mbarrier: a tight spin first (an MMA round
+// trip takes a few hundred cycles), then polls spaced by sleeps, about a
+// second in all; false if it gave up.
+__device__ __forceinline__ bool mbar_wait_parity_bounded(unsigned long long* bar, unsigned parity)
+{
+    for (int it = 0; it < (1 << 12); ++it)
+        if (mbar_test(bar, parity)) return true;
+    for (int it = 0; it < (1 << 24); ++it) {
+        if (mbar_test(bar, parity)) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
+
 // Error-word bits: 1 = non-physical state, 2 = a bounded wait gave up.
 constexpr unsigned kErrNonPhysical = 1u, kErrTimeout = 2u;
 
-template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED = false, int ORDER = 7, bool CONS = false,
+// The learned sensor's inference fused into the FP32 stage (learned mode 2):
+// the network's decision for every cell of the tile's detector box (region
+// cells [3, B + 9) in each direction), from the FP32 primitives the stage
+// has just staged (the same values, features, tensor-core rounds and
+// thresholds as the separate decision pass, so the same decisions). Scratch:
+// `lo` (>= 20 KB, dead until phase 1) holds the 5-wide window maxima and
+// minima and the normalisation scales; `hi` (>= 6.5 KB + 128, dead until
+// phase 2) the weights in the tensor cores' core-matrix order. Per CTA 128
+// tensor-memory columns, allocated here and freed before returning (the
+// kernel's shared memory keeps at most two CTAs on an SM: 256 of 512
+// columns). Returns false if a bounded wait gave up (uniform over the CTA).
+template <int BX, int BY, int NT, bool VISC>
+__device__ bool fused_sensor_decisions(const StageParams& P, const float* sU, unsigned char* sT, unsigned char* lo,
+                                       unsigned char* hi)
+{
+    using L = TileLayout<BX, BY, VISC, false>;
+    constexpr int RW = L::RW, NU = L::NU, BW = L::BOXW, NB = L::NBOX;
+    constexpr int HR = BY + 10;  // region rows [1, BY + 11) of the windows
+    constexpr int G = NT / 128;  // warpgroups: the M = 128 rows of each one's MMAs
+    static_assert(NT % 128 == 0, "whole warpgroups");
+    const int tid = threadIdx.x, warp = tid >> 5;
+    float* hrx = reinterpret_cast<float*>(lo);  // [HR][BW] window max of rho, then min; p likewise
+    float* hrn = hrx + HR * BW;
+    float* hpx = hrn + HR * BW;
+    float* hpn = hpx + HR * BW;
+    float* scr = hpn + HR * BW;  // [NB] scales
+    float* scp = scr + NB;
+    unsigned char* hb = hi + ((128u - (smem_addr(hi) & 127u)) & 127u);
+    __nv_bfloat16* w1c = reinterpret_cast<__nv_bfloat16*>(hb);
+    __nv_bfloat16* w2c = w1c + kSensorH * kSensorK;
+    float* b1 = reinterpret_cast<float*>(w2c + kSensorH * kSensorH);
+    float* b2 = b1 + kSensorH;
+    float* w3 = b2 + kSensorH;
+    float* b3 = w3 + kSensorH;
+    __shared__ __align__(8) unsigned long long mma_bar;  // never reused for anything else
+    __shared__ unsigned tmem_base;
+    const SensorDev* w = P.sensor;
+    for (int i = tid; i < kSensorH * kSensorK; i += NT) {
+        const int n = i / kSensorK, k = i - n * kSensorK;
+        w1c[core_index(n, k, kSensorK / 8)] = w->w1t[n * kW1Pitch + k];
+    }
+    for (int i = tid; i < kSensorH * kSensorH; i += NT) {
+        const int n = i / kSensorH, k = i - n * kSensorH;
+        w2c[core_index(n, k, kSensorH / 8)] = w->w2t[n * kW2Pitch + k];
+    }
+    if (tid < kSensorH) {
+        b1[tid] = w->b1[tid];
+        b2[tid] = w->b2[tid];
+        w3[tid] = w->w3[tid];
+    }
+    if (tid == 0) {
+        *b3 = w->b3;
+        mbar_init(&mma_bar, 1);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the MMAs read the weights
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(kColsPerGroup * G)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // window maxima and minima over 5 columns (region columns bx + 1 .. bx + 5)
+    for (int e = tid; e < HR * BW; e += NT) {
+        const int h = e / BW, bx = e - h * BW;
+        const float* r = sU + (h + 1) * RW + (bx + 1);
+        const float* p = r + 3 * NU;
+        float rmx = r[0], rmn = r[0], pmx = p[0], pmn = p[0];
+#pragma unroll
+        for (int d = 1; d < 5; ++d) {
+            rmx = fmaxf(rmx, r[d]);
+            rmn = fminf(rmn, r[d]);
+            pmx = fmaxf(pmx, p[d]);
+            pmn = fminf(pmn, p[d]);
+        }
+        hrx[e] = rmx;
+        hrn[e] = rmn;
+        hpx[e] = pmx;
+        hpn[e] = pmn;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tm = tmem_base;
+    // ... then over 5 rows: the scales 1/(max_k |q_k - q_c| + floor) of each box cell
+    for (int c = tid; c < NB; c += NT) {
+        const int by = c / BW, bx = c - by * BW;
+        float rmx = hrx[by * BW + bx], rmn = hrn[by * BW + bx], pmx = hpx[by * BW + bx], pmn = hpn[by * BW + bx];
+#pragma unroll
+        for (int d = 1; d < 5; ++d) {
+            const int o = (by + d) * BW + bx;
+            rmx = fmaxf(rmx, hrx[o]);
+            rmn = fminf(rmn, hrn[o]);
+            pmx = fmaxf(pmx, hpx[o]);
+            pmn = fminf(pmn, hpn[o]);
+        }
+        const float rc = sU[(by + 3) * RW + bx + 3], pc = sU[3 * NU + (by + 3) * RW + bx + 3];
+        const float mr = fmaxf(0.f, fmaxf(rmx - rc, rc - rmn)), mp = fmaxf(0.f, fmaxf(pmx - pc, pc - pmn));
+        scr[c] = 1.f / (mr + kSensorFloor);
+        scp[c] = 1.f / (mp + kSensorFloor);
+    }
+    __syncthreads();
+    // this warp's quarter of the lanes, in its warpgroup's columns
+    const uint32_t lanes = ((uint32_t)((warp & 3) * 32) << 16) + kColsPerGroup * (uint32_t)(warp >> 2);
+    const uint64_t d1 = tc_smem_desc(w1c, 128, 128 * (kSensorK / 8));
+    const uint64_t d2 = tc_smem_desc(w2c, 128, 128 * (kSensorH / 8));
+    unsigned phase = 0;
+    bool ok = true;
+    for (int round = 0; round < (NB + NT - 1) / NT && ok; ++round) {
+        const int c = round * NT + tid;
+        const bool valid = c < NB;
+        const int cc = valid ? c : 0;  // a lane past the box works on cell 0 and stores nothing
+        const int by = cc / BW, bx = cc - by * BW;
+        const float* r = sU + (by + 3) * RW + (bx + 3);
+        const float* p = r + 3 * NU;
+        const float sr = scr[cc], sp = scp[cc];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {  // features 32 half .. 32 half + 31
+            uint32_t a[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int k = 32 * half + 2 * j;
+                a[j] = pack_bf16(sensor_feature(r, p, RW, sr, sp, k), sensor_feature(r, p, RW, sr, sp, k + 1));
+            }
+            tc_st16(tm + lanes + kColA + 16 * half, a);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0 && !(P.stall_mma && round == 0)) {
+            tc_fence_after();
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int ks = 0; ks < kSensorK / 16; ++ks)
+                    tc_mma(tm + kColsPerGroup * g + kColD, tm + kColsPerGroup * g + kColA + 8 * ks,
+                           d1 + (uint64_t)((256 * ks) >> 4), ks > 0);
+            tc_commit(&mma_bar);
+        }
+        bool done = true;
+        if (warp == 0) done = mbar_wait_parity_bounded(&mma_bar, phase);
+        if (!__syncthreads_and(done)) {
+            ok = false;
+            break;
+        }
+        phase ^= 1u;
+        tc_fence_after();
+        uint32_t hh[16];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {  // hidden units 16 half .. 16 half + 15
+            uint32_t d[16];
+            tc_ld16(tm + lanes + kColD + 16 * half, d);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int n = 16 * half + 2 * j;
+                hh[8 * half + j] = pack_bf16(fmaxf(__uint_as_float(d[2 * j]) + b1[n], 0.f),
+                                             fmaxf(__uint_as_float(d[2 * j + 1]) + b1[n + 1], 0.f));
+            }
+        }
+        tc_st16(tm + lanes + kColA, hh);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int ks = 0; ks < kSensorH / 16; ++ks)
+                    tc_mma(tm + kColsPerGroup * g + kColD, tm + kColsPerGroup * g + kColA + 8 * ks,
+                           d2 + (uint64_t)((256 * ks) >> 4), ks > 0);
+            tc_commit(&mma_bar);
+        }
+        done = true;
+        if (warp == 0) done = mbar_wait_parity_bounded(&mma_bar, phase);
+        if (!__syncthreads_and(done)) {
+            ok = false;
+            break;
+        }
+        phase ^= 1u;
+        tc_fence_after();
+        float z = 0.f;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            uint32_t d[16];
+            tc_ld16(tm + lanes + kColD + 16 * half, d);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int n = 16 * half + j;
+                z += fmaxf(__uint_as_float(d[j]) + b2[n], 0.f) * w3[n];
+            }
+        }
+        const float pv = 1.f / (1.f + expf(-(z + *b3)));
+        if (valid) sT[c] = pv > kSensorHi ? 1 : (pv < kSensorLo ? 0 : 2);
+    }
+    // release the columns after the last wait (no MMA is in flight: every
+    // issued batch was waited for, and a withheld one was never issued)
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kColsPerGroup * G)
+                     : "memory");
+    }
+    return ok;
+}
+
+// LEARNED: 0 = the density detector; 1 = the learned sensor's decisions
+// read from the decision pass (P.dec); 2 = the learned sensor's inference
+// fused into the stage (FP32 only).
+template <typename T, int BX, int BY, int NT, bool VISC, int LEARNED = 0, int ORDER = 7, bool CONS = false,
           bool TMA = false>
 __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, const int ty0,
                                            unsigned char* smem_raw, const CUtensorMap* tmap = nullptr)
@@ -957,7 +1262,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
             stage_cell(idx, P.q[o], P.q[o + plane], P.q[o + 2 * plane], P.q[o + 3 * plane]);
         }
     }
-    if constexpr (LEARNED) {
+    if constexpr (LEARNED == 1) {
         // The learned sensor's per-cell decisions (1 = trouble, 0 = smooth,
         // 2 = unsure: the plain detector decides below) of the detector's
         // bounding box, written by the sensor pass for padded cells
@@ -972,6 +1277,22 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         }
     }
     __syncthreads();
+    if constexpr (LEARNED == 2) {
+        static_assert(sizeof(T) == 4, "the fused sensor runs in the FP32 form");
+        static_assert(sizeof(T) * (L::oHX - L::oGX) >= sizeof(float) * (4 * (BY + 10) * L::BOXW + 2 * L::NBOX),
+                      "fused sensor scratch exceeds the gradient and flux arrays");
+        static_assert(sizeof(T) * (L::oQc - L::oHX) >= 128 + 2 * (kSensorH * kSensorK + kSensorH * kSensorH) +
+                                                           sizeof(float) * (3 * kSensorH + 1),
+                      "fused sensor weights exceed the face-flux arrays");
+        unsigned char* const sTd = sPY + L::NPY;
+        if (!fused_sensor_decisions<BX, BY, NT, VISC>(P, reinterpret_cast<const float*>(sU), sTd,
+                                                      smem_raw + L::template raw_offset<T>(),
+                                                      smem_raw + sizeof(T) * L::oHX)) {
+            if (tid == 0) atomicOr(P.err, kErrTimeout);
+            return;
+        }
+        __syncthreads();
+    }
 
     // Phase 1: per-cell quantities, each computed once per tile.
     const T* const sV = CONS ? sQc : sU;  // the reconstructed variables
@@ -1235,25 +1556,25 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
 // allows (FP64: 2, 1 for MEG7-cons; FP32: 3, 2 viscous or MEG7-cons): small
 // source changes could otherwise push the allocation over the budget and cut
 // the resident warps.
-template <typename T, bool VISC, bool CONS>
+template <typename T, bool VISC, bool CONS, int LEARNED = 0>
 constexpr int stage_min_blocks()
 {
-    return sizeof(T) == 8 ? (CONS ? 1 : 2) : ((VISC || CONS) ? 2 : 3);
+    return sizeof(T) == 8 ? (CONS ? 1 : 2) : ((VISC || CONS || LEARNED == 2) ? 2 : 3);
 }
 
-template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED, int ORDER, bool CONS>
-__global__ void __launch_bounds__(NT, stage_min_blocks<T, VISC, CONS>()) stage_kernel(const StageParams P, const __grid_constant__ CUtensorMap tmap)
+template <typename T, int BX, int BY, int NT, bool VISC, int LEARNED, int ORDER, bool CONS>
+__global__ void __launch_bounds__(NT, stage_min_blocks<T, VISC, CONS, LEARNED>()) stage_kernel(const StageParams P, const __grid_constant__ CUtensorMap tmap)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     stage_tile<T, BX, BY, NT, VISC, LEARNED, ORDER, CONS, true>(P, blockIdx.x * BX, blockIdx.y * BY, smem_raw,
                                                                  &tmap);
 }
 
-template <typename T, int BX, int BY, int NT, bool VISC, bool LEARNED = false, int ORDER = 7, bool CONS = false>
+template <typename T, int BX, int BY, int NT, bool VISC, int LEARNED = 0, int ORDER = 7, bool CONS = false>
 cudaError_t launch_stage_t(const StageParams& p, cudaStream_t s)
 {
     using L = TileLayout<BX, BY, VISC, CONS>;
-    constexpr size_t smem = L::template total_bytes<T, NT, LEARNED>();
+    constexpr size_t smem = L::template total_bytes<T, NT, LEARNED != 0>();
     static PerDevice<int> configured;  // the shared-memory limit is raised once per device
     auto kern = stage_kernel<T, BX, BY, NT, VISC, LEARNED, ORDER, CONS>;
     int ok = 0;

@@ -50,10 +50,12 @@ def test_staging_wait_gives_up_and_context_recovers(env, precision):
     s.close()
 
 
-def test_tensor_core_wait_gives_up_and_context_recovers(env):
-    """The learned sensor's decision pass waits, bounded, for its tcgen05
-    MMAs; with GBR_OPT_STALL_TEST = 2 the first MMA batch is withheld, the
-    wait gives up, the CTA frees its tensor memory and the call reports
+@pytest.mark.parametrize("mode", [1, 2], ids=["decision_pass", "fused"])
+def test_tensor_core_wait_gives_up_and_context_recovers(env, mode):
+    """The learned sensor waits, bounded, for its tcgen05 MMAs (in the
+    decision pass, mode 1, or inside the stage kernel, mode 2); with
+    GBR_OPT_STALL_TEST = 2 the first MMA batch is withheld, the wait gives
+    up, the CTA frees its tensor memory and the call reports
     GBR_ERR_TIMEOUT; nothing faults and the context keeps working."""
     torch, O, gbr = env
     from paper_2305_00762_gb300 import sensor_train
@@ -62,6 +64,7 @@ def test_tensor_core_wait_gives_up_and_context_recovers(env):
     s = gbr.Solver.for_case(c, precision=32)
     s.set_state(c.Q)
     s.set_sensor(w)
+    gbr.gbr_set_option(s.ctx, gbr.GBR_OPT_SENSOR, mode)
     R0 = s.residual()
     gbr.gbr_set_option(s.ctx, gbr.GBR_OPT_STALL_TEST, 2)
     with pytest.raises(gbr.GbrError) as e:

@@ -228,3 +228,31 @@ def test_learned_flags_full_size_sampled(env):
     c = C.riemann_2d(4096)
     n = _check_learned_flags(env, c, c.Q, nface=3000, rng=np.random.default_rng(41))
     print("faces checked", n)
+
+
+@pytest.mark.parametrize("make", [lambda: C.riemann_2d(150, 130), lambda: C.viscous_shock_tube(90, 70)],
+                         ids=["riemann150x130", "vst90x70"])
+def test_fused_inference_equals_decision_pass(env, make):
+    """The network evaluated by a separate decision pass (GBR_OPT_SENSOR = 1)
+    and inside the FP32 stage kernel (GBR_OPT_SENSOR = 2) take the same
+    decisions from the same FP32 primitives, so 15 steps give bitwise equal
+    states (ragged tiles, inviscid and viscous)."""
+    torch, O, OS, gbr = env
+    import os
+    from paper_2305_00762_gb300 import sensor_train as T
+    if not os.path.exists(T.DEFAULT_WEIGHTS):
+        pytest.skip("no trained sensor weights committed yet")
+    w = T.load_weights()
+    c = make()
+    out = []
+    for mode in (1, 2):
+        s = gbr.Solver.for_case(c, precision=32)
+        s.set_state(c.Q)
+        s.set_sensor(w)
+        gbr.gbr_set_option(s.ctx, gbr.GBR_OPT_SENSOR, mode)
+        dt = 0.3 / s.max_wavespeed()
+        for _ in range(15):
+            s.step(dt)
+        out.append(s.get_state())
+        s.close()
+    assert np.array_equal(out[0], out[1])
