@@ -122,8 +122,8 @@ __global__ void wavespeed_kernel(const Grid g, const Physics ph, const double* _
                                  unsigned long long* lam)
 {
     const long long n = (long long)g.nx * g.ny;
-    const T gamma = T(ph.gamma), gm1 = T(ph.gamma - 1.0), mu = T(ph.mu);
-    const T idx_ = T(1.0 / ph.dx), idy = T(1.0 / ph.dy);
+    const T gamma = T(ph.gamma), gm1 = T(ph.gm1), mu = T(ph.mu);
+    const T idx_ = T(ph.inv_dx), idy = T(ph.inv_dy);
     double m = 0.0;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x) {

@@ -223,6 +223,7 @@ int gbr_batch_create(int n, const int* nx, const int* ny, const double* dx, cons
         c.ph.dx = dx[k];
         c.ph.dy = dy[k];
         c.ph.order = 7;
+        derive_physics(c.ph);
         for (int s = 0; s < 4; ++s) c.bc[s] = bc[4 * k + s];
         c.t_end = 1e300;
         c.ghost_begin = ghosts;

@@ -295,6 +295,7 @@ int gbr_create(int nx, int ny, double gamma, double mu, double Pr, const gbr_bc*
     c->ph.dx = bc->dx;
     c->ph.dy = bc->dy;
     c->ph.order = 7;
+    derive_physics(c->ph);
     c->bc[0] = bc->west;
     c->bc[1] = bc->east;
     c->bc[2] = bc->south;

@@ -69,7 +69,21 @@ struct Physics {
     int order;  // 7: MEG7 (alpha = 38/7, beta = 3/190); 4: the alpha = 4, beta = 0 member
     int cons;   // 0: MEG7-prim (reconstruct U); 1: MEG7-cons (reconstruct Q)
     int riemann;  // 0: HLLC; 1: shock-stable HLLC-LM (Fleischmann et al. 2020)
+    // Derived once on the host (derive_physics), so that no kernel thread
+    // spends FP64 divisions on them: gamma - 1, 1/(gamma - 1), the heat
+    // conduction coefficient mu / (Pr (gamma - 1)), 1/dx, 1/dy.
+    double gm1, igm1, kq, inv_dx, inv_dy;
 };
+
+// Fill the derived members of ph from gamma, mu, Pr, dx, dy.
+inline void derive_physics(Physics& ph)
+{
+    ph.gm1 = ph.gamma - 1.0;
+    ph.igm1 = 1.0 / (ph.gamma - 1.0);
+    ph.kq = ph.mu / (ph.Pr * (ph.gamma - 1.0));
+    ph.inv_dx = 1.0 / ph.dx;
+    ph.inv_dy = 1.0 / ph.dy;
+}
 
 struct SensorDev;
 

@@ -107,6 +107,7 @@ extern "C" int gbr_step_static(const double* Q_in, double* Q_out, int nx, int ny
     ph.dx = bc->dx;
     ph.dy = bc->dy;
     ph.order = 7;
+    derive_physics(ph);
 
     // The array keeps the previous call's contents: clear the error word.
     if ((rc = status_of(cudaMemsetAsync(ds, 0, sizeof(DevScalars), s))) != GBR_OK) return rc;

@@ -1185,12 +1185,12 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
 
     PhysT<T> ph;
     ph.gamma = T(P.ph.gamma);
-    ph.gm1 = T(P.ph.gamma - 1.0);
-    ph.igm1 = T(1.0 / (P.ph.gamma - 1.0));
+    ph.gm1 = T(P.ph.gm1);
+    ph.igm1 = T(P.ph.igm1);
     ph.mu = T(P.ph.mu);
-    ph.kq = T(P.ph.mu / (P.ph.Pr * (P.ph.gamma - 1.0)));
+    ph.kq = T(P.ph.kq);
     ph.lm = P.ph.riemann;
-    const T inv_dx = T(1.0 / P.ph.dx), inv_dy = T(1.0 / P.ph.dy);
+    const T inv_dx = T(P.ph.inv_dx), inv_dy = T(P.ph.inv_dy);
 
     // Phase 0: stage the tile + halo as primitive variables (Eq. pressure).
     // Region cell (rx, ry) is padded cell (tx0 + rx, ty0 + ry).
