@@ -42,7 +42,7 @@ void pack_sensor(const float* w, SensorDev* out)
 // decision region (origin = padded cell 3, extent (nx + 6) x (ny + 6): every
 // cell whose detector flag a stage tile reads).
 // ---------------------------------------------------------------------------
-constexpr int kTX = 32, kTY = 16, kH = 2, kRW = kTX + 2 * kH, kRH = kTY + 2 * kH;
+constexpr int kTX = 32, kTY = 24, kH = 2, kRW = kTX + 2 * kH, kRH = kTY + 2 * kH;
 constexpr int kDecOrigin = 3;
 
 struct SensorTileParams {
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(256) sensor_dataset_kernel(const SensorTilePar
 
 // ---------------------------------------------------------------------------
 // The network on the fifth-generation tensor cores (tcgen05): one CTA of G
-// warpgroups (128 G threads) per 32 x 16 tile, one thread per cell, 4/G
+// warpgroups (128 G threads) per 32 x 24 tile, one thread per cell, 6/G
 // rounds; warpgroup g's 128 cells of a round are the M = 128 rows of its own
 // MMAs, on its own 64 tensor-memory columns.
 // A thread writes its cell's 64 features (50 + zero padding, BF16 pairs) into
@@ -201,7 +201,7 @@ constexpr int kTcGroups = 2;  // warpgroups per CTA (measured fastest of 1, 2 an
 // shared memory per CTA for G warpgroups: more than 228 KB / (8/G + 1) with
 // the 1 KB the runtime reserves per CTA, so no more than 8/G CTAs fit
 template <int G>
-constexpr size_t tc_smem_bytes() { return G == 4 ? 80 * 1024 : (G == 2 ? 48 * 1024 : 28 * 1024); }
+constexpr size_t tc_smem_bytes() { return G == 4 ? 80 * 1024 : (G == 2 ? 56 * 1024 : 28 * 1024); }
 
 // Tensor copy of a tile's FP64 region: x from the region's first column
 // rounded down to even (16-byte aligned), 2 columns wider than the region.
@@ -285,7 +285,7 @@ __device__ void tc_teardown(uint32_t tm)
     }
 }
 
-// One 32 x 16 tile whose region and scales are staged: 4/G rounds of both
+// One 32 x 24 tile whose region and scales are staged: 6/G rounds of both
 // layers. `phase` is the mbarrier's next parity (two completions per round).
 // False if a bounded wait gave up (uniform over the CTA; the remaining rounds
 // are skipped).
