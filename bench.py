@@ -633,7 +633,8 @@ def run_slabs(args, torch, gbr, cases, dist, rank, ws, local):
     pre_precision = args.prelude_precision or (32 if args.n > 2048 else 64)
     q_start, t_start, pre_steps = window_state(torch, gbr, case, st, args.t_window, pre_precision,
                                                args.state_cache)
-    sl = S.DistSlab(case, rank, ws, precision=64)
+    transport = "device" if dist.get_backend() == "nccl" else "host"
+    sl = S.DistSlab(case, rank, ws, transport=transport, precision=64)
     q_local = q_start[:, sl.i0:sl.i1, :].contiguous()
     del q_start
     sl.set_state(q_local)
@@ -682,8 +683,9 @@ def run_slabs(args, torch, gbr, cases, dist, rank, ws, local):
                        "cfl": CFL, "bc": "transmissive", "l2": "flushed between steps (256 MB write)",
                        "window_t_start": round(t_start, 6), "prelude_steps": pre_steps,
                        "prelude_precision": f"fp{pre_precision}", "parallelism": f"y-slabs x{ws}",
-                       "halo": "6 rows x 4 fields per neighbour per stage (NCCL send/recv)",
-                       "wavespeed": "max all-reduce per step (NCCL)"},
+                       "halo": f"6 rows x 4 fields per neighbour per stage ({dist.get_backend()} send/recv, "
+                               f"{transport} buffers)",
+                       "wavespeed": f"max all-reduce per step ({dist.get_backend()})"},
             "e2e": {"value": e2e, "unit": METRIC, "h2d_bytes_per_step": slab_bytes * ws,
                     "d2h_bytes_per_step": slab_bytes * ws},
             "gpu_launches": int(sum(n for _, n in tm.values())),

@@ -169,14 +169,20 @@ class _DeviceWord:
 class DistSlab:
     """Slab `rank` of a grid split over the ranks of a torch.distributed
     group (one slab per rank and GPU). The halo rows travel as contiguous
-    [4][6][nx] device buffers by batched point-to-point messages; the
-    wavespeed words by a MAX all-reduce of their int64 view (the bits of
-    non-negative doubles order as the values). The context works on torch's
-    current stream, which the collectives follow."""
+    [4][6][nx] buffers by batched point-to-point messages, the wavespeed
+    words by a MAX all-reduce of their int64 view (the bits of non-negative
+    doubles order as the values). transport "device" (NCCL): the buffers
+    are device memory and the context works on torch's current stream,
+    which the collectives follow. transport "host" (any backend, e.g. gloo):
+    the buffers are pinned host memory filled and drained by synchronous
+    copies, and the wavespeed word goes through the host."""
 
-    def __init__(self, case, rank, world, group=None, **solver_kw):
+    def __init__(self, case, rank, world, group=None, transport="device", **solver_kw):
         import torch
+        if transport not in ("device", "host"):
+            raise ValueError(f"unknown transport {transport!r}")
         self.case, self.rank, self.world, self.group = case, rank, world, group
+        self.transport = transport
         self.rows = slab_rows(case.ny, world)
         self.periodic = int(case.bc[2]) == gbr.GBR_BC_PERIODIC
         i0, i1 = self.rows[rank]
@@ -186,8 +192,12 @@ class DistSlab:
                                  slab_bc(case.bc, rank, world), **solver_kw)
         self.plan = message_plan(rank, world, self.periodic)
         shape = (4, GHOST, case.nx)
-        self.send = {side: torch.empty(shape, dtype=torch.float64, device="cuda") for side in (SOUTH, NORTH)}
-        self.recv = {side: torch.empty(shape, dtype=torch.float64, device="cuda") for side in (SOUTH, NORTH)}
+        if transport == "device":
+            alloc = lambda: torch.empty(shape, dtype=torch.float64, device="cuda")
+        else:
+            alloc = lambda: torch.empty(shape, dtype=torch.float64).pin_memory()
+        self.send = {side: alloc() for side in (SOUTH, NORTH)}
+        self.recv = {side: alloc() for side in (SOUTH, NORTH)}
 
     def set_state(self, Q_local):
         self.solver.set_state(Q_local)
@@ -197,7 +207,13 @@ class DistSlab:
         import torch
         import torch.distributed as dist
         w = torch.as_tensor(_DeviceWord(self.solver.lambda_word()), device="cuda")
-        dist.all_reduce(w, op=dist.ReduceOp.MAX, group=self.group)
+        if self.transport == "device":
+            dist.all_reduce(w, op=dist.ReduceOp.MAX, group=self.group)
+            return
+        h = w.cpu()  # synchronising copy (stream-ordered after the step)
+        dist.all_reduce(h, op=dist.ReduceOp.MAX, group=self.group)
+        w.copy_(h)
+        torch.cuda.current_stream().synchronize()
 
     def _exchange(self):
         for op, _, side in self.plan:
@@ -219,6 +235,13 @@ class DistSlab:
 
     def step_cfl(self, cfl, dt_max=1e300):
         self._step(0.0, float(cfl), float(dt_max))
+
+    def get_state(self):
+        """This slab's rows of the state ([4][i1 - i0][nx], host)."""
+        return self.solver.get_state()
+
+    def time(self):
+        return self.solver.time()
 
     def close(self):
         self.solver.close()

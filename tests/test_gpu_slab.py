@@ -72,3 +72,105 @@ def test_stage_order_and_halo_arguments_checked(env):
     s0.step_stage(2)
     s0.step(1e-4)
     slabs.close()
+
+
+def _dist_rank(rank, ws, port, name, steps, out):
+    """One rank of a DistSlab run: all ranks share GPU 0 and talk over gloo
+    (halo rows and the wavespeed through pinned host buffers); no kernel
+    waits on another process."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import torch
+    import torch.distributed as dist
+    from paper_2305_00762_gb300 import gbr
+    from paper_2305_00762_gb300 import slab as S
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    torch.cuda.set_device(0)
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    gbr.load()
+    c = dict(DIST_CASES)[name]()
+    sl = S.DistSlab(c, rank, ws, transport="host")
+    sl.set_state(np.ascontiguousarray(c.Q[:, sl.i0:sl.i1, :]))
+    for _ in range(steps):
+        sl.step_cfl(0.5)
+    out[rank] = (sl.get_state(), sl.time())
+    sl.close()
+    dist.destroy_process_group()
+
+
+DIST_CASES = [("riemann96x70", lambda: C.riemann_2d(96, 70)),
+              ("vortex48x50", lambda: C.isentropic_vortex(48, 50))]
+
+
+@pytest.mark.parametrize("name,ws", [("riemann96x70", 2), ("riemann96x70", 3), ("vortex48x50", 2)])
+def test_dist_slabs_reproduce_single_grid(env, name, ws):
+    """DistSlab, the one-slab-per-rank driver the benchmark runs under
+    torchrun, here as ws processes sharing one GPU (gloo, host transport):
+    five CFL steps with halo messages before every stage and the wavespeed
+    max all-reduced after every step give the single-grid state bit for bit
+    (periodic in y: the first and last slabs exchange across the seam)."""
+    torch, gbr, S = env
+    import socket
+    import torch.multiprocessing as mp
+    c = dict(DIST_CASES)[name]()
+    single = gbr.Solver.for_case(c)
+    single.set_state(c.Q)
+    for _ in range(5):
+        single.step_cfl(0.5)
+    ref, t_ref = single.get_state(), single.time()
+    single.close()
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    with mp.get_context("spawn").Manager() as m:  # no fork after CUDA or threads start
+        out = m.dict()
+        mp.spawn(_dist_rank, args=(ws, port, name, 5, out), nprocs=ws, join=True)
+        parts = [out[r] for r in range(ws)]
+    assert np.array_equal(np.concatenate([p[0] for p in parts], axis=1), ref)
+    assert all(p[1] == t_ref for p in parts)
+
+
+def _bench_rank(rank, ws, port, out):
+    import contextlib
+    import io
+    import os
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import torch
+    import torch.distributed as dist
+    import bench
+    from paper_2305_00762_gb300 import cases, gbr
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    torch.cuda.set_device(0)
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    gbr.load()
+    sys.argv = ["bench.py", "--gpus", str(ws), "--n", "256", "--steps", "2", "--warmup", "1", "--t-window", "0.02"]
+    args = bench.parse()
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.run_slabs(args, torch, gbr, cases, dist, rank, ws, 0)
+    out[rank] = buf.getvalue()
+
+
+def test_bench_slab_mode_runs(env):
+    """The benchmark's multi-GPU mode (the grid split into y-slabs, one per
+    rank) end to end, as two processes sharing one GPU over gloo: a
+    functional check of the JSON line, not a measurement."""
+    torch, gbr, S = env
+    import json
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    with mp.get_context("spawn").Manager() as m:  # no fork after CUDA or threads start
+        out = m.dict()
+        mp.spawn(_bench_rank, args=(2, port, out), nprocs=2, join=True)
+        res = dict(out)
+    assert res[1] == ""                      # only rank 0 prints
+    line = json.loads(res[0].strip().splitlines()[-1])
+    assert line["n_gpus"] == 2 and line["scaling"] == "strong" and line["status"] == "ok"
+    assert line["value"] > 0 and line["e2e"]["value"] > 0 and line["gpu_launches"] > 0
+    assert line["config"]["parallelism"] == "y-slabs x2"

@@ -120,7 +120,7 @@ def _rank(rank, ws, port, name, out):
 def test_halo_exchange_reproduces_single_grid_residual(oracle_mod, name, ws):
     c = _make(name)
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork after CUDA or threads start
         out = m.dict()
         mp.spawn(_rank, args=(ws, port, name, out), nprocs=ws, join=True)
         parts = [out[r] for r in range(ws)]
