@@ -106,6 +106,9 @@ template <typename T>
 __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 template <typename T>
 __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+// FP32: one min / max instruction (the same value for operands that are not NaN)
+__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double trsqrt(double x) { return rsqrt(x); }
@@ -132,11 +135,13 @@ __device__ __forceinline__ long long ordkey(double x)
 __device__ __forceinline__ double tmin(double a, double b) { return ordkey(a) < ordkey(b) ? a : b; }
 __device__ __forceinline__ double tmax(double a, double b) { return ordkey(a) > ordkey(b) ? a : b; }
 
-// Eq. alpha: minmod(a, b) = 1/2 (sign a + sign b) min(|a|, |b|).
-template <typename T>
-__device__ __forceinline__ T minmod(T a, T b)
+// Eq. alpha: minmod(a, b) = 1/2 (sign a + sign b) min(|a|, |b|): the operand
+// of smaller magnitude when the signs agree, else 0 (the sign test on the
+// bits; only the sign of a zero result may differ from the formula's).
+__device__ __forceinline__ float minmod(float a, float b)
 {
-    return (a > T(0) && b > T(0)) ? tmin(a, b) : ((a < T(0) && b < T(0)) ? tmax(a, b) : T(0));
+    const float r = fabsf(a) <= fabsf(b) ? a : b;
+    return (__float_as_int(a) ^ __float_as_int(b)) < 0 ? 0.f : r;
 }
 __device__ __forceinline__ double minmod(double a, double b)
 {
@@ -153,19 +158,21 @@ __device__ __forceinline__ bool mp_accept(T x) { return x <= T(1e-40); }
 __device__ __forceinline__ bool mp_accept(double x) { return ordkey(x) <= ordkey(1e-40); }
 
 // Phi^min and Phi^max of Eq. mp-procedure from Phi_j, Phi_{j+1}, Phi^MD,
-// Phi^UL and Phi^LC.
+// Phi^UL and Phi^LC: max(min(Phi_j, Phi_{j+1}, MD), min(Phi_j, UL, LC)) is
+// min(Phi_j, max(min(Phi_{j+1}, MD), min(UL, LC))) (min distributes over max),
+// and likewise for Phi^max: four comparisons each instead of five.
 template <typename T>
 __device__ __forceinline__ void mp_bounds(T p2, T p3, T md, T ul, T lc, T& pmin, T& pmax)
 {
-    pmin = tmax(tmin(p2, tmin(p3, md)), tmin(p2, tmin(ul, lc)));
-    pmax = tmin(tmax(p2, tmax(p3, md)), tmax(p2, tmax(ul, lc)));
+    pmin = tmin(p2, tmax(tmin(p3, md), tmin(ul, lc)));
+    pmax = tmax(p2, tmin(tmax(p3, md), tmax(ul, lc)));
 }
 __device__ __forceinline__ void mp_bounds(double p2, double p3, double md, double ul, double lc, double& pmin,
                                           double& pmax)
 {
     const long long k2 = ordkey(p2), k3 = ordkey(p3), km = ordkey(md), ku = ordkey(ul), kl = ordkey(lc);
-    const long long kmin = max(min(k2, min(k3, km)), min(k2, min(ku, kl)));
-    const long long kmax = min(max(k2, max(k3, km)), max(k2, max(ku, kl)));
+    const long long kmin = min(k2, max(min(k3, km), min(ku, kl)));
+    const long long kmax = max(k2, min(max(k3, km), max(ku, kl)));
     pmin = __longlong_as_double(kmin ^ ((kmin >> 63) & 0x7FFFFFFFFFFFFFFFLL));
     pmax = __longlong_as_double(kmax ^ ((kmax >> 63) & 0x7FFFFFFFFFFFFFFFLL));
 }

@@ -234,9 +234,12 @@ def test_learned_flags_full_size_sampled(env):
                          ids=["riemann150x130", "vst90x70"])
 def test_fused_inference_equals_decision_pass(env, make):
     """The network evaluated by a separate decision pass (GBR_OPT_SENSOR = 1)
-    and inside the FP32 stage kernel (GBR_OPT_SENSOR = 2) take the same
-    decisions from the same FP32 primitives, so 15 steps give bitwise equal
-    states (ragged tiles, inviscid and viscous)."""
+    and inside the FP32 stage kernel (GBR_OPT_SENSOR = 2) takes the same
+    decisions from the same FP32 primitives: on identical states (along a
+    15-step run, ragged tiles, inviscid and viscous) the recorded face flags
+    are bitwise equal. The two forms are two kernel instances whose
+    remaining FP32 multiply-adds the compiler may contract differently, so
+    their residuals and their 15-step states agree to FP32 rounding."""
     torch, O, OS, gbr = env
     import os
     from paper_2305_00762_gb300 import sensor_train as T
@@ -244,15 +247,34 @@ def test_fused_inference_equals_decision_pass(env, make):
         pytest.skip("no trained sensor weights committed yet")
     w = T.load_weights()
     c = make()
-    out = []
+    ss = []
     for mode in (1, 2):
         s = gbr.Solver.for_case(c, precision=32)
         s.set_state(c.Q)
         s.set_sensor(w)
         gbr.gbr_set_option(s.ctx, gbr.GBR_OPT_SENSOR, mode)
-        dt = 0.3 / s.max_wavespeed()
-        for _ in range(15):
-            s.step(dt)
-        out.append(s.get_state())
+        ss.append(s)
+    probe = gbr.Solver.for_case(c, precision=32)
+    probe.set_sensor(w)
+    probe.record_flags(True)
+    dt = 0.3 / ss[0].max_wavespeed()
+    scale = float(np.abs(c.Q).max())
+    for step in range(16):
+        Q = [s.get_state() for s in ss]
+        assert np.allclose(Q[0], Q[1], rtol=0.0, atol=2e-5 * scale), step
+        if step % 5 == 0:
+            got = []
+            for mode in (1, 2):
+                gbr.gbr_set_option(probe.ctx, gbr.GBR_OPT_SENSOR, mode)
+                probe.set_state(Q[0])
+                R = probe.residual()
+                got.append((R, *probe.flags()))
+            (R1, x1, y1), (R2, x2, y2) = got
+            assert np.array_equal(x1, x2) and np.array_equal(y1, y2), step
+            assert (x1 != 1).any() or (y1 != 1).any()  # some faces are not smooth
+            assert np.allclose(R1, R2, rtol=0.0, atol=1e-5 * float(np.abs(R1).max())), step
+        if step < 15:
+            for s in ss:
+                s.step(dt)
+    for s in ss + [probe]:
         s.close()
-    assert np.array_equal(out[0], out[1])
