@@ -157,24 +157,28 @@ template <typename T>
 __device__ __forceinline__ bool mp_accept(T x) { return x <= T(1e-40); }
 __device__ __forceinline__ bool mp_accept(double x) { return ordkey(x) <= ordkey(1e-40); }
 
-// Phi^min and Phi^max of Eq. mp-procedure from Phi_j, Phi_{j+1}, Phi^MD,
-// Phi^UL and Phi^LC: max(min(Phi_j, Phi_{j+1}, MD), min(Phi_j, UL, LC)) is
-// min(Phi_j, max(min(Phi_{j+1}, MD), min(UL, LC))) (min distributes over max),
-// and likewise for Phi^max: four comparisons each instead of five.
+// The last step of Eq. mp-procedure from Phi_j, Phi_{j+1}, Phi^MD, Phi^UL,
+// Phi^LC and the GRB value pl. Phi^min = max(min(Phi_j, Phi_{j+1}, MD),
+// min(Phi_j, UL, LC)) is min(Phi_j, max(min(Phi_{j+1}, MD), min(UL, LC)))
+// (min distributes over max), and likewise Phi^max: four comparisons each
+// instead of five. Phi^min <= Phi_j <= Phi^max, so pl + minmod(Phi^min - pl,
+// Phi^max - pl) is the median of pl, Phi^min and Phi^max: pl clamped to
+// [Phi^min, Phi^max], taken without arithmetic (the formula's value up to
+// the rounding of (Phi^min - pl) + pl).
 template <typename T>
-__device__ __forceinline__ void mp_bounds(T p2, T p3, T md, T ul, T lc, T& pmin, T& pmax)
+__device__ __forceinline__ T mp_clamp(T p2, T p3, T md, T ul, T lc, T pl)
 {
-    pmin = tmin(p2, tmax(tmin(p3, md), tmin(ul, lc)));
-    pmax = tmax(p2, tmin(tmax(p3, md), tmax(ul, lc)));
+    const T pmin = tmin(p2, tmax(tmin(p3, md), tmin(ul, lc)));
+    const T pmax = tmax(p2, tmin(tmax(p3, md), tmax(ul, lc)));
+    return tmin(tmax(pl, pmin), pmax);
 }
-__device__ __forceinline__ void mp_bounds(double p2, double p3, double md, double ul, double lc, double& pmin,
-                                          double& pmax)
+__device__ __forceinline__ double mp_clamp(double p2, double p3, double md, double ul, double lc, double pl)
 {
     const long long k2 = ordkey(p2), k3 = ordkey(p3), km = ordkey(md), ku = ordkey(ul), kl = ordkey(lc);
     const long long kmin = min(k2, max(min(k3, km), min(ku, kl)));
     const long long kmax = max(k2, min(max(k3, km), max(ku, kl)));
-    pmin = __longlong_as_double(kmin ^ ((kmin >> 63) & 0x7FFFFFFFFFFFFFFFLL));
-    pmax = __longlong_as_double(kmax ^ ((kmax >> 63) & 0x7FFFFFFFFFFFFFFFLL));
+    const long long k = min(max(ordkey(pl), kmin), kmax);
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7FFFFFFFFFFFFFFFLL));
 }
 
 // Explicitly rounded products and fused multiply-adds. Per-cell work that is
@@ -366,9 +370,7 @@ __device__ __forceinline__ T mp_limit(const T* p, const T* d, T pl, T s1, T dd, 
     const T Dm1 = p[1] - p[2];
     const T ul = rfma(T(-7), Dm1, p[2]);
     const T lc = rfma(T(4.0 / 3.0), minmod(dj, dm1), rfma(T(-0.5), Dm1, p[2]));
-    T pmin, pmax;
-    mp_bounds(p[2], p[3], md, ul, lc, pmin, pmax);
-    return pl + minmod(pmin - pl, pmax - pl);
+    return mp_clamp(p[2], p[3], md, ul, lc, pl);
 }
 
 // Position of the n-th (0-based) set bit of m; m has more than n set bits.
@@ -703,18 +705,22 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
     // expanded so that the only divisions are 1/((S_L - S*)(S_R - S*)), S* and
     // the Roe weight.
     {
-        const T rsL = trsqrt(rL), rsR = trsqrt(rR);  // 1/sqrt(rho)
-        const T sL = rL * rsL, sR = rR * rsR;        // sqrt(rho)
-        const T irL = rsL * rsL, irR = rsR * rsR;    // 1/rho
-        // c = c^2 / sqrt(c^2): a reciprocal square root instead of a square root
-        const T c2L = P.gamma * pL * irL, c2R = P.gamma * pR * irR;
-        const T icL = trsqrt(c2L), icR = trsqrt(c2R);
-        const T cL = c2L * icL, cR = c2R * icR;
+        // Per side one reciprocal square root y = 1/sqrt(gamma p rho):
+        // c = gamma p y, 1/c = rho y, 1/rho = c y.
+        const T gpL = P.gamma * pL, gpR = P.gamma * pR;
+        const T yL = trsqrt(gpL * rL), yR = trsqrt(gpR * rR);
+        const T cL = gpL * yL, cR = gpR * yR;
+        const T icL = rL * yL, icR = rR * yR;
+        const T irL = cL * yL, irR = cR * yR;
         const T HL = (EL + pL) * irL, HR = (ER + pR) * irR;
-        const T isum = T(1) / (sL + sR);
-        const T ut = (sL * unL + sR * unR) * isum;
-        const T vt = (sL * utL + sR * utR) * isum;
-        const T Ht = (sL * HL + sR * HR) * isum;
+        // Roe weights sqrt(rho_L) / (sqrt(rho_L) + sqrt(rho_R)) = 1 / (1 + q)
+        // and q / (1 + q), q = sqrt(rho_R / rho_L)
+        const T xq = rR * irL;
+        const T q = xq * trsqrt(xq);
+        const T oL = T(1) / (T(1) + q), oR = q * oL;
+        const T ut = oL * unL + oR * unR;
+        const T vt = oL * utL + oR * utR;
+        const T Ht = oL * HL + oR * HR;
         const T c2t = P.gm1 * (Ht - T(0.5) * (ut * ut + vt * vt));
         const T ct = c2t * trsqrt(c2t);
         const T SL = tmin(unL - cL, ut - ct);
