@@ -296,7 +296,7 @@ __device__ __forceinline__ double detector_psi(const double* r, int st)
 // and Eq. fourth with its mirror.
 template <typename T>
 struct GrbCoef {
-    T w1, w2, w3;          // w0 = 420 for both orders
+    T w1, w2, w3;          // w0 = 420 for both orders; the GRB sum takes wk / 840
     T c1, c2, c3, c4, c5;  // pairs (j, j+1), (j-1, j+2), ..., (j-4, j+5)
     T inv_den;
 };
@@ -340,7 +340,9 @@ __device__ __forceinline__ GrbCoef<T> grb_coef(int order)
 template <typename T>
 __device__ __forceinline__ T grb_mp(T pj, T Dm1, T Dp1, T s1, T S2, T dj, T dd, bool& need, const GrbCoef<T>& C)
 {
-    const T delta = (T(420) * dj + C.w1 * dd + C.w2 * s1 + C.w3 * S2) * T(1.0 / 840.0);
+    // the weights divided by 840 (420/840 = 1/2 exactly): one product, three FMAs
+    T delta = rfma(C.w2 * T(1.0 / 840.0), s1, rfma(C.w1 * T(1.0 / 840.0), dd, rmul(T(0.5), dj)));
+    if (C.w3 != T(0)) delta = rfma(C.w3 * T(1.0 / 840.0), S2, delta);
     const T m = minmod(Dp1, T(-7) * Dm1);
     need = !mp_accept(delta * (delta - m));
     return pj + delta;
@@ -355,21 +357,22 @@ __device__ __forceinline__ T grb_mp(T pj, T Dm1, T Dp1, T s1, T S2, T dj, T dd, 
 // The curvature d_{j+1} is the other side's d_j (the right value at the same
 // face is centred on cell j+1, mirrored, and the curvature is unchanged by
 // the mirror): it comes from that side's sums s1o, ddo.
+// The curvatures are carried as 2 d (one operation fewer each); doubling is
+// exact, and minmod(2a, 2b) = 2 minmod(a, b), so Phi^MD and Phi^LC, with the
+// halved factors 1/2 and 2/3, round exactly as from d itself.
 template <typename T>
 __device__ __forceinline__ T mp_limit(const T* p, const T* d, T pl, T s1, T dd, T s1o, T ddo)
 {
-    const T dm1 = rfma(T(2), rfma(T(-2), p[1], p[2]) + p[0], rmul(T(-0.5), d[2] - d[0]));
+    const T dm1 = rfma(T(4), rfma(T(-2), p[1], p[2]) + p[0], d[0] - d[2]);
     // (FP64 takes d_j and d_{j+1} from the sums, which saves FP64
     // operations; FP32, bound by its instruction count rather than by one
     // pipe, recomputes them and keeps fewer values live)
-    const T dj = sizeof(T) == 8 ? rfma(T(2), s1, rmul(T(0.5), dd))
-                                : rfma(T(2), rfma(T(-2), p[2], p[3]) + p[1], rmul(T(-0.5), d[3] - d[1]));
-    const T dp1 = sizeof(T) == 8 ? rfma(T(2), s1o, rmul(T(0.5), ddo))
-                                 : rfma(T(2), rfma(T(-2), p[3], p[4]) + p[2], rmul(T(-0.5), d[4] - d[2]));
-    const T md = rmul(T(0.5), (p[2] + p[3]) - minmod(dj, dp1));
+    const T dj = sizeof(T) == 8 ? rfma(T(4), s1, dd) : rfma(T(4), rfma(T(-2), p[2], p[3]) + p[1], d[1] - d[3]);
+    const T dp1 = sizeof(T) == 8 ? rfma(T(4), s1o, ddo) : rfma(T(4), rfma(T(-2), p[3], p[4]) + p[2], d[2] - d[4]);
+    const T md = rmul(T(0.5), rfma(T(-0.5), minmod(dj, dp1), p[2] + p[3]));
     const T Dm1 = p[1] - p[2];
     const T ul = rfma(T(-7), Dm1, p[2]);
-    const T lc = rfma(T(4.0 / 3.0), minmod(dj, dm1), rfma(T(-0.5), Dm1, p[2]));
+    const T lc = rfma(T(2.0 / 3.0), minmod(dj, dm1), rfma(T(-0.5), Dm1, p[2]));
     return mp_clamp(p[2], p[3], md, ul, lc, pl);
 }
 
@@ -414,8 +417,8 @@ __device__ __forceinline__ void meg7_pair(const GrbCoef<T>& C, const T (&w)[6], 
     const T aL = w[1] - w[2], aR = w[4] - w[3];
     const T s1L = aL + b, s1R = aR - b;          // second differences at j, j+1
     const T ddL = e[1] - e[3], ddR = e[2] - e[4];  // (mirrored for the right side)
-    vl = grb_mp(w[2], aL, b, s1L, (w[0] - w[2]) + (w[4] - w[2]), e[2], ddL, needL, C);
-    vr = grb_mp(w[3], aR, -b, s1R, (w[5] - w[3]) + (w[1] - w[3]), -e[3], ddR, needR, C);
+    vl = grb_mp(w[2], aL, b, s1L, rfma(T(-2), w[2], w[0] + w[4]), e[2], ddL, needL, C);
+    vr = grb_mp(w[3], aR, -b, s1R, rfma(T(-2), w[3], w[5] + w[1]), -e[3], ddR, needR, C);
     if constexpr (sizeof(T) == 8) {
         const unsigned mL = __ballot_sync(0xffffffffu, needL), mR = __ballot_sync(0xffffffffu, needR);
         const int nL = __popc(mL), nR = __popc(mR);
@@ -462,9 +465,12 @@ __device__ __forceinline__ void meg7_pair(const GrbCoef<T>& C, const T (&w)[6], 
 template <typename T>
 __device__ __forceinline__ T recon_mean(const T* f, int s, const GrbCoef<T>& C)
 {
-    return (C.c1 * (f[0] + f[s]) + C.c2 * (f[-s] + f[2 * s]) + C.c3 * (f[-2 * s] + f[3 * s]) +
-            C.c4 * (f[-3 * s] + f[4 * s]) + C.c5 * (f[-4 * s] + f[5 * s])) *
-           C.inv_den;
+    // the weights divided by den (compile-time products): one product, four FMAs
+    T acc = rmul(C.c1 * C.inv_den, f[0] + f[s]);
+    acc = rfma(C.c2 * C.inv_den, f[-s] + f[2 * s], acc);
+    acc = rfma(C.c3 * C.inv_den, f[-2 * s] + f[3 * s], acc);
+    acc = rfma(C.c4 * C.inv_den, f[-3 * s] + f[4 * s], acc);
+    return rfma(C.c5 * C.inv_den, f[-4 * s] + f[5 * s], acc);
 }
 
 template <typename T>
