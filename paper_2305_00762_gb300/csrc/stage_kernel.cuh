@@ -23,7 +23,7 @@
 
 namespace gbr {
 
-template <int BX, int BY, bool VISC, bool CONS = false>
+template <int BX, int BY, bool VISC, bool CONS = false, bool FLUX0 = false>
 struct TileLayout {
     static constexpr int V = VISC ? 1 : 0;
     static constexpr int RW = BX + 12, RH = BY + 12;  // staged region (tile + halo)
@@ -68,12 +68,16 @@ struct TileLayout {
 
     static constexpr int NF = NHX + NHY;  // faces of the tile
 
+    // FLUX0: the cell fluxes are written in phase 0, from the staged
+    // conservative values; their arrays then come before the gradients, so
+    // that the TMA landing area (at the gradients, over the face fluxes) does
+    // not overlap them.
     static constexpr int oU = 0;
-    static constexpr int oGX = oU + 4 * NU;
+    static constexpr int oGX = FLUX0 ? oU + 4 * NU + 4 * (NFX + NFY) : oU + 4 * NU;
     static constexpr int oGY = oGX + 4 * NGX;
-    static constexpr int oFX = oGY + 4 * NGY;
+    static constexpr int oFX = FLUX0 ? oU + 4 * NU : oGY + 4 * NGY;
     static constexpr int oFY = oFX + 4 * NFX;
-    static constexpr int oHX = oFY + 4 * NFY;
+    static constexpr int oHX = FLUX0 ? oGY + 4 * NGY : oFY + 4 * NFY;
     static constexpr int oHY = oHX + 4 * NHX;
     static constexpr int oQc = oHY + 4 * NHY;         // conservative values (MEG7-cons)
     static constexpr int oEnd = oQc + (CONS ? 4 * NU : 0);
@@ -93,8 +97,9 @@ struct TileLayout {
     }
 
     // TMA staging: the FP64 conservative tile + halo lands as [4][RH][RW]
-    // doubles on top of the per-cell and face arrays (first written after
-    // phase 0, and below the MEG7-cons copy that phase 0 fills).
+    // doubles on top of the gradient, face-flux and (without FLUX0)
+    // cell-flux arrays, all first written after phase 0, and below the
+    // MEG7-cons copy that phase 0 fills.
     static constexpr size_t kRawBytes = sizeof(double) * 4 * (size_t)NU;
     template <typename T>
     static constexpr size_t raw_offset() { return sizeof(T) * (size_t)oGX; }
@@ -1183,7 +1188,10 @@ template <typename T, int BX, int BY, int NT, bool VISC, int LEARNED = 0, int OR
 __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, const int ty0,
                                            unsigned char* smem_raw, const CUtensorMap* tmap = nullptr)
 {
-    using L = TileLayout<BX, BY, VISC, CONS>;
+    // FP64: the cell fluxes come from the staged conservative values in
+    // phase 0 (FLUX0)
+    constexpr bool FLUX0 = sizeof(T) == 8;
+    using L = TileLayout<BX, BY, VISC, CONS, FLUX0>;
     using X = typename L::template Cross<LEARNED>;  // the staged cells
     T* const sm = reinterpret_cast<T*>(smem_raw);
     T* const sU = sm + L::oU;
@@ -1220,6 +1228,25 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         sU[NU + idx] = u;
         sU[2 * NU + idx] = v;
         sU[3 * NU + idx] = p;
+        if constexpr (FLUX0) {
+            // cell fluxes F^c = (rho u, rho u u + p, rho u v, u (E + p)) and
+            // G^c (Sec. 1) with rho u, rho v and E taken from the state
+            const int ry = idx / RW, rx = idx - ry * RW;
+            if (ry >= 6 && ry < 6 + BY && rx >= 1 && rx < BX + 11) {
+                const int f = (ry - 6) * L::FXW + (rx - 1);
+                sFX[f] = q1;
+                sFX[L::NFX + f] = rfma(T(q1), u, p);
+                sFX[2 * L::NFX + f] = T(q1) * v;
+                sFX[3 * L::NFX + f] = u * (T(q3) + p);
+            }
+            if (ry >= 1 && ry < BY + 11 && rx >= 6 && rx < BX + 6) {
+                const int f = (ry - 1) * BX + (rx - 6);
+                sFY[f] = q2;
+                sFY[L::NFY + f] = T(q2) * u;
+                sFY[2 * L::NFY + f] = rfma(T(q2), v, p);
+                sFY[3 * L::NFY + f] = v * (T(q3) + p);
+            }
+        }
         if constexpr (CONS) {
             sQc[idx] = r;
             sQc[NU + idx] = from_f64<T>(q1);
@@ -1337,7 +1364,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
             sPY[idx] = trouble_cell(sU + (a + 3) * RW + (b + 6), RW) ? 1 : 0;
         }
     }
-    for (int idx = tid; idx < L::NFX; idx += NT) {  // cell x-fluxes F^c (Sec. 1)
+    for (int idx = tid; idx < (FLUX0 ? 0 : L::NFX); idx += NT) {  // cell x-fluxes F^c (Sec. 1)
         const int a = idx / L::FXW, b = idx - a * L::FXW;
         const int c = (a + 6) * RW + (b + 1);
         const T r = sU[c], u = sU[NU + c], v = sU[2 * NU + c], p = sU[3 * NU + c];
@@ -1348,7 +1375,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& P, const int tx0, 
         sFX[2 * L::NFX + idx] = ru * v;
         sFX[3 * L::NFX + idx] = u * (E + p);
     }
-    for (int idx = tid; idx < L::NFY; idx += NT) {  // cell y-fluxes G^c
+    for (int idx = tid; idx < (FLUX0 ? 0 : L::NFY); idx += NT) {  // cell y-fluxes G^c
         const int a = idx / BX, b = idx - a * BX;
         const int c = (a + 1) * RW + (b + 6);
         const T r = sU[c], u = sU[NU + c], v = sU[2 * NU + c], p = sU[3 * NU + c];
@@ -1592,7 +1619,7 @@ __global__ void __launch_bounds__(NT, stage_min_blocks<T, VISC, CONS, LEARNED>()
 template <typename T, int BX, int BY, int NT, bool VISC, int LEARNED = 0, int ORDER = 7, bool CONS = false>
 cudaError_t launch_stage_t(const StageParams& p, cudaStream_t s)
 {
-    using L = TileLayout<BX, BY, VISC, CONS>;
+    using L = TileLayout<BX, BY, VISC, CONS, sizeof(T) == 8>;
     constexpr size_t smem = L::template total_bytes<T, NT, LEARNED != 0>();
     static PerDevice<int> configured;  // the shared-memory limit is raised once per device
     auto kern = stage_kernel<T, BX, BY, NT, VISC, LEARNED, ORDER, CONS>;
