@@ -62,6 +62,8 @@ def parse():
                     help="only the FP64 steps of the headline workload, bracketed by cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off); prints a short JSON line")
     ap.add_argument("--profile-precision", type=int, default=64, choices=[32, 64])
+    ap.add_argument("--profile-sensor", type=int, default=0, choices=[0, 1, 2],
+                    help="with --profile-only: the learned sensor as a decision pass (1) or fused (2)")
     ap.add_argument("--profile-timed", action="store_true",
                     help="bracket the headline forms' timed steps with cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")
@@ -93,7 +95,7 @@ FP32_PEAK_NOMINAL = 80550.0   # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 G
 # (dram__bytes_read.sum + dram__bytes_write.sum) of
 # `bench.py --profile-only --n N --steps 2 --warmup 1 --state-cache ...`.
 # Re-measure when the kernel changes (None: not measured for this kernel).
-F64_STAGE_DRAM_BYTES = {1024: 60.16e6, 4096: 1409.84e6}
+F64_STAGE_DRAM_BYTES = {4096: 1405.32e6}
 
 
 def fma_peaks():
@@ -727,6 +729,10 @@ def main():
     if args.profile_only:
         s = gbr.Solver.for_case(case, stream=st.cuda_stream, precision=args.profile_precision)
         s.set_state(q_start)
+        if args.profile_sensor:
+            from paper_2305_00762_gb300 import sensor_train
+            s.set_sensor(sensor_train.load_weights())
+            gbr.gbr_set_option(s.ctx, gbr.GBR_OPT_SENSOR, args.profile_sensor)
         for _ in range(args.warmup):
             s.step_cfl(CFL)
         s.sync()
