@@ -157,10 +157,11 @@ __device__ __forceinline__ double minmod(double a, double b)
     return (ba ^ bb) < 0 ? 0.0 : r;     // opposite signs
 }
 
-// The MP test's comparison x <= 1e-40 (Eq. mp5Condition).
+// The MP test's comparison x <= thr (Eq. mp5Condition: thr = 1e-40 for a
+// field in the paper's scaling, 1e-40 s^2 for one carried scaled by s).
 template <typename T>
-__device__ __forceinline__ bool mp_accept(T x) { return x <= T(1e-40); }
-__device__ __forceinline__ bool mp_accept(double x) { return ordkey(x) <= ordkey(1e-40); }
+__device__ __forceinline__ bool mp_accept(T x, T thr) { return x <= thr; }
+__device__ __forceinline__ bool mp_accept(double x, double thr) { return ordkey(x) <= ordkey(thr); }
 
 // The last step of Eq. mp-procedure from Phi_j, Phi_{j+1}, Phi^MD, Phi^UL,
 // Phi^LC and the GRB value pl. Phi^min = max(min(Phi_j, Phi_{j+1}, MD),
@@ -343,13 +344,14 @@ __device__ __forceinline__ GrbCoef<T> grb_coef(int order)
 // limited value is continuous across the test's boundary, where Phi^L lies
 // within the MP bounds).
 template <typename T>
-__device__ __forceinline__ T grb_mp(T pj, T Dm1, T Dp1, T s1, T S2, T dj, T dd, bool& need, const GrbCoef<T>& C)
+__device__ __forceinline__ T grb_mp(T pj, T Dm1, T Dp1, T s1, T S2, T dj, T dd, bool& need, const GrbCoef<T>& C,
+                                    T thr)
 {
     // the weights divided by 840 (420/840 = 1/2 exactly): one product, three FMAs
     T delta = rfma(C.w2 * T(1.0 / 840.0), s1, rfma(C.w1 * T(1.0 / 840.0), dd, rmul(T(0.5), dj)));
     if (C.w3 != T(0)) delta = rfma(C.w3 * T(1.0 / 840.0), S2, delta);
     const T m = minmod(Dp1, T(-7) * Dm1);
-    need = !mp_accept(delta * (delta - m));
+    need = !mp_accept(delta * (delta - m), thr);
     return pj + delta;
 }
 
@@ -411,7 +413,8 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int n)
 // lane of the warp must call this together. The arithmetic of each value is
 // unchanged, so the result is the same.
 template <typename T>
-__device__ __forceinline__ void meg7_pair(const GrbCoef<T>& C, const T (&w)[6], const T (&e)[6], T& vl, T& vr)
+__device__ __forceinline__ void meg7_pair(const GrbCoef<T>& C, const T (&w)[6], const T (&e)[6], T& vl, T& vr,
+                                          T thr = T(1e-40))
 {
     const T pL[5] = {w[0], w[1], w[2], w[3], w[4]}, dL[5] = {e[0], e[1], e[2], e[3], e[4]};
     const T pR[5] = {w[5], w[4], w[3], w[2], w[1]}, dR[5] = {-e[5], -e[4], -e[3], -e[2], -e[1]};
@@ -422,8 +425,8 @@ __device__ __forceinline__ void meg7_pair(const GrbCoef<T>& C, const T (&w)[6], 
     const T aL = w[1] - w[2], aR = w[4] - w[3];
     const T s1L = aL + b, s1R = aR - b;          // second differences at j, j+1
     const T ddL = e[1] - e[3], ddR = e[2] - e[4];  // (mirrored for the right side)
-    vl = grb_mp(w[2], aL, b, s1L, rfma(T(-2), w[2], w[0] + w[4]), e[2], ddL, needL, C);
-    vr = grb_mp(w[3], aR, -b, s1R, rfma(T(-2), w[3], w[5] + w[1]), -e[3], ddR, needR, C);
+    vl = grb_mp(w[2], aL, b, s1L, rfma(T(-2), w[2], w[0] + w[4]), e[2], ddL, needL, C, thr);
+    vr = grb_mp(w[3], aR, -b, s1R, rfma(T(-2), w[3], w[5] + w[1]), -e[3], ddR, needR, C, thr);
     if constexpr (sizeof(T) == 8) {
         const unsigned mL = __ballot_sync(0xffffffffu, needL), mR = __ballot_sync(0xffffffffu, needR);
         const int nL = __popc(mL), nR = __popc(mR);
@@ -546,26 +549,30 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
     const T cb = gp * y;             // c
     const T c2 = cb * cb;            // c^2
     const T irb = cb * y;            // 1 / rho
-    const T al = T(0.5) * rb * icb;  // rho / (2 c)
     const T ic2 = icb * icb;         // 1 / c^2
     const T be = T(0.5) * ic2;       // 1 / (2 c^2)
 
     T wL[4], wR[4];
     if constexpr (!CONS) {
-        {  // fields 1 and 4 (u - c and u + c) share un and p
+        {  // fields 1 and 4 (u - c and u + c) share un and p. They are
+           // carried scaled by 2 c^2, as p -/+ rho c un: GRB, the limiter's
+           // bounds and its clamp are linear and scale-free, and the MP
+           // test's threshold 1e-40 becomes 1e-40 (2 c^2)^2.
+            const T rc = rb * cb;  // rho c
+            const T thr = T(4e-40) * c2 * c2;
             T w0[6], w3[6], e0[6], e3[6];
     #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 const int o = (k - 2);
-                const T tu = al * in.u[1][o * su], p = in.u[3][o * su];
-                w0[k] = rfma(be, p, -tu);
-                w3[k] = rfma(be, p, tu);
-                const T gu = al * in.g[1][o * sg], gp = in.g[3][o * sg];
-                e0[k] = rfma(be, gp, -gu);
-                e3[k] = rfma(be, gp, gu);
+                const T un = in.u[1][o * su], p = in.u[3][o * su];
+                w0[k] = rfma(-rc, un, p);
+                w3[k] = rfma(rc, un, p);
+                const T gu = in.g[1][o * sg], gp = in.g[3][o * sg];
+                e0[k] = rfma(-rc, gu, gp);
+                e3[k] = rfma(rc, gu, gp);
             }
-            meg7_pair(coef, w0, e0, wL[0], wR[0]);
-            meg7_pair(coef, w3, e3, wL[3], wR[3]);
+            meg7_pair(coef, w0, e0, wL[0], wR[0], thr);
+            meg7_pair(coef, w3, e3, wL[3], wR[3], thr);
         }
         {  // field 2 (entropy): rho - p / c^2
             T w[6], e[6];
@@ -609,15 +616,19 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
     T rL, unL, utL, pL, EL, rR, unR, utR, pR, ER;
     T QL[4], QR[4];
     if constexpr (!CONS) {
-        const T crb = cb * irb;
-        rL = wL[0] + wL[1] + wL[3];
-        unL = crb * (wL[3] - wL[0]);
+        // fields 1 and 4 back from their 2 c^2 scaling: with
+        // a = w1 + w4, rho = a / (2 c^2) + w2, p = a / 2 and
+        // un = (w4 - w1) / (2 rho c)
+        const T hrc = T(0.5) * irb * icb;  // 1 / (2 rho c)
+        const T aL03 = wL[0] + wL[3], aR03 = wR[0] + wR[3];
+        rL = rfma(be, aL03, wL[1]);
+        unL = hrc * (wL[3] - wL[0]);
         utL = wL[2];
-        pL = c2 * (wL[0] + wL[3]);
-        rR = wR[0] + wR[1] + wR[3];
-        unR = crb * (wR[3] - wR[0]);
+        pL = T(0.5) * aL03;
+        rR = rfma(be, aR03, wR[1]);
+        unR = hrc * (wR[3] - wR[0]);
         utR = wR[2];
-        pR = c2 * (wR[0] + wR[3]);
+        pR = T(0.5) * aR03;
         // positivity fallback: a face state with rho <= 0 or p <= 0 takes the
         // adjacent cell's state (characteristic reconstruction across a
         // strong shock, e.g. the foot of the double Mach reflection)
