@@ -759,8 +759,6 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
         const T d2z = den * den * z;
         const T iL = nR * d2z, iR = nL * d2z;
         const T kL = mL * iL, kR = mR * iR;
-        const T QsL[4] = {kL, kL * Ss, kL * utL, kL * (EL * irL + (Ss - unL) * Ss) + (Ss - unL) * pL * iL};
-        const T QsR[4] = {kR, kR * Ss, kR * utR, kR * (ER * irR + (Ss - unR) * Ss) + (Ss - unR) * pR * iR};
         T aL = tabs(SL), aR = tabs(SR);
         const T aS = tabs(Ss);
         if (P.lm) {
@@ -776,10 +774,18 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
             }
         }
         // 1/2 |A| dQ = 1/2 (aL (QsL - QL) + aS (QsR - QsL) + aR (QR - QsR)),
-        // regrouped by state: four fused terms per component
+        // regrouped by state: hL QsL + hS QsR - hQL QL + hQR QR. The star
+        // states are Q*_K = k_K (1, S*, ut_K, E_K / rho_K + (S* - un_K) S*)
+        // + (0, 0, 0, (S* - un_K) p_K / (S_K - S*)): the factors h k are
+        // formed once and the star states never built.
         const T hL = T(0.5) * (aL - aS), hS = T(0.5) * (aS - aR), hQL = T(0.5) * aL, hQR = T(0.5) * aR;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) out[m] = Fc[m] - hL * QsL[m] - hS * QsR[m] + hQL * QL[m] - hQR * QR[m];
+        const T fL = hL * kL, fR = hS * kR;
+        const T tL = Ss - unL, tR = Ss - unR;
+        out[0] = Fc[0] - fL - fR + hQL * QL[0] - hQR * QR[0];
+        out[1] = Fc[1] - (fL + fR) * Ss + hQL * QL[1] - hQR * QR[1];
+        out[2] = Fc[2] - fL * utL - fR * utR + hQL * QL[2] - hQR * QR[2];
+        out[3] = Fc[3] - fL * (EL * irL + tL * Ss) - (hL * iL) * (tL * pL) - fR * (ER * irR + tR * Ss) -
+                 (hS * iR) * (tR * pR) + hQL * QL[3] - hQR * QR[3];
     }
 
     if constexpr (VISC) {
