@@ -141,12 +141,13 @@ __device__ __forceinline__ double tmin(double a, double b) { return ordkey(a) < 
 __device__ __forceinline__ double tmax(double a, double b) { return ordkey(a) > ordkey(b) ? a : b; }
 
 // Eq. alpha: minmod(a, b) = 1/2 (sign a + sign b) min(|a|, |b|): the operand
-// of smaller magnitude when the signs agree, else 0 (the sign test on the
-// bits; only the sign of a zero result may differ from the formula's).
+// of smaller magnitude when the signs agree, else 0. FP32: that is the
+// median of a, b and 0, four min / max instructions; FP64: the sign test on
+// the bits and the magnitudes compared as integers. Only the sign of a zero
+// result may differ from the formula's.
 __device__ __forceinline__ float minmod(float a, float b)
 {
-    const float r = fabsf(a) <= fabsf(b) ? a : b;
-    return (__float_as_int(a) ^ __float_as_int(b)) < 0 ? 0.f : r;
+    return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.f));
 }
 __device__ __forceinline__ double minmod(double a, double b)
 {
@@ -371,11 +372,9 @@ template <typename T>
 __device__ __forceinline__ T mp_limit(const T* p, const T* d, T pl, T s1, T dd, T s1o, T ddo)
 {
     const T dm1 = rfma(T(4), rfma(T(-2), p[1], p[2]) + p[0], d[0] - d[2]);
-    // (FP64 takes d_j and d_{j+1} from the sums, which saves FP64
-    // operations; FP32, bound by its instruction count rather than by one
-    // pipe, recomputes them and keeps fewer values live)
-    const T dj = sizeof(T) == 8 ? rfma(T(4), s1, dd) : rfma(T(4), rfma(T(-2), p[2], p[3]) + p[1], d[1] - d[3]);
-    const T dp1 = sizeof(T) == 8 ? rfma(T(4), s1o, ddo) : rfma(T(4), rfma(T(-2), p[3], p[4]) + p[2], d[2] - d[4]);
+    // (d_j and d_{j+1} from the sums: one FMA each)
+    const T dj = rfma(T(4), s1, dd);
+    const T dp1 = rfma(T(4), s1o, ddo);
     const T md = rmul(T(0.5), rfma(T(-0.5), minmod(dj, dp1), p[2] + p[3]));
     const T Dm1 = p[1] - p[2];
     const T ul = rfma(T(-7), Dm1, p[2]);
