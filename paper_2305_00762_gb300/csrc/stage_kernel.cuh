@@ -341,7 +341,8 @@ __device__ __forceinline__ GrbCoef<T> grb_coef(int order)
 // Phi'_{j+1}: Phi^L = Phi_j + delta with delta the weighted sum above, and
 // Phi^MP = Phi_j + m with m = minmod(Dp1, -7 Dm1). The MP test of Eq.
 // mp5Condition, (Phi^L - Phi_j)(Phi^L - Phi^MP) <= 1e-40, is taken as
-// delta (delta - m) <= 1e-40 (the same quantity, rounded differently; the
+// delta (delta - m) <= thr (the same quantity, rounded differently; thr is
+// 1e-40 times the square of the field's scaling, see mp_accept; the
 // limited value is continuous across the test's boundary, where Phi^L lies
 // within the MP bounds).
 template <typename T>
