@@ -383,6 +383,28 @@ __device__ __forceinline__ T mp_limit(const T* p, const T* d, T pl, T s1, T dd, 
     return mp_clamp(p[2], p[3], md, ul, lc, pl);
 }
 
+// mp_limit for both values of one face and field, where a lane limits its
+// own left and right values (w = Phi_{j-2..j+3}, e their gradients; aL, aR,
+// s1L, s1R, ddL, ddR as formed for the GRB values). The two sides share
+// Phi^MD: the right value's stencil is the left's mirrored about the face,
+// so Phi_j + Phi_{j+1} and minmod(d_j, d_{j+1}) are the same for both (the
+// sum and minmod are symmetric in their operands), and each side's d_{j+1}
+// is the other side's d_j. Every value is bitwise that of mp_limit.
+template <typename T>
+__device__ __forceinline__ void mp_limit_pair(const T (&w)[6], const T (&e)[6], T aL, T aR, T s1L, T s1R, T ddL,
+                                              T ddR, T& vl, T& vr, bool needL, bool needR)
+{
+    const T djL = rfma(T(4), s1L, ddL), djR = rfma(T(4), s1R, ddR);  // 2 d at j and j+1
+    const T md = rmul(T(0.5), rfma(T(-0.5), minmod(djL, djR), w[2] + w[3]));
+    const T dmL = rfma(T(4), rfma(T(-2), w[1], w[2]) + w[0], e[0] - e[2]);  // 2 d at j-1
+    const T dmR = rfma(T(4), rfma(T(-2), w[4], w[3]) + w[5], e[3] - e[5]);  // 2 d at j+2
+    const T ulL = rfma(T(-7), aL, w[2]), ulR = rfma(T(-7), aR, w[3]);
+    const T lcL = rfma(T(2.0 / 3.0), minmod(djL, dmL), rfma(T(-0.5), aL, w[2]));
+    const T lcR = rfma(T(2.0 / 3.0), minmod(djR, dmR), rfma(T(-0.5), aR, w[3]));
+    if (needL) vl = mp_clamp(w[2], w[3], md, ulL, lcL, vl);
+    if (needR) vr = mp_clamp(w[3], w[2], md, ulR, lcR, vr);
+}
+
 // Position of the n-th (0-based) set bit of m; m has more than n set bits.
 __device__ __forceinline__ int nth_set_bit(unsigned m, int n)
 {
@@ -416,8 +438,6 @@ template <typename T>
 __device__ __forceinline__ void meg7_pair(const GrbCoef<T>& C, const T (&w)[6], const T (&e)[6], T& vl, T& vr,
                                           T thr = T(1e-40))
 {
-    const T pL[5] = {w[0], w[1], w[2], w[3], w[4]}, dL[5] = {e[0], e[1], e[2], e[3], e[4]};
-    const T pR[5] = {w[5], w[4], w[3], w[2], w[1]}, dR[5] = {-e[5], -e[4], -e[3], -e[2], -e[1]};
     bool needL, needR;
     // The two sides share the difference w3 - w2 (the left side's D_{+1} is
     // minus the right side's).
@@ -463,8 +483,7 @@ __device__ __forceinline__ void meg7_pair(const GrbCoef<T>& C, const T (&w)[6], 
             return;
         }
     }
-    if (needL) vl = mp_limit(pL, dL, vl, s1L, ddL, s1R, ddR);
-    if (needR) vr = mp_limit(pR, dR, vr, s1R, ddR, s1L, ddL);
+    if (needL || needR) mp_limit_pair(w, e, aL, aR, s1L, s1R, ddL, ddR, vl, vr, needL, needR);
 }
 
 // 1/2 (F(f_L) + F(f_R)) at the face after cell f[0]: the sum of Eq.
