@@ -259,13 +259,16 @@ __device__ __forceinline__ bool tpositive(double x) { return positive_bits(x); }
 __device__ __forceinline__ bool tless(float a, float b) { return a < b; }
 __device__ __forceinline__ bool tless(double a, double b) { return ordkey(a) < ordkey(b); }
 
-// Eq. six: dx-scaled sixth-order gradient at s[0] along stride st.
+// Eq. six: the dx-scaled sixth-order gradient at s[0] along stride st,
+// carried as 60 times its value (45 D1 - 9 D2 + D3, without the final
+// division): every consumer is linear in the gradients and takes the 1/60
+// into its own constant factors (kGrad below).
 template <typename T>
 __device__ __forceinline__ T grad6(const T* s, int st)
 {
-    return rmul(rfma(T(45), s[st] - s[-st], rfma(T(-9), s[2 * st] - s[-2 * st], s[3 * st] - s[-3 * st])),
-                T(1.0 / 60.0));
+    return rfma(T(45), s[st] - s[-st], rfma(T(-9), s[2 * st] - s[-2 * st], s[3 * st] - s[-3 * st]));
 }
+constexpr double kGrad = 60.0;  // the scale of the carried gradients
 
 // Eq. detector with eps = 0.9 psi_c xi^2 / (1 - 0.9 psi_c), xi = 1e-3: returns
 // true when psi_j < psi_c = 0.5. psi = (2ab + eps)/(a^2 + b^2 + eps) and the
@@ -349,8 +352,10 @@ template <typename T>
 __device__ __forceinline__ T grb_mp(T pj, T Dm1, T Dp1, T s1, T S2, T dj, T dd, bool& need, const GrbCoef<T>& C,
                                     T thr)
 {
-    // the weights divided by 840 (420/840 = 1/2 exactly): one product, three FMAs
-    T delta = rfma(C.w2 * T(1.0 / 840.0), s1, rfma(C.w1 * T(1.0 / 840.0), dd, rmul(T(0.5), dj)));
+    // the weights divided by 840 (and the gradients' by their scale):
+    // one product, three FMAs
+    T delta = rfma(C.w2 * T(1.0 / 840.0), s1,
+                   rfma(C.w1 * T(1.0 / (840.0 * kGrad)), dd, rmul(T(0.5 / kGrad), dj)));
     if (C.w3 != T(0)) delta = rfma(C.w3 * T(1.0 / 840.0), S2, delta);
     const T m = minmod(Dp1, T(-7) * Dm1);
     need = !mp_accept(delta * (delta - m), thr);
@@ -366,20 +371,21 @@ __device__ __forceinline__ T grb_mp(T pj, T Dm1, T Dp1, T s1, T S2, T dj, T dd, 
 // The curvature d_{j+1} is the other side's d_j (the right value at the same
 // face is centred on cell j+1, mirrored, and the curvature is unchanged by
 // the mirror): it comes from that side's sums s1o, ddo.
-// The curvatures are carried as 2 d (one operation fewer each); doubling is
-// exact, and minmod(2a, 2b) = 2 minmod(a, b), so Phi^MD and Phi^LC, with the
-// halved factors 1/2 and 2/3, round exactly as from d itself.
+// The curvatures are carried as 2 kGrad d (one operation fewer each, with
+// the gradients at their carried scale; minmod(s a, s b) = s minmod(a, b)
+// for s > 0), so Phi^MD and Phi^LC take the factors 1/(2 kGrad) and
+// 2/(3 kGrad).
 template <typename T>
 __device__ __forceinline__ T mp_limit(const T* p, const T* d, T pl, T s1, T dd, T s1o, T ddo)
 {
-    const T dm1 = rfma(T(4), rfma(T(-2), p[1], p[2]) + p[0], d[0] - d[2]);
+    const T dm1 = rfma(T(4 * kGrad), rfma(T(-2), p[1], p[2]) + p[0], d[0] - d[2]);
     // (d_j and d_{j+1} from the sums: one FMA each)
-    const T dj = rfma(T(4), s1, dd);
-    const T dp1 = rfma(T(4), s1o, ddo);
-    const T md = rmul(T(0.5), rfma(T(-0.5), minmod(dj, dp1), p[2] + p[3]));
+    const T dj = rfma(T(4 * kGrad), s1, dd);
+    const T dp1 = rfma(T(4 * kGrad), s1o, ddo);
+    const T md = rmul(T(0.5), rfma(T(-0.5 / kGrad), minmod(dj, dp1), p[2] + p[3]));
     const T Dm1 = p[1] - p[2];
     const T ul = rfma(T(-7), Dm1, p[2]);
-    const T lc = rfma(T(2.0 / 3.0), minmod(dj, dm1), rfma(T(-0.5), Dm1, p[2]));
+    const T lc = rfma(T(2.0 / (3.0 * kGrad)), minmod(dj, dm1), rfma(T(-0.5), Dm1, p[2]));
     return mp_clamp(p[2], p[3], md, ul, lc, pl);
 }
 
@@ -394,13 +400,13 @@ template <typename T>
 __device__ __forceinline__ void mp_limit_pair(const T (&w)[6], const T (&e)[6], T aL, T aR, T s1L, T s1R, T ddL,
                                               T ddR, T& vl, T& vr, bool needL, bool needR)
 {
-    const T djL = rfma(T(4), s1L, ddL), djR = rfma(T(4), s1R, ddR);  // 2 d at j and j+1
-    const T md = rmul(T(0.5), rfma(T(-0.5), minmod(djL, djR), w[2] + w[3]));
-    const T dmL = rfma(T(4), rfma(T(-2), w[1], w[2]) + w[0], e[0] - e[2]);  // 2 d at j-1
-    const T dmR = rfma(T(4), rfma(T(-2), w[4], w[3]) + w[5], e[3] - e[5]);  // 2 d at j+2
+    const T djL = rfma(T(4 * kGrad), s1L, ddL), djR = rfma(T(4 * kGrad), s1R, ddR);  // at j and j+1
+    const T md = rmul(T(0.5), rfma(T(-0.5 / kGrad), minmod(djL, djR), w[2] + w[3]));
+    const T dmL = rfma(T(4 * kGrad), rfma(T(-2), w[1], w[2]) + w[0], e[0] - e[2]);  // at j-1
+    const T dmR = rfma(T(4 * kGrad), rfma(T(-2), w[4], w[3]) + w[5], e[3] - e[5]);  // at j+2
     const T ulL = rfma(T(-7), aL, w[2]), ulR = rfma(T(-7), aR, w[3]);
-    const T lcL = rfma(T(2.0 / 3.0), minmod(djL, dmL), rfma(T(-0.5), aL, w[2]));
-    const T lcR = rfma(T(2.0 / 3.0), minmod(djR, dmR), rfma(T(-0.5), aR, w[3]));
+    const T lcL = rfma(T(2.0 / (3.0 * kGrad)), minmod(djL, dmL), rfma(T(-0.5), aL, w[2]));
+    const T lcR = rfma(T(2.0 / (3.0 * kGrad)), minmod(djR, dmR), rfma(T(-0.5), aR, w[3]));
     if (needL) vl = mp_clamp(w[2], w[3], md, ulL, lcL, vl);
     if (needR) vr = mp_clamp(w[3], w[2], md, ulR, lcR, vr);
 }
@@ -832,9 +838,11 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
         const T T0 = P.gamma * p0 * ir0, T1 = P.gamma * p1 * ir1;
         const T dT0 = P.gamma * (dp0 * ir0 - p0 * dr0 * ir0 * ir0);
         const T dT1 = P.gamma * (dp1 * ir1 - p1 * dr1 * ir1 * ir1);
-        const T un_n = (T(0.5) * (dn0 + dn1) + T(2) * (n1 - T(0.5) * dn1 - n0 - T(0.5) * dn0)) * inv_dn;
-        const T ut_n = (T(0.5) * (dt0 + dt1) + T(2) * (t1 - T(0.5) * dt1 - t0 - T(0.5) * dt0)) * inv_dn;
-        const T T_n = (T(0.5) * (dT0 + dT1) + T(2) * (T1 - T(0.5) * dT1 - T0 - T(0.5) * dT0)) * inv_dn;
+        // (the gradients, and so T', at their carried scale kGrad)
+        const T hg = T(0.5 / kGrad);
+        const T un_n = (hg * (dn0 + dn1) + T(2) * (n1 - hg * dn1 - n0 - hg * dn0)) * inv_dn;
+        const T ut_n = (hg * (dt0 + dt1) + T(2) * (t1 - hg * dt1 - t0 - hg * dt0)) * inv_dn;
+        const T T_n = (hg * (dT0 + dT1) + T(2) * (T1 - hg * dT1 - T0 - hg * dT0)) * inv_dn;
         T gn0 = in.tun[0], gn1 = in.tun[in.stq], gt0 = in.tut[0], gt1 = in.tut[in.stq];
         if constexpr (CONS) {  // tangential derivatives of un, ut from those of rho un, rho ut, rho
             const T ra0 = in.tr0[0], ra1 = in.tr0[in.stq];
@@ -843,8 +851,8 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
             gt0 = (gt0 - t0 * ra0) * ir0;
             gt1 = (gt1 - t1 * ra1) * ir1;
         }
-        const T un_t = T(0.5) * (gn0 + gn1) * inv_dt;
-        const T ut_t = T(0.5) * (gt0 + gt1) * inv_dt;
+        const T un_t = hg * (gn0 + gn1) * inv_dt;
+        const T ut_t = hg * (gt0 + gt1) * inv_dt;
         const T unf = T(0.5) * (n0 + n1), utf = T(0.5) * (t0 + t1);
         const T tau_nn = T(2.0 / 3.0) * P.mu * (T(2) * un_n - ut_t);
         const T tau_nt = P.mu * (un_t + ut_n);
