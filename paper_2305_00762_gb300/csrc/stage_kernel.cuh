@@ -158,8 +158,9 @@ __device__ __forceinline__ double minmod(double a, double b)
     return (ba ^ bb) < 0 ? 0.0 : r;     // opposite signs
 }
 
-// The MP test's comparison x <= thr (Eq. mp5Condition: thr = 1e-40 for a
-// field in the paper's scaling, 1e-40 s^2 for one carried scaled by s).
+// The MP test's comparison x <= thr (Eq. mp5Condition: 1e-40 for a field in
+// the paper's scaling, 1e-40 s^2 for one carried scaled by s; grb_mp tests
+// a multiple of the product and scales thr alike).
 template <typename T>
 __device__ __forceinline__ bool mp_accept(T x, T thr) { return x <= thr; }
 __device__ __forceinline__ bool mp_accept(double x, double thr) { return ordkey(x) <= ordkey(thr); }
@@ -344,22 +345,25 @@ __device__ __forceinline__ GrbCoef<T> grb_coef(int order)
 // Phi'_{j+1}: Phi^L = Phi_j + delta with delta the weighted sum above, and
 // Phi^MP = Phi_j + m with m = minmod(Dp1, -7 Dm1). The MP test of Eq.
 // mp5Condition, (Phi^L - Phi_j)(Phi^L - Phi^MP) <= 1e-40, is taken as
-// delta (delta - m) <= thr (the same quantity, rounded differently; thr is
-// 1e-40 times the square of the field's scaling, see mp_accept; the
+// delta (delta - m) <= 1e-40 (the same quantity, rounded differently; the
 // limited value is continuous across the test's boundary, where Phi^L lies
-// within the MP bounds).
+// within the MP bounds). With the gradients at their carried scale kGrad,
+// D = 2 kGrad delta has the unit weight on Phi'_j (three FMAs, no product),
+// and the test is taken on D: D (D - 2 kGrad m) <= (2 kGrad)^2 1e-40. The
+// caller passes Dp1s = 2 kGrad Dp1 and thr = 1e-40 kMP (times the square of
+// the field's own scaling, see mp_accept).
+constexpr double kGrbD = 2.0 * kGrad;           // D = kGrbD delta
+constexpr double kMP = kGrbD * kGrbD;           // the MP threshold's factor
 template <typename T>
-__device__ __forceinline__ T grb_mp(T pj, T Dm1, T Dp1, T s1, T S2, T dj, T dd, bool& need, const GrbCoef<T>& C,
+__device__ __forceinline__ T grb_mp(T pj, T Dm1, T Dp1s, T s1, T S2, T dj, T dd, bool& need, const GrbCoef<T>& C,
                                     T thr)
 {
-    // the weights divided by 840 (and the gradients' by their scale):
-    // one product, three FMAs
-    T delta = rfma(C.w2 * T(1.0 / 840.0), s1,
-                   rfma(C.w1 * T(1.0 / (840.0 * kGrad)), dd, rmul(T(0.5 / kGrad), dj)));
-    if (C.w3 != T(0)) delta = rfma(C.w3 * T(1.0 / 840.0), S2, delta);
-    const T m = minmod(Dp1, T(-7) * Dm1);
-    need = !mp_accept(delta * (delta - m), thr);
-    return pj + delta;
+    // the weights times kGrbD / 840 (the gradients' divided by their scale)
+    T D = rfma(C.w2 * T(kGrbD / 840.0), s1, rfma(C.w1 * T(2.0 / 840.0), dd, dj));
+    if (C.w3 != T(0)) D = rfma(C.w3 * T(kGrbD / 840.0), S2, D);
+    const T ms = minmod(Dp1s, T(-7.0 * kGrbD) * Dm1);
+    need = !mp_accept(D * (D - ms), thr);
+    return rfma(T(1.0 / kGrbD), D, pj);
 }
 
 // Eq. mp-procedure: the MP-limited value given the GRB value pl. The
@@ -442,7 +446,7 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int n)
 // unchanged, so the result is the same.
 template <typename T>
 __device__ __forceinline__ void meg7_pair(const GrbCoef<T>& C, const T (&w)[6], const T (&e)[6], T& vl, T& vr,
-                                          T thr = T(1e-40))
+                                          T thr = T(1e-40 * kMP))
 {
     bool needL, needR;
     // The two sides share the difference w3 - w2 (the left side's D_{+1} is
@@ -451,8 +455,9 @@ __device__ __forceinline__ void meg7_pair(const GrbCoef<T>& C, const T (&w)[6], 
     const T aL = w[1] - w[2], aR = w[4] - w[3];
     const T s1L = aL + b, s1R = aR - b;          // second differences at j, j+1
     const T ddL = e[1] - e[3], ddR = e[2] - e[4];  // (mirrored for the right side)
-    vl = grb_mp(w[2], aL, b, s1L, rfma(T(-2), w[2], w[0] + w[4]), e[2], ddL, needL, C, thr);
-    vr = grb_mp(w[3], aR, -b, s1R, rfma(T(-2), w[3], w[5] + w[1]), -e[3], ddR, needR, C, thr);
+    const T bs = T(kGrbD) * b;
+    vl = grb_mp(w[2], aL, bs, s1L, rfma(T(-2), w[2], w[0] + w[4]), e[2], ddL, needL, C, thr);
+    vr = grb_mp(w[3], aR, -bs, s1R, rfma(T(-2), w[3], w[5] + w[1]), -e[3], ddR, needR, C, thr);
     if constexpr (sizeof(T) == 8) {
         const unsigned mL = __ballot_sync(0xffffffffu, needL), mR = __ballot_sync(0xffffffffu, needR);
         const int nL = __popc(mL), nR = __popc(mR);
@@ -584,7 +589,7 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
            // bounds and its clamp are linear and scale-free, and the MP
            // test's threshold 1e-40 becomes 1e-40 (2 c^2)^2.
             const T rc = rb * cb;  // rho c
-            const T thr = T(4e-40) * c2 * c2;
+            const T thr = T(4e-40 * kMP) * c2 * c2;
             T w0[6], w3[6], e0[6], e3[6];
     #pragma unroll
             for (int k = 0; k < 6; ++k) {
