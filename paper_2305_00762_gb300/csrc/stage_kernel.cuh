@@ -370,8 +370,9 @@ __device__ __forceinline__ T grb_mp(T pj, T Dm1, T Dp1s, T s1, T S2, T dj, T dd,
 // curvature d_j = 2 (Phi_{j-1} - 2 Phi_j + Phi_{j+1}) - (Phi'_{j+1} -
 // Phi'_{j-1})/2 can come from the sums the GRB value was formed with: s1 =
 // Dm1 + Dp1 and dd = Phi'_{j-1} - Phi'_{j+1}.
-// Its products are explicitly rounded: it is inlined at two sites (packed
-// and per lane, see meg7_pair) that must round alike.
+// Its products are explicitly rounded: the packed path of meg7_pair inlines
+// it and the per-lane path runs the same arithmetic in mp_limit_pair, and
+// the two must round alike.
 // The curvature d_{j+1} is the other side's d_j (the right value at the same
 // face is centred on cell j+1, mirrored, and the curvature is unchanged by
 // the mirror): it comes from that side's sums s1o, ddo.
