@@ -675,15 +675,16 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
             utR = in.u[2][su];
             pR = in.u[3][su];
         }
-        EL = pL * P.igm1 + T(0.5) * rL * (unL * unL + utL * utL);
-        ER = pR * P.igm1 + T(0.5) * rR * (unR * unR + utR * utR);
         QL[0] = rL;
         QL[1] = rL * unL;
         QL[2] = rL * utL;
-        QL[3] = EL;
         QR[0] = rR;
         QR[1] = rR * unR;
         QR[2] = rR * utR;
+        // E = p / (gamma - 1) + (rho un un + rho ut ut) / 2, from the momenta
+        EL = rfma(T(0.5), rfma(QL[1], unL, rmul(QL[2], utL)), rmul(pL, P.igm1));
+        ER = rfma(T(0.5), rfma(QR[1], unR, rmul(QR[2], utR)), rmul(pR, P.igm1));
+        QL[3] = EL;
         QR[3] = ER;
     } else {
         const T ub = T(0.5) * (in.u[1][0] + in.u[1][su]), vb = T(0.5) * (in.u[2][0] + in.u[2][su]);
@@ -765,15 +766,15 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
         const T cL = gpL * yL, cR = gpR * yR;
         const T icL = rL * yL, icR = rR * yR;
         const T irL = cL * yL, irR = cR * yR;
-        const T HL = (EL + pL) * irL, HR = (ER + pR) * irR;
-        // Roe weights sqrt(rho_L) / (sqrt(rho_L) + sqrt(rho_R)) = 1 / (1 + q)
-        // and q / (1 + q), q = sqrt(rho_R / rho_L)
+        const T eL = EL * irL, eR = ER * irR;  // E / rho
+        const T HL = rfma(pL, irL, eL), HR = rfma(pR, irR, eR);
+        // Roe averages (a_L + q a_R) / (1 + q), q = sqrt(rho_R / rho_L)
         const T xq = rR * irL;
         const T q = xq * trsqrt(xq);
-        const T oL = T(1) / (T(1) + q), oR = q * oL;
-        const T ut = oL * unL + oR * unR;
-        const T vt = oL * utL + oR * utR;
-        const T Ht = oL * HL + oR * HR;
+        const T oL = T(1) / (T(1) + q);
+        const T ut = oL * rfma(q, unR, unL);
+        const T vt = oL * rfma(q, utR, utL);
+        const T Ht = oL * rfma(q, HR, HL);
         const T c2t = P.gm1 * (Ht - T(0.5) * (ut * ut + vt * vt));
         const T ct = c2t * trsqrt(c2t);
         const T SL = tmin(unL - cL, ut - ct);
@@ -788,8 +789,7 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
         const T z = T(1) / (den * nLR);
         const T Ss = num * nLR * z;
         const T d2z = den * den * z;
-        const T iL = nR * d2z, iR = nL * d2z;
-        const T kL = mL * iL, kR = mR * iR;
+        const T iL = nR * d2z, iR = nL * d2z;  // 1/(S_L - S*), 1/(S_R - S*)
         T aL = tabs(SL), aR = tabs(SR);
         const T aS = tabs(Ss);
         if (P.lm) {
@@ -807,16 +807,18 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
         // 1/2 |A| dQ = 1/2 (aL (QsL - QL) + aS (QsR - QsL) + aR (QR - QsR)),
         // regrouped by state: hL QsL + hS QsR - hQL QL + hQR QR. The star
         // states are Q*_K = k_K (1, S*, ut_K, E_K / rho_K + (S* - un_K) S*)
-        // + (0, 0, 0, (S* - un_K) p_K / (S_K - S*)): the factors h k are
-        // formed once and the star states never built.
+        // + (0, 0, 0, (S* - un_K) p_K / (S_K - S*)), k_K = m_K / (S_K - S*):
+        // the factors h / (S_K - S*) and h k are formed once and the star
+        // states never built.
         const T hL = T(0.5) * (aL - aS), hS = T(0.5) * (aS - aR), hQL = T(0.5) * aL, hQR = T(0.5) * aR;
-        const T fL = hL * kL, fR = hS * kR;
+        const T giL = hL * iL, giR = hS * iR;
+        const T fL = giL * mL, fR = giR * mR;
         const T tL = Ss - unL, tR = Ss - unR;
         out[0] = Fc[0] - fL - fR + hQL * QL[0] - hQR * QR[0];
         out[1] = Fc[1] - (fL + fR) * Ss + hQL * QL[1] - hQR * QR[1];
         out[2] = Fc[2] - fL * utL - fR * utR + hQL * QL[2] - hQR * QR[2];
-        out[3] = Fc[3] - fL * (EL * irL + tL * Ss) - (hL * iL) * (tL * pL) - fR * (ER * irR + tR * Ss) -
-                 (hS * iR) * (tR * pR) + hQL * QL[3] - hQR * QR[3];
+        out[3] = Fc[3] - fL * (eL + tL * Ss) - giL * (tL * pL) - fR * (eR + tR * Ss) - giR * (tR * pR) +
+                 hQL * QL[3] - hQR * QR[3];
     }
 
     if constexpr (VISC) {
