@@ -571,7 +571,7 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
     const int su = in.su, sg = in.sg;
     // Characteristic projection at the arithmetic-mean state.
     // Every factor from one reciprocal square root y = 1/sqrt(gamma p rho):
-    // 1/c = rho y, c = gamma p y, 1/rho = gamma p y^2.
+    // 1/c = rho y, c = gamma p y, 1/(rho c) = y.
     const T rb = T(0.5) * (in.u[0][0] + in.u[0][su]);
     const T pb = T(0.5) * (in.u[3][0] + in.u[3][su]);
     const T gp = P.gamma * pb;
@@ -579,7 +579,6 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
     const T icb = rb * y;            // 1 / c
     const T cb = gp * y;             // c
     const T c2 = cb * cb;            // c^2
-    const T irb = cb * y;            // 1 / rho
     const T ic2 = icb * icb;         // 1 / c^2
     const T be = T(0.5) * ic2;       // 1 / (2 c^2)
 
@@ -650,7 +649,7 @@ __device__ __forceinline__ void face_flux(const FaceIn<T>& in, const PhysT<T>& P
         // fields 1 and 4 back from their 2 c^2 scaling: with
         // a = w1 + w4, rho = a / (2 c^2) + w2, p = a / 2 and
         // un = (w4 - w1) / (2 rho c)
-        const T hrc = T(0.5) * irb * icb;  // 1 / (2 rho c)
+        const T hrc = T(0.5) * y;  // 1 / (2 rho c): rho c = gamma p rho y = 1 / y
         const T aL03 = wL[0] + wL[3], aR03 = wR[0] + wR[3];
         rL = rfma(be, aL03, wL[1]);
         unL = hrc * (wL[3] - wL[0]);
