@@ -155,7 +155,11 @@ typedef enum {
      * phi = sin(pi/2 min(1, Ma / 0.1)), Ma = max(|u_L|/c_L, |u_R|/c_R) over
      * the face-normal velocities. Faces at Ma >= 0.1 (every supersonic face)
      * keep plain HLLC. All precisions and reconstructions; batches too. */
-    GBR_OPT_RIEMANN = 7
+    GBR_OPT_RIEMANN = 7,
+    /* Batches only: launch form of the stage kernel, 1 = one CTA per tile
+     * (default), 0 = a persistent grid of resident CTAs walking the tile
+     * list. The same results either way; gbr_batch_autotune sets it. */
+    GBR_OPT_LAUNCH = 8
 } gbr_option;
 
 /* Kernel classes reported by gbr_get_timing. */
@@ -353,8 +357,10 @@ int gbr_sync(gbr_ctx *ctx);
 
 /* ----------------------------------------------------------------------
  * Batches: many independent inviscid grids of uneven size stepped together.
- * Every RK stage of every grid runs in one persistent kernel launch (each CTA
- * walks the batch's tile list); each grid advances with its own
+ * Every RK stage of every grid runs in one kernel launch over the batch's
+ * tile list (one CTA per tile, or a persistent grid of resident CTAs that
+ * walks the list, whichever gbr_batch_autotune measured faster; one CTA per
+ * tile until then); each grid advances with its own
  * dt = min(cfl / lambda_k, t_end_k - t_k) formed on the device, so a call to
  * gbr_batch_step_cfl replays a CUDA graph of its nsteps steps without any
  * host synchronisation. Grids, gas and the scheme are as for gbr_create with
@@ -379,7 +385,7 @@ int gbr_batch_destroy(gbr_batch *b);
 int gbr_batch_set_stream(gbr_batch *b, void *stream);
 
 /* GBR_OPT_PRECISION (64 or 32, as for a single grid), GBR_OPT_SENSOR,
- * GBR_OPT_TIMING or GBR_OPT_RIEMANN (for every case). */
+ * GBR_OPT_TIMING or GBR_OPT_RIEMANN (for every case), GBR_OPT_LAUNCH. */
 int gbr_batch_set_option(gbr_batch *b, int key, double val);
 
 /* Set grid k's state ([4][ny_k][nx_k] float64); resets its time to 0 and
@@ -394,9 +400,9 @@ int gbr_batch_get_state(gbr_batch *b, int k, double *Q, int on_device);
 int gbr_batch_set_end_times(gbr_batch *b, const double *t_end);
 
 /* nsteps >= 1 TVD-RK3 steps of every grid at its own CFL time step
- * (cfl > 0). The launch sequence (batched ghost fills and persistent stage
- * kernels) is captured once into a CUDA graph per (nsteps, cfl, precision,
- * tile shape) and replayed. Asynchronous. */
+ * (cfl > 0). The launch sequence (batched ghost fills and stage kernels) is
+ * captured once into a CUDA graph per (nsteps, cfl, precision, tile shape,
+ * launch form) and replayed. Asynchronous. */
 int gbr_batch_step_cfl(gbr_batch *b, double cfl, int nsteps);
 
 /* One TVD-RK3 step (Sec. 2.5, Eq. rk) of every grid at the caller's step
@@ -415,10 +421,13 @@ int gbr_batch_step(gbr_batch *b, const double *dt_per_case);
  * produced rho <= 0, p <= 0 or a non-finite value. */
 int gbr_batch_get_times(gbr_batch *b, double *t, double *dt);
 
-/* Time every candidate tile shape of the current precision on the batch's
- * own grids (`trials` launches of the first RK stage each, which leave the
- * states untouched) and keep the fastest; *choice (may be NULL) receives its
- * index and *bx, *by (may be NULL) its shape. */
+/* Time every candidate tile shape of the current precision, each in both
+ * launch forms (a persistent grid of resident CTAs walking the tile list, or
+ * one CTA per tile), on the batch's own grids (`trials` launches of the
+ * first RK stage each, which leave the states untouched) and keep the
+ * fastest; *choice (may be NULL) receives its index, shape + S * form with S
+ * the number of shapes and form 0 persistent, 1 one CTA per tile, and *bx,
+ * *by (may be NULL) its shape. */
 int gbr_batch_autotune(gbr_batch *b, int trials, int *choice, int *bx, int *by);
 
 /* Sensor weights of the batch (as gbr_set_sensor_weights); enable with

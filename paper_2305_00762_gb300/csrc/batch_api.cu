@@ -25,12 +25,13 @@ struct gbr_batch {
     double* pool;             // all padded states
     int precision;
     int shape;                // index into the precision's tile-shape table
+    int per_tile;             // 1: one CTA per tile; 0: a persistent grid walking the tiles
     int total_tiles;
     long long total_ghosts;
     bool dirty;               // descriptors need uploading
     // cached graph
     cudaGraphExec_t graph;
-    int g_nsteps, g_precision, g_shape;
+    int g_nsteps, g_precision, g_shape, g_per_tile;
     double g_cfl;
     int g_sensor;
     int timing;
@@ -108,12 +109,12 @@ int stage(gbr_batch* b, int k, cudaStream_t s)
     const SensorDev* w = sensor_of(b);
     if (w) TRY(launch_batch_sensor_decide(b->d_cases, b->n, b->total_dtiles, k, w, s));
     cudaError_t e = b->precision == 32
-                        ? launch_batch_stage_f32(b->shape, b->d_cases, b->n, b->total_tiles, k, s, w)
-                        : launch_batch_stage_f64(b->shape, b->d_cases, b->n, b->total_tiles, k, s);
+                        ? launch_batch_stage_f32(b->shape, b->d_cases, b->n, b->total_tiles, k, s, w, b->per_tile)
+                        : launch_batch_stage_f64(b->shape, b->d_cases, b->n, b->total_tiles, k, s, b->per_tile);
     return st(e);
 }
 
-// One RK3 step of every case (Eq. rk): ghost fill + persistent stage kernel,
+// One RK3 step of every case (Eq. rk): ghost fill + batch stage kernel,
 // three times; the first ghost fill forms each case's dt on the device
 // (mode 2: CFL) or takes it from b->d_dt (mode 3: the caller's dt).
 int enqueue_step(gbr_batch* b, double cfl, cudaStream_t s, int mode = 2)
@@ -149,10 +150,10 @@ int batch_step_cfl(gbr_batch* b, double cfl, int nsteps)
     int rc = upload(b);
     if (rc != GBR_OK) return rc;
     if (!b->graph || b->g_nsteps != nsteps || b->g_cfl != cfl || b->g_precision != b->precision ||
-        b->g_shape != b->shape || b->g_sensor != (sensor_of(b) != nullptr)) {
+        b->g_shape != b->shape || b->g_per_tile != b->per_tile || b->g_sensor != (sensor_of(b) != nullptr)) {
         drop_graph(b);
         // first-use kernel setup outside the capture (a negative tile count
-        // prepares the persistent kernel without launching it)
+        // prepares the stage kernel without launching it)
         TRY(b->precision == 32 ? launch_batch_stage_f32(b->shape, b->d_cases, b->n, -1, 0, b->stream, sensor_of(b))
                                : launch_batch_stage_f64(b->shape, b->d_cases, b->n, -1, 0, b->stream));
         if (sensor_of(b)) TRY(launch_batch_sensor_decide(b->d_cases, b->n, -1, 0, sensor_of(b), b->stream));
@@ -179,6 +180,7 @@ int batch_step_cfl(gbr_batch* b, double cfl, int nsteps)
         b->g_cfl = cfl;
         b->g_precision = b->precision;
         b->g_shape = b->shape;
+        b->g_per_tile = b->per_tile;
         b->g_sensor = sensor_of(b) != nullptr;
     }
     return st(cudaGraphLaunch(b->graph, b->stream));
@@ -206,6 +208,7 @@ int gbr_batch_create(int n, const int* nx, const int* ny, const double* dx, cons
     if (!b) return GBR_ERR_NOMEM;
     b->n = n;
     b->precision = 64;
+    b->per_tile = 1;  // measured faster than the persistent grid on the 64-grid ensemble
     b->cases.resize(n);
     int rc = st(cudaGetDevice(&b->device));
     long long total = 0, ghosts = 0;
@@ -319,6 +322,11 @@ int gbr_batch_set_option(gbr_batch* b, int key, double val)
         b->dirty = true;
         return GBR_OK;
     }
+    if (key == GBR_OPT_LAUNCH) {  // a cached graph of the other form is re-captured
+        if (val != 0.0 && val != 1.0) return GBR_ERR_ARG;
+        b->per_tile = (int)val;
+        return GBR_OK;
+    }
     return GBR_ERR_ARG;
 }
 
@@ -425,8 +433,10 @@ int gbr_batch_autotune(gbr_batch* b, int trials, int* choice, int* bx, int* by)
     if (rc == GBR_OK)
         rc = st(cudaMemcpyAsync(b->d_scal, tuned.data(), sizeof(DevScalars) * b->n, cudaMemcpyHostToDevice,
                                 b->stream));
-    for (int c = 0; c < ns && rc == GBR_OK; ++c) {
-        b->shape = c;
+    // candidate c: shape c % ns, launch form c / ns (0 persistent, 1 one CTA per tile)
+    for (int c = 0; c < 2 * ns && rc == GBR_OK; ++c) {
+        b->shape = c % ns;
+        b->per_tile = c / ns;
         retile(b);
         if ((rc = upload(b)) != GBR_OK) break;
         rc = st(launch_batch_ghosts(b->d_cases, b->n, b->total_ghosts, 0, 0, 0.0, b->stream));
@@ -447,14 +457,15 @@ int gbr_batch_autotune(gbr_batch* b, int trials, int* choice, int* bx, int* by)
     int rc2 = st(cudaMemcpyAsync(b->d_scal, h.data(), sizeof(DevScalars) * b->n, cudaMemcpyHostToDevice, b->stream));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->shape = best;
+    b->shape = best % ns;
+    b->per_tile = best / ns;
     retile(b);
     if (rc == GBR_OK) rc = rc2;
     if (rc == GBR_OK) rc = upload(b);
     if (rc == GBR_OK) rc = st(cudaStreamSynchronize(b->stream));
     if (choice) *choice = best;
-    if (bx) *bx = sh[best].bx;
-    if (by) *by = sh[best].by;
+    if (bx) *bx = sh[best % ns].bx;
+    if (by) *by = sh[best % ns].by;
     return rc;
 }
 

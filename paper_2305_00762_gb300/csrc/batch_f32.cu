@@ -1,5 +1,5 @@
-// FP32-arithmetic instantiations of the persistent batch stage kernel
-// (candidate tile shapes picked by the batch autotuner).
+// FP32-arithmetic instantiations of the batch stage kernel (candidate tile
+// shapes and launch forms picked by the batch autotuner).
 #include "batch_stage.cuh"
 
 namespace gbr {
@@ -13,19 +13,19 @@ int batch_tile_shapes_f32(const TileShape** shapes)
 }
 
 cudaError_t launch_batch_stage_f32(int shape, const BatchCase* cases, int ncases, int total_tiles, int stage,
-                                   cudaStream_t s, const SensorDev* sensor)
+                                   cudaStream_t s, const SensorDev* sensor, bool per_tile)
 {
     if (sensor) {
         switch (shape) {
-        case 0: return launch_batch_t<float, 28, 16, 256, true>(cases, ncases, total_tiles, stage, s, sensor);
-        case 1: return launch_batch_t<float, 32, 16, 256, true>(cases, ncases, total_tiles, stage, s, sensor);
-        default: return launch_batch_t<float, 32, 8, 256, true>(cases, ncases, total_tiles, stage, s, sensor);
+        case 0: return launch_batch_t<float, 28, 16, 256, true>(cases, ncases, total_tiles, stage, s, sensor, per_tile);
+        case 1: return launch_batch_t<float, 32, 16, 256, true>(cases, ncases, total_tiles, stage, s, sensor, per_tile);
+        default: return launch_batch_t<float, 32, 8, 256, true>(cases, ncases, total_tiles, stage, s, sensor, per_tile);
         }
     }
     switch (shape) {
-    case 0: return launch_batch_t<float, 28, 16, 256>(cases, ncases, total_tiles, stage, s);
-    case 1: return launch_batch_t<float, 32, 16, 256>(cases, ncases, total_tiles, stage, s);
-    default: return launch_batch_t<float, 32, 8, 256>(cases, ncases, total_tiles, stage, s);
+    case 0: return launch_batch_t<float, 28, 16, 256>(cases, ncases, total_tiles, stage, s, nullptr, per_tile);
+    case 1: return launch_batch_t<float, 32, 16, 256>(cases, ncases, total_tiles, stage, s, nullptr, per_tile);
+    default: return launch_batch_t<float, 32, 8, 256>(cases, ncases, total_tiles, stage, s, nullptr, per_tile);
     }
 }
 

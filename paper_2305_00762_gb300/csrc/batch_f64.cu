@@ -1,5 +1,5 @@
-// FP64 instantiations of the persistent batch stage kernel (candidate tile
-// shapes picked by the batch autotuner).
+// FP64 instantiations of the batch stage kernel (candidate tile shapes and
+// launch forms picked by the batch autotuner).
 #include "batch_stage.cuh"
 
 namespace gbr {
@@ -13,12 +13,12 @@ int batch_tile_shapes_f64(const TileShape** shapes)
 }
 
 cudaError_t launch_batch_stage_f64(int shape, const BatchCase* cases, int ncases, int total_tiles, int stage,
-                                   cudaStream_t s)
+                                   cudaStream_t s, bool per_tile)
 {
     switch (shape) {
-    case 0: return launch_batch_t<double, 32, 8, 256>(cases, ncases, total_tiles, stage, s);
-    case 1: return launch_batch_t<double, 16, 16, 256>(cases, ncases, total_tiles, stage, s);
-    default: return launch_batch_t<double, 64, 4, 256>(cases, ncases, total_tiles, stage, s);
+    case 0: return launch_batch_t<double, 32, 8, 256>(cases, ncases, total_tiles, stage, s, nullptr, per_tile);
+    case 1: return launch_batch_t<double, 16, 16, 256>(cases, ncases, total_tiles, stage, s, nullptr, per_tile);
+    default: return launch_batch_t<double, 64, 4, 256>(cases, ncases, total_tiles, stage, s, nullptr, per_tile);
     }
 }
 

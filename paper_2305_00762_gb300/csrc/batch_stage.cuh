@@ -1,8 +1,9 @@
-// Persistent per-stage kernel of a batch of independent grids: every CTA
-// walks the batch's tile list (tile = blockIdx.x + k gridDim.x), finds the
-// tile's grid and runs the same fused tile body as the single-grid kernel,
-// with that grid's own dt, wavespeed slot and error word. Grids whose dt is
-// zero (stopped at their end time) are skipped.
+// Per-stage kernel of a batch of independent grids: every CTA walks the
+// batch's tile list (tile = blockIdx.x + k gridDim.x; a persistent grid of
+// resident CTAs, or one CTA per tile when the grid covers the list), finds
+// the tile's grid and runs the same fused tile body as the single-grid
+// kernel, with that grid's own dt, wavespeed slot and error word. Grids
+// whose dt is zero (stopped at their end time) are skipped.
 #pragma once
 
 #include "stage_kernel.cuh"
@@ -83,14 +84,14 @@ cudaError_t batch_blocks(int* out)
 // total_tiles < 0: only prepare the kernel (batch_blocks), launch nothing.
 template <typename T, int BX, int BY, int NT, bool LEARNED = false>
 cudaError_t launch_batch_t(const BatchCase* cases, int ncases, int total_tiles, int stage, cudaStream_t s,
-                           const SensorDev* sensor = nullptr)
+                           const SensorDev* sensor = nullptr, bool per_tile = false)
 {
     using L = TileLayout<BX, BY, false>;
     constexpr size_t smem = L::template total_bytes<T, NT, LEARNED>();
     int blocks = 0;
     cudaError_t e = batch_blocks<T, BX, BY, NT, LEARNED>(&blocks);
     if (e != cudaSuccess || total_tiles <= 0) return e;
-    const int grid = total_tiles < blocks ? total_tiles : blocks;
+    const int grid = (per_tile || total_tiles < blocks) ? total_tiles : blocks;
     batch_stage_kernel<T, BX, BY, NT, LEARNED><<<grid, NT, smem, s>>>(cases, ncases, total_tiles, stage, sensor);
     return cudaGetLastError();
 }

@@ -156,11 +156,13 @@ cudaError_t launch_batch_ghosts(const BatchCase* cases, int ncases, long long to
 // Candidate tile shapes of the persistent batch kernel (returns the count).
 int batch_tile_shapes_f64(const TileShape** shapes);
 int batch_tile_shapes_f32(const TileShape** shapes);
-// Persistent kernel over all tiles of all cases for RK stage `stage` (0, 1, 2).
+// One kernel over all tiles of all cases for RK stage `stage` (0, 1, 2):
+// per_tile = false, a persistent grid (resident CTAs x SMs) whose CTAs walk
+// the tile list; true, one CTA per tile.
 cudaError_t launch_batch_stage_f64(int shape, const BatchCase* cases, int ncases, int total_tiles, int stage,
-                                   cudaStream_t s);
+                                   cudaStream_t s, bool per_tile = false);
 cudaError_t launch_batch_stage_f32(int shape, const BatchCase* cases, int ncases, int total_tiles, int stage,
-                                   cudaStream_t s, const SensorDev* sensor = nullptr);
+                                   cudaStream_t s, const SensorDev* sensor = nullptr, bool per_tile = false);
 // Learned sensor (sensor.cu): host packing of the weight vector, per-cell
 // evaluation / dataset extraction on a padded state, training.
 void pack_sensor(const float* w, SensorDev* out);

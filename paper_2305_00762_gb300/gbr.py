@@ -21,7 +21,7 @@ GBR_ERR_TIMEOUT, GBR_ERR_STATE, GBR_ERR_NOMEM, GBR_ERR_UNSUPPORTED = -4, -5, -6,
 GBR_BC_PERIODIC, GBR_BC_TRANSMISSIVE, GBR_BC_NOSLIP_WALL, GBR_BC_SYMMETRY = 0, 1, 2, 3
 GBR_BC_CUSTOM, GBR_BC_FIXED, GBR_BC_HALO = 4, 5, 6
 GBR_OPT_PRECISION, GBR_OPT_RECORD_FLAGS, GBR_OPT_SENSOR, GBR_OPT_TIMING, GBR_OPT_ORDER = 0, 1, 2, 3, 4
-GBR_OPT_VARIABLES, GBR_OPT_STALL_TEST, GBR_OPT_RIEMANN = 5, 6, 7
+GBR_OPT_VARIABLES, GBR_OPT_STALL_TEST, GBR_OPT_RIEMANN, GBR_OPT_LAUNCH = 5, 6, 7, 8
 GBR_KERNEL_STAGE, GBR_KERNEL_GHOST, GBR_KERNEL_WAVESPEED, GBR_KERNEL_CLASSES = 0, 1, 2, 3
 GBR_GHOST = 6
 GBR_STATIC_SCRATCH_DOUBLES = 1 << 20
