@@ -95,7 +95,7 @@ FP32_PEAK_NOMINAL = 80550.0   # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 G
 # (dram__bytes_read.sum + dram__bytes_write.sum) of
 # `bench.py --profile-only --n N --steps 2 --warmup 1 --state-cache ...`.
 # Re-measure when the kernel changes (None: not measured for this kernel).
-F64_STAGE_DRAM_BYTES = {1024: 59.80e6, 4096: 1406.19e6}
+F64_STAGE_DRAM_BYTES = {1024: 59.58e6, 4096: 1405.94e6}
 
 
 def fma_peaks():
