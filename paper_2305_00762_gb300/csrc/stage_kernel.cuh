@@ -180,6 +180,27 @@ __device__ __forceinline__ T mp_clamp(T p2, T p3, T md, T ul, T lc, T pl)
     const T pmax = tmax(p2, tmin(tmax(p3, md), tmax(ul, lc)));
     return tmin(tmax(pl, pmin), pmax);
 }
+// FP32: the bounds as the paper writes them, each a maximum (minimum) of two
+// three-operand minima (maxima), the min / max instructions taking three
+// operands.
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float mp_clamp(float p2, float p3, float md, float ul, float lc, float pl)
+{
+    const float pmin = fmaxf(fmin3(p2, p3, md), fmin3(p2, ul, lc));
+    const float pmax = fminf(fmax3(p2, p3, md), fmax3(p2, ul, lc));
+    return fminf(fmaxf(pl, pmin), pmax);
+}
 __device__ __forceinline__ double mp_clamp(double p2, double p3, double md, double ul, double lc, double pl)
 {
     const long long k2 = ordkey(p2), k3 = ordkey(p3), km = ordkey(md), ku = ordkey(ul), kl = ordkey(lc);
